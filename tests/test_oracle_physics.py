@@ -1,0 +1,133 @@
+"""Physics pins of the FP64 oracle (CPU): closed-form or textbook results the whole step must
+reproduce.  Laplace law for a static drop (Sec. 6.2), the tanh equilibrium interface profile
+(Sec. 2 Eq. hyperbolictangentprofile), layered two-phase Poiseuille flow (viscosity
+interpolation, Eq. fluidviscosity, body force, walls), diffusion at the mobility M_phi (Sec. 5),
+and the integrated Marangoni traction of a flat interface (Sec. 6.7).
+"""
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import oracle as O
+from paper_1909_04166_gb300 import workloads as W
+
+
+def discrete_surface_factor(width, offset=0.0):
+    """Sum over nodes of (central-difference d phi/d zeta)^2 across a sampled tanh profile,
+    divided by its continuum value 2/(3W): the discrete surface-energy factor that multiplies
+    sigma in kappa-tilde = (3/2) sigma W on the lattice."""
+    z = np.arange(-80, 81) + offset
+    phi = W.tanh_profile(z, width)
+    d = 0.5 * (phi[2:] - phi[:-2])
+    return float(np.sum(d * d) / (2.0 / (3.0 * width)))
+
+
+def run_case(case, nsteps):
+    oc = O.OracleCase.from_dict(case.params)
+    fl = case["fields"]
+    g, f = O.init(oc, fl["phi"], fl["p"], fl["ux"], fl["uy"])
+    g, f = O.run(oc, g, f, nsteps)
+    return oc, g, f, O.fields(oc, g, f)
+
+
+def laplace_dp(case, fields):
+    n = case["nx"]
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    r = np.hypot(x - n / 2, y - n / 2)
+    R, Wd = case["meta"]["radius"], case["width"]
+    return fields["p"][r < R - 2 * Wd].mean() - fields["p"][r > R + 2 * Wd].mean()
+
+
+@pytest.mark.parametrize("ratio,width", [(1000.0, 5.0), (10.0, 4.0)])
+def test_laplace_law(ratio, width):
+    sigma = 1e-3
+    case = W.laplace(n=64, radius=16.0, width=width, rho_ratio=ratio, sigma=sigma)
+    oc, g, f, fl = run_case(case, 3000)
+    assert np.isfinite(fl["p"]).all()
+    dp = laplace_dp(case, fl)
+    r_eff = np.sqrt(fl["phi"].sum() / np.pi)
+    expect = sigma * discrete_surface_factor(width) / r_eff
+    assert dp == pytest.approx(expect, rel=0.015)
+    # spurious currents stay small next to the capillary velocity sigma / mu
+    assert np.hypot(fl["ux"], fl["uy"]).max() < 0.1 * sigma / case["mu_a"]
+
+
+def test_laplace_pressure_is_linear_in_sigma():
+    dps = []
+    for sigma in (5e-4, 1e-3, 2e-3):
+        case = W.laplace(n=48, radius=12.0, width=5.0, rho_ratio=100.0, sigma=sigma)
+        _, _, _, fl = run_case(case, 2000)
+        dps.append(laplace_dp(case, fl))
+    assert dps[1] / dps[0] == pytest.approx(2.0, rel=0.01)
+    assert dps[2] / dps[1] == pytest.approx(2.0, rel=0.01)
+
+
+def test_flat_interface_keeps_tanh_profile():
+    """The tanh profile is the interface's equilibrium up to the second-order lattice error:
+    the steady deviation falls like 1/W^2 and the slab stays at rest."""
+    errs = []
+    for width in (4.0, 8.0):
+        case = W.flat(nx=4, ny=64, width=width, mobility=0.05, rho_ratio=10.0)
+        _, _, _, fl = run_case(case, 2000)
+        errs.append(np.abs(fl["phi"] - case["fields"]["phi"]).max())
+        assert errs[-1] < 0.11 / width ** 2
+        assert np.hypot(fl["ux"], fl["uy"]).max() < 1e-7
+    assert 3.0 < errs[0] / errs[1] < 5.0
+
+
+def _layered_reference(case):
+    """Steady u(y) of d/dy (mu(y) du/dy) = -F between walls at y = -1/2 and ny - 1/2, with
+    mu(y) = mu_B + phi(y) (mu_A - mu_B) and phi the tanh profile of the initial interface."""
+    ny = case["ny"]
+    F = case["gx"] * case["rho_a"]
+    yi = (ny - 1) / 2.0
+    mu = lambda s: case["mu_b"] + W.tanh_profile(yi - s, case["width"]) * (case["mu_a"]
+                                                                            - case["mu_b"])
+    a, b = -0.5, ny - 0.5
+    i1 = integrate.quad(lambda s: 1.0 / mu(s), a, b, limit=200)[0]
+    i2 = integrate.quad(lambda s: s / mu(s), a, b, limit=200)[0]
+    y0 = i2 / i1
+    return np.array([-F * integrate.quad(lambda s: (s - y0) / mu(s), a, yy, limit=200)[0]
+                     for yy in range(ny)])
+
+
+@pytest.mark.parametrize("mu_b", [0.1, 0.025])
+def test_layered_poiseuille(mu_b):
+    case = W.layered(nx=4, ny=32, mu_a=0.1, mu_b=mu_b, force=1e-6, width=4.0)
+    _, _, _, fl = run_case(case, 30000)
+    u = fl["ux"].mean(axis=1)
+    ref = _layered_reference(case)
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 0.01
+    assert np.abs(fl["uy"]).max() < 1e-3 * np.abs(ref).max()
+
+
+def test_phase_field_diffuses_at_the_mobility():
+    """With equal densities, no surface tension and a very wide interface (theta -> 0) the
+    interface lattice solves d phi/dt = M_phi lap phi: a Gaussian's variance grows by 2 M_phi t
+    per axis."""
+    n, s0, M, t = 64, 4.0, 0.05, 200
+    case = W.flat(nx=n, ny=n, width=1e9, mobility=M, rho_ratio=1.0, sigma=0.0)
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    bump = 0.1 * np.exp(-((x - n / 2) ** 2 + (y - n / 2) ** 2) / (2 * s0 * s0))
+    case["fields"]["phi"] = 0.5 + bump
+    _, _, _, fl = run_case(case, t)
+    d = fl["phi"] - 0.5
+    var_x = np.sum(d * (x - n / 2) ** 2) / np.sum(d)
+    assert (var_x - s0 * s0) / (2 * t) == pytest.approx(M, rel=0.01)
+
+
+@pytest.mark.parametrize("width,tol", [(4.0, 0.07), (8.0, 0.02)])
+def test_marangoni_traction_of_flat_interface(width, tol):
+    """Across a flat interface the tangential surface force integrates to the surface gradient
+    of sigma (Sec. 6.7 Eq. surfacetensiongeometricsurfactantsxcomp); the normal one to zero."""
+    case = W.flat(nx=8, ny=64, width=width, mobility=0.05, rho_ratio=1.0, sigma=1e-3)
+    case.update(dsigma_dT=-2e-6, gradT_x=0.01)
+    oc = O.OracleCase.from_dict(case.params)
+    fl = case["fields"]
+    g, f = O.init(oc, fl["phi"], fl["p"], fl["ux"], fl["uy"])
+    col = [O.node_info(oc, g, f, 3, j) for j in range(case["ny"] // 2)]   # lower interface
+    fsx = sum(c["Fsx"] for c in col)
+    fsy = sum(c["Fsy"] for c in col)
+    dsig_dx = case["dsigma_dT"] * case["gradT_x"]
+    assert fsx == pytest.approx(dsig_dx, rel=tol)
+    assert abs(fsy) < 1e-9 * abs(dsig_dx)
