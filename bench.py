@@ -1,0 +1,372 @@
+"""Throughput of the fused cascaded two-phase LB step on GB300.
+
+One bench step = one time step of both D2Q9 lattices over the whole grid (one fused kernel
+launch).  Default workload: drop impact on a thin film at density ratio 1000 on a 2048 x 1024
+grid, FP32 populations (the bandwidth headline).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload impact|rt|marangoni|laplace] [--precision fp32|fp64]
+
+For N > 1 (torchrun, one rank per GPU) every rank advances its own replica of the workload
+(weak scaling; the path has no data exchange between replicas).  ``--impl reference`` times the
+FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_LU = {"fp32": 144, "fp64": 288}       # 18 populations read + written once per node
+HBM_FALLBACK_GBS = 6800.0
+L2_BYTES = 129e6
+METRIC = "MLUPS (million node updates of both lattices per second)"
+
+
+def workload(name: str):
+    from paper_1909_04166_gb300 import workloads as W
+    if name == "impact":
+        return W.impact()
+    if name == "rt":
+        return W.rt()
+    if name == "marangoni":
+        return W.marangoni()
+    if name == "laplace":
+        return W.laplace(n=64, radius=16.0, width=5.0)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def describe(case) -> dict:
+    keys = ("nx", "ny", "rho_a", "rho_b", "mu_a", "mu_b", "sigma0", "dsigma_dT", "gradT_x",
+            "mobility", "width", "gx", "gy")
+    d = {k: case[k] for k in keys}
+    d["bc"] = ("wall" if case["wall_x"] else "periodic") + "_x/" + (
+        "wall" if case["wall_y"] else "periodic") + "_y"
+    return d
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs"):
+            if k in d:
+                return float(d[k]), "measured"
+    except Exception:
+        pass
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("lbm_step.cu", "lbm_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1909_04166_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM traffic per launch of the step kernel from an ncu capture (profiles/), keyed by the
+# hash of the kernel sources it was taken on; scaled by node count to the bench workload.
+NCU_TRAFFIC = {}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1909_04166_gb300 import lbm
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    case = workload(args.workload)
+    N = case.nodes
+    stream = torch.cuda.current_stream()
+    params = lbm.make_params(case, args.precision, device=local, stream=stream.cuda_stream)
+    nbytes = lbm.lbm_state_bytes(params)
+    state = torch.empty(nbytes, dtype=torch.uint8, device="cuda")        # device memory
+    ctx = lbm.lbm_create_with_buffer(params, state.data_ptr(), nbytes)
+    fl = case["fields"]
+    dev = {k: torch.tensor(fl[k], dtype=torch.float64, device="cuda") for k in
+           ("phi", "p", "ux", "uy")}
+    lbm.lbm_init_fields_device(ctx, *(dev[k].data_ptr() for k in ("phi", "p", "ux", "uy")))
+    lbm.lbm_step(ctx, args.warmup)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ev[0].record(stream)
+        for k in range(K):
+            lbm.lbm_step(ctx, 1)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms_total = ev[0].elapsed_time(ev[K])
+    per_launch = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
+    ms_launch = float(np.mean(per_launch))
+    t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    diag = lbm.lbm_diagnostics(ctx)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = {k: torch.tensor(fl[k], dtype=torch.float64).pin_memory() for k in
+               ("phi", "p", "ux", "uy")}
+        out = {k: torch.empty((case["ny"], case["nx"]), dtype=torch.float64).pin_memory()
+               for k in ("phi", "p", "ux", "uy", "rho")}
+        host = {k: v.numpy() for k, v in pin.items()}
+        hout = {k: v.numpy() for k, v in out.items()}
+        Ke = args.e2e_steps
+        lbm.lbm_init_fields(ctx, *(host[k] for k in ("phi", "p", "ux", "uy")))
+        lbm.lbm_step(ctx, 3)
+        lbm.lbm_get_fields(ctx, *(hout[k] for k in ("phi", "p", "ux", "uy", "rho")))
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        lbm.lbm_init_fields(ctx, *(host[k] for k in ("phi", "p", "ux", "uy")))
+        lbm.lbm_step(ctx, Ke)
+        lbm.lbm_get_fields(ctx, *(hout[k] for k in ("phi", "p", "ux", "uy", "rho")))
+        te = time.perf_counter() - t0
+        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+        e2e = {"value": round(ws * N * Ke / te / 1e6, 2), "unit": "MLUPS",
+               "h2d_bytes_per_step": int(4 * 8 * N / Ke),
+               "d2h_bytes_per_step": int(5 * 8 * N / Ke),
+               "steps_per_call": Ke,
+               "note": "lbm_init_fields(host) + lbm_step(K) + lbm_get_fields(host), wall clock"}
+
+    lbm.lbm_destroy(ctx)
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    bpl = BYTES_PER_LU[args.precision]
+    peak, peak_kind = measured_peak()
+    achieved = bpl * N / (ms_launch * 1e-3) / 1e9
+    traffic = None
+    hsh = kernel_source_hash()
+    key = (hsh, args.workload, args.precision)
+    if key in NCU_TRAFFIC:
+        traffic = NCU_TRAFFIC[key]
+    seg, block = None, None
+    value = ws * N * K / (ms_max * 1e-3) / 1e6
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "MLUPS",
+        "n_gpus": ws,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_max / K, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded initial fields of the paper's setup; no dataset)",
+        "config": {
+            "workload": f"{args.workload} {case['nx']}x{case['ny']} {args.precision} "
+                        f"populations",
+            **describe(case),
+            "nodes": N,
+            "l2": f"inputs larger than L2 (no flush): state {N * bpl / 1e6:.0f} MB "
+                  f"vs {L2_BYTES / 1e6:.0f} MB L2",
+            "parallelism": f"replicas x{ws}",
+        },
+        "roofline": {
+            "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "peak_source": f"{peak_kind} HBM copy bandwidth",
+            "bytes_per_lu": bpl, "ms_per_launch": round(ms_launch, 5),
+            "kernel": "cmlbm::step_kernel", "kernel_hash": hsh,
+        },
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": K,
+        "state_check": {"sum_phi": diag["sum_phi"], "max_speed": diag["max_speed"],
+                        "nonfinite": diag["nonfinite"]},
+    }
+    if args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(case, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_band(case, rows):
+    """Oracle state on a band of rows [y0 - 1, y0 + rows] of the case (initialisation is
+    node-local, so rows of a smaller initialisation are rows of the full one)."""
+    from oracle import oracle as O
+    ny, nx = case["ny"], case["nx"]
+    y0 = max(1, ny // 2 - rows // 2)
+    y1 = min(ny - 1, y0 + rows)
+    sub = dict(case.params)
+    lo, hi = y0 - 1, y1 + 1
+    sub["ny"] = hi - lo
+    fl = case["fields"]
+    g_band, f_band = O.init(O.OracleCase.from_dict(sub), *(fl[k][lo:hi] for k in
+                                                           ("phi", "p", "ux", "uy")))
+    g = np.zeros((9, ny, nx))
+    f = np.zeros((9, ny, nx))
+    g[:, lo:hi] = g_band
+    f[:, lo:hi] = f_band
+    return O.OracleCase.from_dict(case.params), g, f, y0, y1
+
+
+def cpu_baseline(case, seconds):
+    """FP64 oracle on the host cores: one time step over a band of rows of the same grid,
+    repeated for about `seconds` of CPU work."""
+    from oracle import oracle as O
+    oc, g, f, y0, y1 = _oracle_band(case, 64)
+    gn, fn = np.zeros_like(g), np.zeros_like(f)
+    O.step_rows(oc, g, f, gn, fn, y0, y1)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        O.step_rows(oc, g, f, gn, fn, y0, y1)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            break
+    nodes = n * (y1 - y0) * case["nx"]
+    return {"value": round(nodes / dt / 1e6, 3), "unit": "MLUPS", "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": f"{n} time steps of rows [{y0},{y1}) of the {case['nx']}x{case['ny']} "
+                      f"grid ({nodes} node updates, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    case = workload(args.workload)
+    rows = 16
+    oc, g, f, y0, y1 = _oracle_band(case, rows)
+    gn, fn = np.zeros_like(g), np.zeros_like(f)
+    for _ in range(args.warmup):
+        O.step_rows(oc, g, f, gn, fn, y0, y1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.step_rows(oc, g, f, gn, fn, y0, y1)
+    dt = time.perf_counter() - t0
+    nodes = args.steps * (y1 - y0) * case["nx"]
+    v = nodes / dt / 1e6
+    line = {
+        "metric": METRIC, "value": round(v, 3), "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded initial fields of the paper's setup; no dataset)",
+        "config": {"workload": f"{args.workload} {case['nx']}x{case['ny']} {args.precision} "
+                               f"populations", **describe(case), "nodes": case.nodes,
+                   "parallelism": "host cores (OpenMP over rows)"},
+        "impl": "reference",
+        "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": O.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"each step: one time step of rows [{y0},{y1}) of the grid"},
+        "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="impact")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=2000)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * cmlbm.h - C ABI of the GB300 (sm_103a) library for the coupled cascaded central-moment
+ * lattice Boltzmann schemes of Hajabdollahi, Premnath & Welch, "Central Moment Lattice
+ * Boltzmann Method using a Pressure-based Formulation for Multiphase Flows at High Density
+ * Ratios and including Effects of Surface Tension and Marangoni Stresses" (arXiv:1909.04166).
+ *
+ * What one time step computes (lbm_step), for every node of an nx x ny D2Q9 lattice:
+ *   - phi = sum_a f_a (Sec. 5) and p* = sum_a g-bar_a (Sec. 4) on the node and its neighbours;
+ *   - rho = rho_B + phi (rho_A - rho_B), mu = mu_B + phi (mu_A - mu_B) (Sec. 2, linear
+ *     interpolation with phi_A = 1, phi_B = 0);
+ *   - second-order isotropic gradients / Laplacian / Hessian of phi and the gradient of p*
+ *     (Sec. 4, closing remark);
+ *   - the geometric surface-tension force with its Marangoni part (Sec. 2 Eq.
+ *     surfacetensiongeometric; Sec. 6.7 Eqs. surfacetensiongeometricsurfactantsxcomp/ycomp),
+ *     kappa-tilde = (3/2) sigma(T) W, sigma(T) = sigma0 + dsigma_dT (T - T0),
+ *     T = T0 + gradT_x x + gradT_y y;
+ *   - F_ext = (rho - rho_ref) (gx, gy); F_t = F_s + F_ext; F_p = -grad p* + c_s^2 (rho_A -
+ *     rho_B) grad phi (Sec. 3 Eq. netgradientpressureforce);
+ *   - corrected u and p (Sec. 4 Eq. hydrodynamicfields);
+ *   - the fluid cascaded collision with its cumulative source (Sec. 4 Eqs.
+ *     cascadedcollisionoperator, cumulativesourcetermcomponents, postcollisioncascadedLBscheme),
+ *     shear rates from mu (Eq. fluidviscosity), all other rates 1;
+ *   - the interface (conservative Allen-Cahn) cascaded collision with M_phi theta n in its
+ *     first-order equilibria (Sec. 5), omega^phi_{1,2} from M_phi, all other rates 1;
+ *   - streaming of both lattices, with half-way bounce-back at no-slip walls.
+ *
+ * Conventions: c_s^2 = 1/3, lattice units (dx = dt = 1).  Node (i, j) is at x = i, y = j.
+ * Host nodal arrays are row-major [ny][nx] doubles.  Population arrays are [9][ny][nx] doubles
+ * with the D2Q9 ordering e_x = (0,1,0,-1,0,1,-1,-1,1), e_y = (0,0,1,0,-1,1,1,-1,-1) (Sec. 4
+ * Eq. particlevelocities); g is the fluid lattice (g-bar of Sec. 4), f the interface lattice.
+ * The library state holds the streamed (pre-collision) populations of the current time level.
+ *
+ * Ownership: the caller owns every host array; the library copies in and out and never keeps a
+ * host pointer.  The library owns its device buffers unless they are supplied through
+ * lbm_create_with_buffer, in which case the caller owns them and must keep them alive until
+ * lbm_destroy.  All device work is issued on params.stream (a cudaStream_t; NULL = the legacy
+ * default stream).  Calls that return host data synchronise that stream.
+ *
+ * Errors: every int-returning call returns LBM_OK (0) or a negative code; no call aborts, exits
+ * or traps on the device.  lbm_strerror gives a message.  A failed call leaves the context
+ * usable unless the code is LBM_ERR_CUDA (then the CUDA context may be unusable; see
+ * lbm_last_cuda_error).
+ */
+#ifndef CMLBM_H
+#define CMLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_ERR_ARG (-1)        /* NULL pointer, size out of range, unknown enum value */
+#define LBM_ERR_PARAM (-2)      /* physically invalid parameter (rho <= 0, mu <= 0, W <= 0,
+                                   M_phi <= 0, non-finite value) */
+#define LBM_ERR_CUDA (-3)       /* a CUDA runtime call failed */
+#define LBM_ERR_NOMEM (-4)      /* device allocation failed */
+#define LBM_ERR_STATE (-5)      /* the state was never initialised */
+#define LBM_ERR_NONFINITE (-6)  /* a diagnostic found NaN or Inf in the fields */
+#define LBM_ERR_UNSUPPORTED (-7)/* precision mode not built into this library */
+
+/* Storage / compute precision of a context. */
+typedef enum {
+    LBM_FP64 = 0,  /* populations stored and collided in double (correctness mode) */
+    LBM_FP32 = 1   /* populations stored and collided in float */
+} lbm_precision;
+
+/* Boundary pair along one axis. */
+typedef enum {
+    LBM_PERIODIC = 0,
+    LBM_WALL = 1   /* no-slip walls half a node outside the first and last node (half-way
+                      bounce-back on both lattices; mirror ghosts for the stencils) */
+} lbm_bc;
+
+/* Problem statement of one case (Secs. 2, 4-6 of the paper). */
+typedef struct {
+    int32_t nx, ny;                 /* nodes along x and y, 1 .. 65536 each */
+    int32_t bc_x, bc_y;             /* lbm_bc for the x pair (left/right) and y pair (bottom/top) */
+    double rho_a, rho_b;            /* densities of phase A (phi = 1) and phase B (phi = 0) */
+    double mu_a, mu_b;              /* dynamic viscosities */
+    double sigma0, dsigma_dT;       /* sigma(T) = sigma0 + dsigma_dT (T - T0) */
+    double T0, gradT_x, gradT_y;    /* prescribed temperature T = T0 + gradT_x x + gradT_y y */
+    double mobility, width;         /* M_phi and interface width W of the Allen-Cahn equation */
+    double gx, gy, rho_ref;         /* body force F_ext = (rho - rho_ref) (gx, gy) */
+    int32_t precision;              /* lbm_precision */
+    int32_t device;                 /* CUDA device ordinal */
+    void* stream;                   /* cudaStream_t for all work of the context */
+} lbm_params;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Scalar diagnostics of the current state, accumulated in double on the device. */
+typedef struct {
+    double sum_phi;      /* sum over nodes of phi = sum_a f_a (global phase mass) */
+    double sum_p;        /* sum over nodes of the corrected pressure p */
+    double max_speed;    /* max over nodes of |u| */
+    double dp_laplace;   /* mean p over r < r_in minus mean p over r > r_out about (xc, yc)
+                            (periodic distances), 0 if a region is empty */
+    int64_t nonfinite;   /* nodes whose phi, p or u is NaN or Inf */
+} lbm_diag;
+
+/* Device bytes the state of a case needs (two ping-pong population buffers); for
+ * lbm_create_with_buffer.  Returns LBM_OK, or LBM_ERR_ARG / LBM_ERR_PARAM. */
+int lbm_state_bytes(const lbm_params* params, size_t* bytes);
+
+/* Validate params, derive the per-case constants and allocate the state on params.device.
+ * On success *out is a new context; on error *out is NULL. */
+int lbm_create(const lbm_params* params, lbm_ctx** out);
+
+/* As lbm_create, but the state lives in the caller's device buffer (16-byte aligned, at least
+ * lbm_state_bytes bytes, on params.device); the caller keeps ownership. */
+int lbm_create_with_buffer(const lbm_params* params, void* device_buffer, size_t bytes,
+                           lbm_ctx** out);
+
+/* Equilibrium initialisation from host nodal fields phi, p, ux, uy ([ny][nx] doubles): the
+ * fluid populations take the central moments of the transformed Maxwellian (Sec. 3 Eq.
+ * centralmomentsgeqcomponents), the interface populations those of Sec. 5 with the
+ * M_phi theta n term zero.  Synchronises the stream.  Resets the step counter. */
+int lbm_init_fields(lbm_ctx* ctx, const double* phi, const double* p, const double* ux,
+                    const double* uy);
+
+/* As lbm_init_fields with device pointers (doubles on params.device); asynchronous. */
+int lbm_init_fields_device(lbm_ctx* ctx, const double* phi, const double* p, const double* ux,
+                           const double* uy);
+
+/* Advance nsteps (>= 0) time steps: one fused kernel launch per step on params.stream,
+ * asynchronous; launch errors are returned. */
+int lbm_step(lbm_ctx* ctx, int32_t nsteps);
+
+/* Fields of the current state into host arrays ([ny][nx] doubles): phi, the corrected p, u and
+ * rho as defined by Sec. 4 Eq. hydrodynamicfields.  Any pointer may be NULL.  Synchronises. */
+int lbm_get_fields(lbm_ctx* ctx, double* phi, double* p, double* ux, double* uy, double* rho);
+
+/* Checkpoint / restore of the raw state: g and f as [9][ny][nx] doubles each (converted from /
+ * to the storage precision).  Synchronises.  A restored state steps exactly as the saved one. */
+int lbm_get_populations(lbm_ctx* ctx, double* g, double* f);
+int lbm_set_populations(lbm_ctx* ctx, const double* g, const double* f);
+
+/* Device pointer of the current state (18 planes of ny rows of `pitch` elements, element type
+ * double for LBM_FP64, float for LBM_FP32); valid until the next lbm_step. */
+int lbm_state_device(lbm_ctx* ctx, void** state, int32_t* pitch, int64_t* plane);
+
+/* Diagnostics of the current state; see lbm_diag.  r_in < 0 skips dp_laplace.  Synchronises.
+ * Returns LBM_ERR_NONFINITE (with *out filled) when any node is non-finite. */
+int lbm_diagnostics(lbm_ctx* ctx, double xc, double yc, double r_in, double r_out,
+                    lbm_diag* out);
+
+/* Tuning of the step launch: rows per warp segment (>= 1) and threads per block (a multiple of
+ * 32, 32..1024).  0 keeps the current value.  Results do not depend on these. */
+int lbm_set_launch(lbm_ctx* ctx, int32_t seg_rows, int32_t block_threads);
+int lbm_get_launch(lbm_ctx* ctx, int32_t* seg_rows, int32_t* block_threads);
+
+/* Time steps taken since the last initialisation. */
+int64_t lbm_steps_done(const lbm_ctx* ctx);
+
+/* Release the context and the device memory it owns; NULL is allowed. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Static message for a status code. */
+const char* lbm_strerror(int status);
+
+/* The last CUDA error code the context saw (cudaError_t as int), 0 if none. */
+int lbm_last_cuda_error(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CMLBM_H */

@@ -1,0 +1,524 @@
+// C ABI of the library (declared in include/cmlbm.h): parameter validation, per-case constants,
+// device buffers, launches and diagnostics.  All device work goes through the kernels of
+// lbm_step.cu and the reductions below; nothing here computes physics on the host.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/cmlbm.h"
+#include "lbm_device.cuh"
+
+namespace cmlbm {
+template <typename R, typename S>
+cudaError_t launch_step(const void*, void*, const Geometry&, const Consts<R>&, int, int,
+                        cudaStream_t);
+template <typename R, typename S>
+cudaError_t launch_init(const double*, const double*, const double*, const double*, void*,
+                        const Geometry&, const Consts<R>&, cudaStream_t);
+template <typename R, typename S>
+cudaError_t launch_fields(const void*, const Geometry&, const Consts<R>&, double*, double*,
+                          double*, double*, double*, cudaStream_t);
+template <typename S>
+cudaError_t launch_pack(const void*, double*, const Geometry&, cudaStream_t);
+template <typename S>
+cudaError_t launch_unpack(const double*, void*, const Geometry&, cudaStream_t);
+}  // namespace cmlbm
+
+using namespace cmlbm;
+
+struct lbm_ctx {
+    lbm_params P;
+    Geometry G;
+    Consts<double> Kd;
+    Consts<float> Kf;
+    size_t elem;           // bytes per stored population
+    size_t state_bytes;    // one buffer (18 planes)
+    char* buf;             // two buffers back to back
+    bool own;
+    int cur;               // buffer holding the current state
+    bool initialised;
+    long long steps;
+    int seg_h, block;
+    cudaStream_t st;
+    double* scratch;       // nodal fields for diagnostics / field extraction (5 N doubles)
+    double* partials;      // reduction partials
+    int nsm;
+    int last_cuda;
+};
+
+namespace {
+
+constexpr int kReduceSlots = 8;
+
+bool finite(double v) { return std::isfinite(v); }
+
+int validate(const lbm_params* P)
+{
+    if (!P) return LBM_ERR_ARG;
+    if (P->nx < 1 || P->ny < 1 || P->nx > 65536 || P->ny > 65536) return LBM_ERR_ARG;
+    if ((P->bc_x != LBM_PERIODIC && P->bc_x != LBM_WALL) ||
+        (P->bc_y != LBM_PERIODIC && P->bc_y != LBM_WALL))
+        return LBM_ERR_ARG;
+    if (P->precision != LBM_FP64 && P->precision != LBM_FP32) return LBM_ERR_UNSUPPORTED;
+    const double v[] = {P->rho_a, P->rho_b, P->mu_a, P->mu_b, P->sigma0, P->dsigma_dT, P->T0,
+                        P->gradT_x, P->gradT_y, P->mobility, P->width, P->gx, P->gy,
+                        P->rho_ref};
+    for (double d : v)
+        if (!finite(d)) return LBM_ERR_PARAM;
+    if (P->rho_a <= 0 || P->rho_b <= 0 || P->mu_a <= 0 || P->mu_b <= 0) return LBM_ERR_PARAM;
+    if (P->width <= 0 || P->mobility <= 0) return LBM_ERR_PARAM;
+    return LBM_OK;
+}
+
+int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
+
+size_t elem_of(int precision) { return precision == LBM_FP64 ? sizeof(double) : sizeof(float); }
+
+template <typename R>
+Consts<R> make_consts(const lbm_params& P)
+{
+    Consts<R> K;
+    K.rho_b = R(P.rho_b);
+    K.drho = R(P.rho_a - P.rho_b);
+    K.mu_b = R(P.mu_b);
+    K.dmu = R(P.mu_a - P.mu_b);
+    // kappa-tilde = 3/2 sigma W with sigma = sigma0 + dsigma_dT (gradT . x)
+    K.kt0 = R(1.5 * P.width * P.sigma0);
+    K.dktx = R(1.5 * P.width * P.dsigma_dT * P.gradT_x);
+    K.dkty = R(1.5 * P.width * P.dsigma_dT * P.gradT_y);
+    K.mob = R(P.mobility);
+    K.four_over_w = R(4.0 / P.width);
+    // M_phi = c^2 (1/omega - 1/2) -> omega = 1 / (3 M_phi + 1/2)
+    K.omega_phi_6 = R(1.0 / (3.0 * P.mobility + 0.5) / 6.0);
+    K.gx = R(P.gx);
+    K.gy = R(P.gy);
+    K.rho_ref = R(P.rho_ref);
+    K.cs2_drho = R((P.rho_a - P.rho_b) / 3.0);
+    return K;
+}
+
+int cuda_fail(lbm_ctx* c, cudaError_t e)
+{
+    if (c) c->last_cuda = (int)e;
+    if (e == cudaErrorMemoryAllocation) return LBM_ERR_NOMEM;
+    return LBM_ERR_CUDA;
+}
+
+void* cur_state(lbm_ctx* c) { return c->buf + (size_t)c->cur * c->state_bytes; }
+
+int default_seg_rows(const lbm_ctx* c)
+{
+    // about 24 resident warps per SM, a few waves of warps over the grid
+    const long long strips = (c->G.nx + 31) / 32;
+    const long long target = (long long)c->nsm * 24 * 2;
+    long long nseg = (target + strips - 1) / strips;
+    if (nseg < 1) nseg = 1;
+    long long h = (c->G.ny + nseg - 1) / nseg;
+    if (h < 4) h = 4;
+    if (h > c->G.ny) h = c->G.ny;
+    return (int)h;
+}
+
+int make_ctx(const lbm_params* params, void* ext, size_t ext_bytes, lbm_ctx** out)
+{
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    int s = validate(params);
+    if (s) return s;
+    cudaError_t e = cudaSetDevice(params->device);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ERR_NOMEM;
+    c->P = *params;
+    c->G.nx = params->nx;
+    c->G.ny = params->ny;
+    c->G.pitch = pitch_of(params->nx);
+    c->G.wall_x = params->bc_x == LBM_WALL;
+    c->G.wall_y = params->bc_y == LBM_WALL;
+    c->G.plane = (long long)c->G.pitch * c->G.ny;
+    c->Kd = make_consts<double>(*params);
+    c->Kf = make_consts<float>(*params);
+    c->elem = elem_of(params->precision);
+    c->state_bytes = (size_t)18 * (size_t)c->G.plane * c->elem;
+    c->st = static_cast<cudaStream_t>(params->stream);
+    int dev = params->device, nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    c->nsm = nsm > 0 ? nsm : 1;
+    c->block = 128;
+    c->seg_h = default_seg_rows(c);
+    if (ext) {
+        if (ext_bytes < 2 * c->state_bytes || (reinterpret_cast<uintptr_t>(ext) & 15)) {
+            delete c;
+            return LBM_ERR_ARG;
+        }
+        c->buf = static_cast<char*>(ext);
+        c->own = false;
+    } else {
+        e = cudaMalloc(&c->buf, 2 * c->state_bytes);
+        if (e != cudaSuccess) {
+            delete c;
+            return e == cudaErrorMemoryAllocation ? LBM_ERR_NOMEM : LBM_ERR_CUDA;
+        }
+        c->own = true;
+    }
+    // zero the padding columns once so that every byte of the state is defined
+    e = cudaMemsetAsync(c->buf, 0, 2 * c->state_bytes, c->st);
+    if (e != cudaSuccess) {
+        int r = cuda_fail(c, e);
+        if (c->own) cudaFree(c->buf);
+        delete c;
+        return r;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+int ensure_scratch(lbm_ctx* c)
+{
+    if (c->scratch) return LBM_OK;
+    const size_t N = (size_t)c->G.nx * c->G.ny;
+    cudaError_t e = cudaMalloc(&c->scratch, 5 * N * sizeof(double));
+    if (e != cudaSuccess) { c->scratch = nullptr; return cuda_fail(c, e); }
+    e = cudaMalloc(&c->partials, (size_t)(4 * c->nsm + 1) * kReduceSlots * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaFree(c->scratch);
+        c->scratch = nullptr;
+        c->partials = nullptr;
+        return cuda_fail(c, e);
+    }
+    return LBM_OK;
+}
+
+int run_fields(lbm_ctx* c, double* phi, double* p, double* ux, double* uy, double* rho)
+{
+    cudaError_t e;
+    if (c->P.precision == LBM_FP64)
+        e = launch_fields<double, double>(cur_state(c), c->G, c->Kd, phi, p, ux, uy, rho, c->st);
+    else
+        e = launch_fields<float, float>(cur_state(c), c->G, c->Kf, phi, p, ux, uy, rho, c->st);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(c, e);
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP64 reductions of the diagnostics (block partials, then one block in a fixed order)
+// ---------------------------------------------------------------------------------------------
+struct DiagArgs {
+    int nx, ny, wall_x, wall_y;
+    double xc, yc, r_in, r_out;
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// slots: 0 sum phi, 1 sum p, 2 max |u|, 3 sum p inside, 4 count inside, 5 sum p outside,
+// 6 count outside, 7 non-finite count
+__global__ void diag_partial_kernel(const double* __restrict__ phi, const double* __restrict__ p,
+                                    const double* __restrict__ ux, const double* __restrict__ uy,
+                                    DiagArgs A, double* __restrict__ part)
+{
+    double acc[kReduceSlots] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const long long N = (long long)A.nx * A.ny;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const double ph = phi[n], pp = p[n], u = ux[n], v = uy[n];
+        if (!(isfinite(ph) && isfinite(pp) && isfinite(u) && isfinite(v))) {
+            acc[7] += 1.0;
+            continue;
+        }
+        acc[0] += ph;
+        acc[1] += pp;
+        acc[2] = fmax(acc[2], sqrt(u * u + v * v));
+        if (A.r_in >= 0) {
+            const int y = (int)(n / A.nx), x = (int)(n % A.nx);
+            double dx = fabs(x - A.xc), dy = fabs(y - A.yc);
+            if (!A.wall_x) dx = fmin(dx, A.nx - dx);
+            if (!A.wall_y) dy = fmin(dy, A.ny - dy);
+            const double r = sqrt(dx * dx + dy * dy);
+            if (r < A.r_in) { acc[3] += pp; acc[4] += 1.0; }
+            if (r > A.r_out) { acc[5] += pp; acc[6] += 1.0; }
+        }
+    }
+    __shared__ double sh[32][kReduceSlots];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < kReduceSlots; ++k) {
+        const double r = (k == 2) ? warp_max(acc[k]) : warp_sum(acc[k]);
+        if (lane == 0) sh[wid][k] = r;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        for (int k = 0; k < kReduceSlots; ++k) {
+            double r = lane < nw ? sh[lane][k] : 0.0;
+            r = (k == 2) ? warp_max(r) : warp_sum(r);
+            if (lane == 0) part[(size_t)blockIdx.x * kReduceSlots + k] = r;
+        }
+    }
+}
+
+__global__ void diag_final_kernel(double* __restrict__ part, int nblocks)
+{
+    // one warp; lanes take slots, blocks summed in index order
+    const int k = threadIdx.x;
+    if (k >= kReduceSlots) return;
+    double r = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        const double v = part[(size_t)b * kReduceSlots + k];
+        r = (k == 2) ? fmax(r, v) : r + v;
+    }
+    part[(size_t)nblocks * kReduceSlots + k] = r;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------------------------
+extern "C" {
+
+int lbm_state_bytes(const lbm_params* params, size_t* bytes)
+{
+    if (!bytes) return LBM_ERR_ARG;
+    int s = validate(params);
+    if (s) return s;
+    *bytes = 2 * (size_t)18 * (size_t)pitch_of(params->nx) * (size_t)params->ny *
+             elem_of(params->precision);
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_params* params, lbm_ctx** out)
+{
+    return make_ctx(params, nullptr, 0, out);
+}
+
+int lbm_create_with_buffer(const lbm_params* params, void* device_buffer, size_t bytes,
+                           lbm_ctx** out)
+{
+    if (!device_buffer) {
+        if (out) *out = nullptr;
+        return LBM_ERR_ARG;
+    }
+    return make_ctx(params, device_buffer, bytes, out);
+}
+
+int lbm_init_fields_device(lbm_ctx* c, const double* phi, const double* p, const double* ux,
+                           const double* uy)
+{
+    if (!c || !phi || !p || !ux || !uy) return LBM_ERR_ARG;
+    cudaSetDevice(c->P.device);
+    c->cur = 0;
+    cudaError_t e;
+    if (c->P.precision == LBM_FP64)
+        e = launch_init<double, double>(phi, p, ux, uy, cur_state(c), c->G, c->Kd, c->st);
+    else
+        e = launch_init<float, float>(phi, p, ux, uy, cur_state(c), c->G, c->Kf, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    c->initialised = true;
+    c->steps = 0;
+    return LBM_OK;
+}
+
+int lbm_init_fields(lbm_ctx* c, const double* phi, const double* p, const double* ux,
+                    const double* uy)
+{
+    if (!c || !phi || !p || !ux || !uy) return LBM_ERR_ARG;
+    cudaSetDevice(c->P.device);
+    int s = ensure_scratch(c);
+    if (s) return s;
+    const size_t N = (size_t)c->G.nx * c->G.ny, B = N * sizeof(double);
+    const double* src[4] = {phi, p, ux, uy};
+    for (int k = 0; k < 4; ++k) {
+        cudaError_t e = cudaMemcpyAsync(c->scratch + k * N, src[k], B, cudaMemcpyHostToDevice,
+                                        c->st);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    s = lbm_init_fields_device(c, c->scratch, c->scratch + N, c->scratch + 2 * N,
+                               c->scratch + 3 * N);
+    if (s) return s;
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(c, e);
+}
+
+int lbm_step(lbm_ctx* c, int32_t nsteps)
+{
+    if (!c || nsteps < 0) return LBM_ERR_ARG;
+    if (!c->initialised) return LBM_ERR_STATE;
+    for (int32_t k = 0; k < nsteps; ++k) {
+        void* src = cur_state(c);
+        void* dst = c->buf + (size_t)(1 - c->cur) * c->state_bytes;
+        cudaError_t e;
+        if (c->P.precision == LBM_FP64)
+            e = launch_step<double, double>(src, dst, c->G, c->Kd, c->seg_h, c->block, c->st);
+        else
+            e = launch_step<float, float>(src, dst, c->G, c->Kf, c->seg_h, c->block, c->st);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        c->cur = 1 - c->cur;
+        ++c->steps;
+    }
+    return LBM_OK;
+}
+
+int lbm_get_fields(lbm_ctx* c, double* phi, double* p, double* ux, double* uy, double* rho)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (!c->initialised) return LBM_ERR_STATE;
+    cudaSetDevice(c->P.device);
+    int s = ensure_scratch(c);
+    if (s) return s;
+    const size_t N = (size_t)c->G.nx * c->G.ny, B = N * sizeof(double);
+    double* d[5];
+    for (int k = 0; k < 5; ++k) d[k] = c->scratch + k * N;
+    s = run_fields(c, d[0], d[1], d[2], d[3], d[4]);
+    if (s) return s;
+    double* h[5] = {phi, p, ux, uy, rho};
+    for (int k = 0; k < 5; ++k) {
+        if (!h[k]) continue;
+        cudaError_t e = cudaMemcpyAsync(h[k], d[k], B, cudaMemcpyDeviceToHost, c->st);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(c, e);
+}
+
+int lbm_get_populations(lbm_ctx* c, double* g, double* f)
+{
+    if (!c || !g || !f) return LBM_ERR_ARG;
+    if (!c->initialised) return LBM_ERR_STATE;
+    cudaSetDevice(c->P.device);
+    const size_t N = (size_t)c->G.nx * c->G.ny;
+    double* tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, 18 * N * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    e = (c->P.precision == LBM_FP64) ? launch_pack<double>(cur_state(c), tmp, c->G, c->st)
+                                     : launch_pack<float>(cur_state(c), tmp, c->G, c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g, tmp, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f, tmp + 9 * N, 9 * N * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    cudaFree(tmp);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(c, e);
+}
+
+int lbm_set_populations(lbm_ctx* c, const double* g, const double* f)
+{
+    if (!c || !g || !f) return LBM_ERR_ARG;
+    cudaSetDevice(c->P.device);
+    const size_t N = (size_t)c->G.nx * c->G.ny;
+    double* tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, 18 * N * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    e = cudaMemcpyAsync(tmp, g, 9 * N * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tmp + 9 * N, f, 9 * N * sizeof(double), cudaMemcpyHostToDevice,
+                            c->st);
+    c->cur = 0;
+    if (e == cudaSuccess)
+        e = (c->P.precision == LBM_FP64) ? launch_unpack<double>(tmp, cur_state(c), c->G, c->st)
+                                         : launch_unpack<float>(tmp, cur_state(c), c->G, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    c->initialised = true;
+    return LBM_OK;
+}
+
+int lbm_state_device(lbm_ctx* c, void** state, int32_t* pitch, int64_t* plane)
+{
+    if (!c || !state) return LBM_ERR_ARG;
+    if (!c->initialised) return LBM_ERR_STATE;
+    *state = cur_state(c);
+    if (pitch) *pitch = c->G.pitch;
+    if (plane) *plane = c->G.plane;
+    return LBM_OK;
+}
+
+int lbm_diagnostics(lbm_ctx* c, double xc, double yc, double r_in, double r_out, lbm_diag* out)
+{
+    if (!c || !out) return LBM_ERR_ARG;
+    if (!c->initialised) return LBM_ERR_STATE;
+    cudaSetDevice(c->P.device);
+    int s = ensure_scratch(c);
+    if (s) return s;
+    const size_t N = (size_t)c->G.nx * c->G.ny;
+    s = run_fields(c, c->scratch, c->scratch + N, c->scratch + 2 * N, c->scratch + 3 * N,
+                   c->scratch + 4 * N);
+    if (s) return s;
+    DiagArgs A{c->G.nx, c->G.ny, c->G.wall_x, c->G.wall_y, xc, yc, r_in, r_out};
+    const int nb = 4 * c->nsm;
+    diag_partial_kernel<<<nb, 256, 0, c->st>>>(c->scratch, c->scratch + N, c->scratch + 2 * N,
+                                               c->scratch + 3 * N, A, c->partials);
+    diag_final_kernel<<<1, 32, 0, c->st>>>(c->partials, nb);
+    double r[kReduceSlots];
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r, c->partials + (size_t)nb * kReduceSlots, sizeof(r),
+                            cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    out->sum_phi = r[0];
+    out->sum_p = r[1];
+    out->max_speed = r[2];
+    out->dp_laplace = (r[4] > 0 && r[6] > 0) ? r[3] / r[4] - r[5] / r[6] : 0.0;
+    out->nonfinite = (int64_t)r[7];
+    return out->nonfinite ? LBM_ERR_NONFINITE : LBM_OK;
+}
+
+int lbm_set_launch(lbm_ctx* c, int32_t seg_rows, int32_t block_threads)
+{
+    if (!c || seg_rows < 0 || block_threads < 0) return LBM_ERR_ARG;
+    if (block_threads && (block_threads % 32 || block_threads > 256)) return LBM_ERR_ARG;
+    if (seg_rows) c->seg_h = seg_rows;
+    if (block_threads) c->block = block_threads;
+    return LBM_OK;
+}
+
+int lbm_get_launch(lbm_ctx* c, int32_t* seg_rows, int32_t* block_threads)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (seg_rows) *seg_rows = c->seg_h;
+    if (block_threads) *block_threads = c->block;
+    return LBM_OK;
+}
+
+int64_t lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : -1; }
+
+void lbm_destroy(lbm_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->P.device);
+    cudaStreamSynchronize(c->st);
+    if (c->own) cudaFree(c->buf);
+    if (c->scratch) cudaFree(c->scratch);
+    if (c->partials) cudaFree(c->partials);
+    delete c;
+}
+
+const char* lbm_strerror(int s)
+{
+    switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_PARAM: return "invalid physical parameter";
+    case LBM_ERR_CUDA: return "CUDA runtime error";
+    case LBM_ERR_NOMEM: return "device allocation failed";
+    case LBM_ERR_STATE: return "state not initialised";
+    case LBM_ERR_NONFINITE: return "non-finite values in the fields";
+    case LBM_ERR_UNSUPPORTED: return "unsupported precision mode";
+    default: return "unknown status";
+    }
+}
+
+int lbm_last_cuda_error(const lbm_ctx* c) { return c ? c->last_cuda : 0; }
+
+}  // extern "C"

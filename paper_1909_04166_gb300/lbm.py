@@ -1,0 +1,294 @@
+"""Thin ctypes binding of the C ABI in ``include/cmlbm.h`` (argument marshalling only).
+
+Every function keeps the C name and returns what the C call returns through its out-arguments;
+a non-zero status raises ``LbmError``.  All computation runs in ``libcmlbm.so``; if the library
+is missing or cannot be loaded this module raises on first use - there is no fallback.
+
+Host arrays are numpy float64, nodal fields ``(ny, nx)``, populations ``(9, ny, nx)``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK = 0
+LBM_ERR_ARG = -1
+LBM_ERR_PARAM = -2
+LBM_ERR_CUDA = -3
+LBM_ERR_NOMEM = -4
+LBM_ERR_STATE = -5
+LBM_ERR_NONFINITE = -6
+LBM_ERR_UNSUPPORTED = -7
+
+LBM_FP64 = 0
+LBM_FP32 = 1
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32}
+
+LBM_PERIODIC = 0
+LBM_WALL = 1
+
+EXPORTS = [
+    "lbm_state_bytes", "lbm_create", "lbm_create_with_buffer", "lbm_init_fields",
+    "lbm_init_fields_device", "lbm_step", "lbm_get_fields", "lbm_get_populations",
+    "lbm_set_populations", "lbm_state_device", "lbm_diagnostics", "lbm_set_launch",
+    "lbm_get_launch", "lbm_steps_done", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error",
+]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {lbm_strerror(status)} ({status})")
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
+        ("rho_a", ctypes.c_double), ("rho_b", ctypes.c_double),
+        ("mu_a", ctypes.c_double), ("mu_b", ctypes.c_double),
+        ("sigma0", ctypes.c_double), ("dsigma_dT", ctypes.c_double),
+        ("T0", ctypes.c_double), ("gradT_x", ctypes.c_double), ("gradT_y", ctypes.c_double),
+        ("mobility", ctypes.c_double), ("width", ctypes.c_double),
+        ("gx", ctypes.c_double), ("gy", ctypes.c_double), ("rho_ref", ctypes.c_double),
+        ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class lbm_diag(ctypes.Structure):
+    _fields_ = [("sum_phi", ctypes.c_double), ("sum_p", ctypes.c_double),
+                ("max_speed", ctypes.c_double), ("dp_laplace", ctypes.c_double),
+                ("nonfinite", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libcmlbm.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: build it with "
+                           "paper_1909_04166_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, dp, i32, i64 = ctypes.c_void_p, P(ctypes.c_double), ctypes.c_int32, ctypes.c_int64
+    pp = P(lbm_params)
+    L.lbm_state_bytes.argtypes = [pp, P(ctypes.c_size_t)]
+    L.lbm_create.argtypes = [pp, P(vp)]
+    L.lbm_create_with_buffer.argtypes = [pp, vp, ctypes.c_size_t, P(vp)]
+    L.lbm_init_fields.argtypes = [vp, dp, dp, dp, dp]
+    L.lbm_init_fields_device.argtypes = [vp, vp, vp, vp, vp]
+    L.lbm_step.argtypes = [vp, i32]
+    L.lbm_get_fields.argtypes = [vp, dp, dp, dp, dp, dp]
+    L.lbm_get_populations.argtypes = [vp, dp, dp]
+    L.lbm_set_populations.argtypes = [vp, dp, dp]
+    L.lbm_state_device.argtypes = [vp, P(vp), P(i32), P(i64)]
+    L.lbm_diagnostics.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, P(lbm_diag)]
+    L.lbm_set_launch.argtypes = [vp, i32, i32]
+    L.lbm_get_launch.argtypes = [vp, P(i32), P(i32)]
+    L.lbm_steps_done.argtypes = [vp]
+    L.lbm_steps_done.restype = i64
+    L.lbm_destroy.argtypes = [vp]
+    L.lbm_destroy.restype = None
+    L.lbm_strerror.argtypes = [ctypes.c_int]
+    L.lbm_strerror.restype = ctypes.c_char_p
+    L.lbm_last_cuda_error.argtypes = [vp]
+    _lib = L
+    return L
+
+
+def _check(status: int, what: str) -> None:
+    if status != LBM_OK:
+        raise LbmError(status, what)
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_params(case: dict, precision="fp32", device=0, stream=0) -> lbm_params:
+    """lbm_params from a case dictionary (keys of ``workloads.Case``)."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return lbm_params(
+        int(case["nx"]), int(case["ny"]),
+        LBM_WALL if case.get("wall_x") else LBM_PERIODIC,
+        LBM_WALL if case.get("wall_y") else LBM_PERIODIC,
+        float(case["rho_a"]), float(case["rho_b"]), float(case["mu_a"]), float(case["mu_b"]),
+        float(case.get("sigma0", 0.0)), float(case.get("dsigma_dT", 0.0)),
+        float(case.get("T0", 0.0)), float(case.get("gradT_x", 0.0)),
+        float(case.get("gradT_y", 0.0)), float(case["mobility"]), float(case["width"]),
+        float(case.get("gx", 0.0)), float(case.get("gy", 0.0)), float(case.get("rho_ref", 0.0)),
+        prec, int(device), ctypes.c_void_p(int(stream)))
+
+
+# ---- ABI wrappers (same names as the C entry points) ------------------------------------------
+
+def lbm_strerror(status: int) -> str:
+    return lib().lbm_strerror(int(status)).decode()
+
+
+def lbm_state_bytes(params: lbm_params) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().lbm_state_bytes(ctypes.byref(params), ctypes.byref(n)), "lbm_state_bytes")
+    return int(n.value)
+
+
+def lbm_create(params: lbm_params) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(lib().lbm_create(ctypes.byref(params), ctypes.byref(ctx)), "lbm_create")
+    return ctx
+
+
+def lbm_create_with_buffer(params: lbm_params, device_ptr: int, nbytes: int):
+    ctx = ctypes.c_void_p()
+    _check(lib().lbm_create_with_buffer(ctypes.byref(params), ctypes.c_void_p(int(device_ptr)),
+                                        ctypes.c_size_t(int(nbytes)), ctypes.byref(ctx)),
+           "lbm_create_with_buffer")
+    return ctx
+
+
+def lbm_init_fields(ctx, phi, p, ux, uy) -> None:
+    _check(lib().lbm_init_fields(ctx, _dptr(phi), _dptr(p), _dptr(ux), _dptr(uy)),
+           "lbm_init_fields")
+
+
+def lbm_init_fields_device(ctx, phi_ptr: int, p_ptr: int, ux_ptr: int, uy_ptr: int) -> None:
+    v = ctypes.c_void_p
+    _check(lib().lbm_init_fields_device(ctx, v(phi_ptr), v(p_ptr), v(ux_ptr), v(uy_ptr)),
+           "lbm_init_fields_device")
+
+
+def lbm_step(ctx, nsteps: int) -> None:
+    _check(lib().lbm_step(ctx, int(nsteps)), "lbm_step")
+
+
+def lbm_get_fields(ctx, phi=None, p=None, ux=None, uy=None, rho=None) -> None:
+    _check(lib().lbm_get_fields(ctx, _dptr(phi), _dptr(p), _dptr(ux), _dptr(uy), _dptr(rho)),
+           "lbm_get_fields")
+
+
+def lbm_get_populations(ctx, g, f) -> None:
+    _check(lib().lbm_get_populations(ctx, _dptr(g), _dptr(f)), "lbm_get_populations")
+
+
+def lbm_set_populations(ctx, g, f) -> None:
+    _check(lib().lbm_set_populations(ctx, _dptr(g), _dptr(f)), "lbm_set_populations")
+
+
+def lbm_state_device(ctx):
+    ptr, pitch, plane = ctypes.c_void_p(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().lbm_state_device(ctx, ctypes.byref(ptr), ctypes.byref(pitch),
+                                  ctypes.byref(plane)), "lbm_state_device")
+    return int(ptr.value or 0), int(pitch.value), int(plane.value)
+
+
+def lbm_diagnostics(ctx, xc=0.0, yc=0.0, r_in=-1.0, r_out=0.0, allow_nonfinite=True) -> dict:
+    d = lbm_diag()
+    s = lib().lbm_diagnostics(ctx, float(xc), float(yc), float(r_in), float(r_out),
+                              ctypes.byref(d))
+    if s != LBM_OK and not (allow_nonfinite and s == LBM_ERR_NONFINITE):
+        _check(s, "lbm_diagnostics")
+    return {k: getattr(d, k) for k, _ in lbm_diag._fields_}
+
+
+def lbm_set_launch(ctx, seg_rows: int = 0, block_threads: int = 0) -> None:
+    _check(lib().lbm_set_launch(ctx, int(seg_rows), int(block_threads)), "lbm_set_launch")
+
+
+def lbm_get_launch(ctx):
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().lbm_get_launch(ctx, ctypes.byref(a), ctypes.byref(b)), "lbm_get_launch")
+    return int(a.value), int(b.value)
+
+
+def lbm_steps_done(ctx) -> int:
+    return int(lib().lbm_steps_done(ctx))
+
+
+def lbm_destroy(ctx) -> None:
+    if ctx is not None and ctx.value:
+        lib().lbm_destroy(ctx)
+        ctx.value = None
+
+
+def lbm_last_cuda_error(ctx) -> int:
+    return int(lib().lbm_last_cuda_error(ctx))
+
+
+# ---- convenience ------------------------------------------------------------------------------
+
+class Simulation:
+    """Owns one context; a case dictionary from ``workloads`` gives its parameters."""
+
+    def __init__(self, case: dict, precision="fp32", device=0, stream=0):
+        self.case = case
+        self.nx, self.ny = int(case["nx"]), int(case["ny"])
+        self.params = make_params(case, precision, device, stream)
+        self.ctx = lbm_create(self.params)
+
+    def init(self, phi, p, ux, uy):
+        shape = (self.ny, self.nx)
+        arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), shape))
+                for a in (phi, p, ux, uy)]
+        lbm_init_fields(self.ctx, *arrs)
+        return self
+
+    def init_case(self):
+        f = self.case["fields"]
+        return self.init(f["phi"], f["p"], f["ux"], f["uy"])
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+        return self
+
+    def fields(self) -> dict:
+        shape = (self.ny, self.nx)
+        out = {k: np.empty(shape) for k in ("phi", "p", "ux", "uy", "rho")}
+        lbm_get_fields(self.ctx, out["phi"], out["p"], out["ux"], out["uy"], out["rho"])
+        return out
+
+    def populations(self):
+        g = np.empty((9, self.ny, self.nx))
+        f = np.empty((9, self.ny, self.nx))
+        lbm_get_populations(self.ctx, g, f)
+        return g, f
+
+    def set_populations(self, g, f):
+        lbm_set_populations(self.ctx, np.ascontiguousarray(g, np.float64),
+                            np.ascontiguousarray(f, np.float64))
+        return self
+
+    def diagnostics(self, xc=0.0, yc=0.0, r_in=-1.0, r_out=0.0) -> dict:
+        return lbm_diagnostics(self.ctx, xc, yc, r_in, r_out)
+
+    def close(self):
+        lbm_destroy(self.ctx)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
