@@ -164,21 +164,20 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     K = args.steps
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
-        ev[0].record(stream)
-        for k in range(K):
-            lbm.lbm_step(ctx, 1)
-            ev[k + 1].record(stream)
+        ev0.record(stream)
+        lbm.lbm_step(ctx, K)         # K fused-kernel launches (graph replays of 32 steps)
+        ev1.record(stream)
         torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
-    ms_total = ev[0].elapsed_time(ev[K])
-    per_launch = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
-    ms_launch = float(np.mean(per_launch))
+    ms_total = ev0.elapsed_time(ev1)
+    ms_launch = ms_total / K         # every launch in the region is the step kernel
     t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
     if ws > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

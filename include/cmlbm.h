@@ -60,6 +60,9 @@ extern "C" {
 #define LBM_ERR_STATE (-5)      /* the state was never initialised */
 #define LBM_ERR_NONFINITE (-6)  /* a diagnostic found NaN or Inf in the fields */
 #define LBM_ERR_UNSUPPORTED (-7)/* precision mode not built into this library */
+#define LBM_ERR_TIMEOUT (-8)    /* a bounded wait inside the step kernel gave up; the state of
+                                   that step is invalid (reported by the next synchronising
+                                   call or lbm_check) */
 
 /* Storage / compute precision of a context. */
 typedef enum {
@@ -126,8 +129,12 @@ int lbm_init_fields_device(lbm_ctx* ctx, const double* phi, const double* p, con
                            const double* uy);
 
 /* Advance nsteps (>= 0) time steps: one fused kernel launch per step on params.stream,
- * asynchronous; launch errors are returned. */
+ * asynchronous; launch errors are returned.  Runs of 32 steps are issued as replays of a CUDA
+ * graph of 32 launches (built on first use; see lbm_set_graphs). */
 int lbm_step(lbm_ctx* ctx, int32_t nsteps);
+
+/* Enable (default) or disable the graph replays of lbm_step; results are identical. */
+int lbm_set_graphs(lbm_ctx* ctx, int32_t enable);
 
 /* Fields of the current state into host arrays ([ny][nx] doubles): phi, the corrected p, u and
  * rho as defined by Sec. 4 Eq. hydrodynamicfields.  Any pointer may be NULL.  Synchronises. */
@@ -138,9 +145,15 @@ int lbm_get_fields(lbm_ctx* ctx, double* phi, double* p, double* ux, double* uy,
 int lbm_get_populations(lbm_ctx* ctx, double* g, double* f);
 int lbm_set_populations(lbm_ctx* ctx, const double* g, const double* f);
 
-/* Device pointer of the current state (18 planes of ny rows of `pitch` elements, element type
- * double for LBM_FP64, float for LBM_FP32); valid until the next lbm_step. */
-int lbm_state_device(lbm_ctx* ctx, void** state, int32_t* pitch, int64_t* plane);
+/* Device pointer of the current state, valid until the next lbm_step.  Element type double for
+ * LBM_FP64, float for LBM_FP32.  Layout: tiles of 32 columns; population a (0..8 fluid g-bar,
+ * 9..17 interface f) of node (x, y) is element ((y * nstrips + x / 32) * 18 + a) * 32 + x % 32,
+ * nstrips = ceil(nx / 32).  *elements receives the element count of one state buffer. */
+int lbm_state_device(lbm_ctx* ctx, void** state, int32_t* nstrips, int64_t* elements);
+
+/* Synchronise the stream and report LBM_ERR_TIMEOUT if any step since creation gave up on a
+ * bounded device wait; LBM_OK otherwise. */
+int lbm_check(lbm_ctx* ctx);
 
 /* Diagnostics of the current state; see lbm_diag.  r_in < 0 skips dp_laplace.  Synchronises.
  * Returns LBM_ERR_NONFINITE (with *out filled) when any node is non-finite. */
@@ -148,7 +161,7 @@ int lbm_diagnostics(lbm_ctx* ctx, double xc, double yc, double r_in, double r_ou
                     lbm_diag* out);
 
 /* Tuning of the step launch: rows per warp segment (>= 1) and threads per block (a multiple of
- * 32, 32..1024).  0 keeps the current value.  Results do not depend on these. */
+ * 32, 32..256).  0 keeps the current value.  Results do not depend on these. */
 int lbm_set_launch(lbm_ctx* ctx, int32_t seg_rows, int32_t block_threads);
 int lbm_get_launch(lbm_ctx* ctx, int32_t* seg_rows, int32_t* block_threads);
 

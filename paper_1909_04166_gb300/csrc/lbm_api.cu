@@ -13,8 +13,15 @@
 
 namespace cmlbm {
 template <typename R, typename S>
-cudaError_t launch_step(const void*, void*, const Geometry&, const Consts<R>&, int, int,
+cudaError_t launch_step(const void*, void*, const Geometry&, const Consts<R>&, int, int, int*,
                         cudaStream_t);
+template <typename R, typename S>
+cudaError_t configure_step(int block);
+template <typename R, typename S>
+int step_blocks_per_sm(int block);
+template <typename R, typename S>
+cudaError_t build_step_graph(const void*, const void*, const Geometry&, const Consts<R>&, int,
+                             int, int*, int, cudaGraphExec_t*);
 template <typename R, typename S>
 cudaError_t launch_init(const double*, const double*, const double*, const double*, void*,
                         const Geometry&, const Consts<R>&, cudaStream_t);
@@ -35,7 +42,7 @@ struct lbm_ctx {
     Consts<double> Kd;
     Consts<float> Kf;
     size_t elem;           // bytes per stored population
-    size_t state_bytes;    // one buffer (18 planes)
+    size_t state_bytes;    // one buffer (18 populations per node, tiles of 32 columns)
     char* buf;             // two buffers back to back
     bool own;
     int cur;               // buffer holding the current state
@@ -45,6 +52,9 @@ struct lbm_ctx {
     cudaStream_t st;
     double* scratch;       // nodal fields for diagnostics / field extraction (5 N doubles)
     double* partials;      // reduction partials
+    int* err;              // device error word of the step kernel (bounded waits)
+    cudaGraphExec_t graph[2];   // kGraphChunk steps starting from buffer 0 / buffer 1
+    int use_graph;
     int nsm;
     int last_cuda;
 };
@@ -52,6 +62,7 @@ struct lbm_ctx {
 namespace {
 
 constexpr int kReduceSlots = 8;
+constexpr int kGraphChunk = 32;   // steps per replayed graph (even: the buffer parity returns)
 
 bool finite(double v) { return std::isfinite(v); }
 
@@ -73,7 +84,9 @@ int validate(const lbm_params* P)
     return LBM_OK;
 }
 
-int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
+int strips_of(int nx) { return (nx + 31) / 32; }
+
+size_t buffer_elems(int nx, int ny) { return (size_t)ny * strips_of(nx) * 18 * 32; }
 
 size_t elem_of(int precision) { return precision == LBM_FP64 ? sizeof(double) : sizeof(float); }
 
@@ -109,17 +122,65 @@ int cuda_fail(lbm_ctx* c, cudaError_t e)
 
 void* cur_state(lbm_ctx* c) { return c->buf + (size_t)c->cur * c->state_bytes; }
 
+// Rows per warp segment so that the warps of one launch fill the resident slots of every SM
+// about once (one wave): warps = strips * ceil(ny / rows).
 int default_seg_rows(const lbm_ctx* c)
 {
-    // about 24 resident warps per SM, a few waves of warps over the grid
-    const long long strips = (c->G.nx + 31) / 32;
-    const long long target = (long long)c->nsm * 24 * 2;
-    long long nseg = (target + strips - 1) / strips;
+    const int bps = c->P.precision == LBM_FP64 ? step_blocks_per_sm<double, double>(c->block)
+                                               : step_blocks_per_sm<float, float>(c->block);
+    const long long resident = (long long)c->nsm * bps * (c->block / 32);
+    const long long strips = c->G.nstrips;
+    long long nseg = resident / strips;
     if (nseg < 1) nseg = 1;
     long long h = (c->G.ny + nseg - 1) / nseg;
-    if (h < 4) h = 4;
+    if (h < 1) h = 1;
     if (h > c->G.ny) h = c->G.ny;
     return (int)h;
+}
+
+cudaError_t configure(lbm_ctx* c)
+{
+    return c->P.precision == LBM_FP64 ? configure_step<double, double>(c->block)
+                                      : configure_step<float, float>(c->block);
+}
+
+void drop_graphs(lbm_ctx* c)
+{
+    for (int k = 0; k < 2; ++k)
+        if (c->graph[k]) {
+            cudaGraphExecDestroy(c->graph[k]);
+            c->graph[k] = nullptr;
+        }
+}
+
+cudaError_t launch_one(lbm_ctx* c, const void* src, void* dst)
+{
+    if (c->P.precision == LBM_FP64)
+        return launch_step<double, double>(src, dst, c->G, c->Kd, c->seg_h, c->block, c->err,
+                                           c->st);
+    return launch_step<float, float>(src, dst, c->G, c->Kf, c->seg_h, c->block, c->err, c->st);
+}
+
+cudaError_t ensure_graph(lbm_ctx* c, int start)
+{
+    if (c->graph[start]) return cudaSuccess;
+    const void* a = c->buf + (size_t)start * c->state_bytes;
+    const void* b = c->buf + (size_t)(1 - start) * c->state_bytes;
+    if (c->P.precision == LBM_FP64)
+        return build_step_graph<double, double>(a, b, c->G, c->Kd, c->seg_h, c->block, c->err,
+                                                kGraphChunk, &c->graph[start]);
+    return build_step_graph<float, float>(a, b, c->G, c->Kf, c->seg_h, c->block, c->err,
+                                          kGraphChunk, &c->graph[start]);
+}
+
+// Read the step kernel's error word (synchronises the stream).
+int check_device_error(lbm_ctx* c)
+{
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return h ? LBM_ERR_TIMEOUT : LBM_OK;
 }
 
 int make_ctx(const lbm_params* params, void* ext, size_t ext_bytes, lbm_ctx** out)
@@ -135,20 +196,19 @@ int make_ctx(const lbm_params* params, void* ext, size_t ext_bytes, lbm_ctx** ou
     c->P = *params;
     c->G.nx = params->nx;
     c->G.ny = params->ny;
-    c->G.pitch = pitch_of(params->nx);
+    c->G.nstrips = strips_of(params->nx);
     c->G.wall_x = params->bc_x == LBM_WALL;
     c->G.wall_y = params->bc_y == LBM_WALL;
-    c->G.plane = (long long)c->G.pitch * c->G.ny;
     c->Kd = make_consts<double>(*params);
     c->Kf = make_consts<float>(*params);
     c->elem = elem_of(params->precision);
-    c->state_bytes = (size_t)18 * (size_t)c->G.plane * c->elem;
+    c->state_bytes = buffer_elems(params->nx, params->ny) * c->elem;
     c->st = static_cast<cudaStream_t>(params->stream);
     int dev = params->device, nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     c->nsm = nsm > 0 ? nsm : 1;
     c->block = 128;
-    c->seg_h = default_seg_rows(c);
+    c->use_graph = 1;
     if (ext) {
         if (ext_bytes < 2 * c->state_bytes || (reinterpret_cast<uintptr_t>(ext) & 15)) {
             delete c;
@@ -166,9 +226,14 @@ int make_ctx(const lbm_params* params, void* ext, size_t ext_bytes, lbm_ctx** ou
     }
     // zero the padding columns once so that every byte of the state is defined
     e = cudaMemsetAsync(c->buf, 0, 2 * c->state_bytes, c->st);
+    if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->st);
+    if (e == cudaSuccess) e = configure(c);
+    if (e == cudaSuccess) c->seg_h = default_seg_rows(c);
     if (e != cudaSuccess) {
         int r = cuda_fail(c, e);
         if (c->own) cudaFree(c->buf);
+        if (c->err) cudaFree(c->err);
         delete c;
         return r;
     }
@@ -290,8 +355,7 @@ int lbm_state_bytes(const lbm_params* params, size_t* bytes)
     if (!bytes) return LBM_ERR_ARG;
     int s = validate(params);
     if (s) return s;
-    *bytes = 2 * (size_t)18 * (size_t)pitch_of(params->nx) * (size_t)params->ny *
-             elem_of(params->precision);
+    *bytes = 2 * buffer_elems(params->nx, params->ny) * elem_of(params->precision);
     return LBM_OK;
 }
 
@@ -352,18 +416,30 @@ int lbm_step(lbm_ctx* c, int32_t nsteps)
 {
     if (!c || nsteps < 0) return LBM_ERR_ARG;
     if (!c->initialised) return LBM_ERR_STATE;
-    for (int32_t k = 0; k < nsteps; ++k) {
+    int32_t k = 0;
+    // whole chunks as replays of a prebuilt graph of kGraphChunk launches
+    while (c->use_graph && nsteps - k >= kGraphChunk) {
+        cudaError_t e = ensure_graph(c, c->cur);
+        if (e == cudaSuccess) e = cudaGraphLaunch(c->graph[c->cur], c->st);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        k += kGraphChunk;
+        c->steps += kGraphChunk;   // even chunk: the current buffer is unchanged
+    }
+    for (; k < nsteps; ++k) {
         void* src = cur_state(c);
         void* dst = c->buf + (size_t)(1 - c->cur) * c->state_bytes;
-        cudaError_t e;
-        if (c->P.precision == LBM_FP64)
-            e = launch_step<double, double>(src, dst, c->G, c->Kd, c->seg_h, c->block, c->st);
-        else
-            e = launch_step<float, float>(src, dst, c->G, c->Kf, c->seg_h, c->block, c->st);
+        cudaError_t e = launch_one(c, src, dst);
         if (e != cudaSuccess) return cuda_fail(c, e);
         c->cur = 1 - c->cur;
         ++c->steps;
     }
+    return LBM_OK;
+}
+
+int lbm_set_graphs(lbm_ctx* c, int32_t enable)
+{
+    if (!c) return LBM_ERR_ARG;
+    c->use_graph = enable ? 1 : 0;
     return LBM_OK;
 }
 
@@ -386,7 +462,8 @@ int lbm_get_fields(lbm_ctx* c, double* phi, double* p, double* ux, double* uy, d
         if (e != cudaSuccess) return cuda_fail(c, e);
     }
     cudaError_t e = cudaStreamSynchronize(c->st);
-    return e == cudaSuccess ? LBM_OK : cuda_fail(c, e);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return check_device_error(c);
 }
 
 int lbm_get_populations(lbm_ctx* c, double* g, double* f)
@@ -407,7 +484,8 @@ int lbm_get_populations(lbm_ctx* c, double* g, double* f)
                             c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     cudaFree(tmp);
-    return e == cudaSuccess ? LBM_OK : cuda_fail(c, e);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return check_device_error(c);
 }
 
 int lbm_set_populations(lbm_ctx* c, const double* g, const double* f)
@@ -433,14 +511,21 @@ int lbm_set_populations(lbm_ctx* c, const double* g, const double* f)
     return LBM_OK;
 }
 
-int lbm_state_device(lbm_ctx* c, void** state, int32_t* pitch, int64_t* plane)
+int lbm_state_device(lbm_ctx* c, void** state, int32_t* nstrips, int64_t* elements)
 {
     if (!c || !state) return LBM_ERR_ARG;
     if (!c->initialised) return LBM_ERR_STATE;
     *state = cur_state(c);
-    if (pitch) *pitch = c->G.pitch;
-    if (plane) *plane = c->G.plane;
+    if (nstrips) *nstrips = c->G.nstrips;
+    if (elements) *elements = (int64_t)buffer_elems(c->G.nx, c->G.ny);
     return LBM_OK;
+}
+
+int lbm_check(lbm_ctx* c)
+{
+    if (!c) return LBM_ERR_ARG;
+    cudaSetDevice(c->P.device);
+    return check_device_error(c);
 }
 
 int lbm_diagnostics(lbm_ctx* c, double xc, double yc, double r_in, double r_out, lbm_diag* out)
@@ -471,6 +556,8 @@ int lbm_diagnostics(lbm_ctx* c, double xc, double yc, double r_in, double r_out,
     out->max_speed = r[2];
     out->dp_laplace = (r[4] > 0 && r[6] > 0) ? r[3] / r[4] - r[5] / r[6] : 0.0;
     out->nonfinite = (int64_t)r[7];
+    int s2 = check_device_error(c);
+    if (s2) return s2;
     return out->nonfinite ? LBM_ERR_NONFINITE : LBM_OK;
 }
 
@@ -478,8 +565,14 @@ int lbm_set_launch(lbm_ctx* c, int32_t seg_rows, int32_t block_threads)
 {
     if (!c || seg_rows < 0 || block_threads < 0) return LBM_ERR_ARG;
     if (block_threads && (block_threads % 32 || block_threads > 256)) return LBM_ERR_ARG;
+    drop_graphs(c);
     if (seg_rows) c->seg_h = seg_rows;
-    if (block_threads) c->block = block_threads;
+    if (block_threads) {
+        c->block = block_threads;
+        cudaSetDevice(c->P.device);
+        cudaError_t e = configure(c);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
     return LBM_OK;
 }
 
@@ -501,6 +594,8 @@ void lbm_destroy(lbm_ctx* c)
     if (c->own) cudaFree(c->buf);
     if (c->scratch) cudaFree(c->scratch);
     if (c->partials) cudaFree(c->partials);
+    if (c->err) cudaFree(c->err);
+    drop_graphs(c);
     delete c;
 }
 
@@ -515,6 +610,7 @@ const char* lbm_strerror(int s)
     case LBM_ERR_STATE: return "state not initialised";
     case LBM_ERR_NONFINITE: return "non-finite values in the fields";
     case LBM_ERR_UNSUPPORTED: return "unsupported precision mode";
+    case LBM_ERR_TIMEOUT: return "a bounded device wait timed out (state invalid)";
     default: return "unknown status";
     }
 }

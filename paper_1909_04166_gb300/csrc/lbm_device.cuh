@@ -4,9 +4,10 @@
 //
 // Conventions (shared with the C ABI in include/cmlbm.h):
 //   D2Q9 ordering of Sec. 4 Eq. particlevelocities: e_x = (0,1,0,-1,0,1,-1,-1,1),
-//   e_y = (0,0,1,0,-1,1,1,-1,-1).  A state is 18 planes (9 fluid g-bar, then 9 interface f) of
-//   ny rows of `pitch` elements; node (x, y) of plane a sits at a*plane + y*pitch + x.  The state
-//   holds the streamed (pre-collision) populations of the current time level.
+//   e_y = (0,0,1,0,-1,1,1,-1,-1).  A state holds 18 populations per node (9 fluid g-bar, then 9
+//   interface f) in tiles of 32 columns: element (a, x, y) sits at
+//   ((y * nstrips + x / 32) * 18 + a) * 32 + x % 32.  The state holds the streamed
+//   (pre-collision) populations of the current time level.
 //   c_s^2 = c_sphi^2 = 1/3 (Sec. 5).
 #pragma once
 
@@ -31,19 +32,10 @@ struct Consts {
 };
 
 struct Geometry {
-    int nx, ny, pitch;
+    int nx, ny;
+    int nstrips;         // ceil(nx / 32): tiles of 32 columns per row
     int wall_x, wall_y;
-    long long plane;     // elements per plane = ny * pitch
 };
-
-// ---------------------------------------------------------------------------------------------
-// Storage element types.  FP32 and FP64 states store populations directly.
-// ---------------------------------------------------------------------------------------------
-template <typename S, typename R>
-__device__ __forceinline__ R load_pop(const S* p) { return static_cast<R>(__ldg(p)); }
-
-template <typename S, typename R>
-__device__ __forceinline__ void store_pop(S* p, R v) { *p = static_cast<S>(v); }
 
 // ---------------------------------------------------------------------------------------------
 // Nine-point stencil window of a nodal field: value at (x + i, y + j), i, j in {-1, 0, 1}.
@@ -82,6 +74,7 @@ __device__ __forceinline__ void lap_hess(const Win<R>& a, R& lap, R& hxx, R& hyy
 }
 
 template <typename R> __device__ __forceinline__ R rcp_(R v) { return R(1) / v; }
+template <> __device__ __forceinline__ float rcp_<float>(float v) { return __fdividef(1.0f, v); }
 template <typename R> __device__ __forceinline__ R rsqrt_(R v) { return R(1) / sqrt(v); }
 template <> __device__ __forceinline__ float rsqrt_<float>(float v) { return rsqrtf(v); }
 
@@ -113,20 +106,19 @@ __device__ __forceinline__ void node_macro(const Win<R>& ph, const Win<R>& ps, R
     lap_hess(ph, lap, hxx, hyy, hxy);
     grad_iso(ps, dpx, dpy);
 
+    // where |grad phi|^2 <= 1e-24 the normal and the surface force are zero (branch-free)
     const R g2 = dphx * dphx + dphy * dphy;
-    R Fsx = R(0), Fsy = R(0), nx = R(0), ny = R(0);
-    if (g2 > R(1e-24)) {
-        const R ig = rsqrt_(g2);
-        const R gm = g2 * ig;
-        nx = dphx * ig;
-        ny = dphy * ig;
-        const R nHn = nx * nx * hxx + R(2) * nx * ny * hxy + ny * ny * hyy;
-        const R kt = K.kt0 + K.dktx * xf + K.dkty * yf;
-        const R cap = -kt * gm * (lap - nHn);          // -kappa-tilde |grad phi|^2 div n
-        const R nd = nx * K.dktx + ny * K.dkty;         // n . grad kappa-tilde
-        Fsx = cap * nx + g2 * (K.dktx - nx * nd);       // + |grad phi|^2 (I - n n) grad kappa-tilde
-        Fsy = cap * ny + g2 * (K.dkty - ny * nd);
-    }
+    const bool has_n = g2 > R(1e-24);
+    const R ig = has_n ? rsqrt_(g2) : R(0);
+    const R g2m = has_n ? g2 : R(0);
+    const R gm = g2m * ig;
+    const R nx = dphx * ig, ny = dphy * ig;
+    const R nHn = nx * nx * hxx + R(2) * nx * ny * hxy + ny * ny * hyy;
+    const R kt = K.kt0 + K.dktx * xf + K.dkty * yf;
+    const R cap = -kt * gm * (lap - nHn);          // -kappa-tilde |grad phi|^2 div n
+    const R nd = nx * K.dktx + ny * K.dkty;         // n . grad kappa-tilde
+    const R Fsx = cap * nx + g2m * (K.dktx - nx * nd);   // + |grad phi|^2 (I - n n) grad kappa-tilde
+    const R Fsy = cap * ny + g2m * (K.dkty - ny * nd);
     const R dr = m.rho - K.rho_ref;
     m.Ftx = Fsx + dr * K.gx;
     m.Fty = Fsy + dr * K.gy;
@@ -229,14 +221,14 @@ __device__ __forceinline__ void collide_fluid(R g[9], const Macro<R>& m)
 }
 
 // Interface-lattice collision (Sec. 5): g-hat_1..8 with the sharpening flux M_phi theta n in the
-// first-order equilibria; omega^phi_{1,2} from M_phi, all other rates 1.
+// first-order equilibria; omega^phi_{1,2} from M_phi, all other rates 1.  phi = sum f (the
+// node's zeroth moment, already formed for the stencil window).
 template <typename R>
-__device__ __forceinline__ void collide_ace(R f[9], const Macro<R>& m, R omega_phi_6)
+__device__ __forceinline__ void collide_ace(R f[9], R phi, const Macro<R>& m, R omega_phi_6)
 {
     const R third = R(1) / R(3);
     const R ux = m.ux, uy = m.uy;
     const R ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
-    const R phi = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     const R d = (f[5] + f[6]) + (f[7] + f[8]);
     const R k10 = (f[1] - f[3]) + (f[5] - f[6]) - (f[7] - f[8]);
     const R k01 = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);

@@ -1,30 +1,105 @@
 // Fused time-step kernel, equilibrium initialisation and field extraction for the coupled
 // cascaded central-moment LB schemes of arXiv:1909.04166 on sm_103a.
 //
-// Step kernel design (one launch = one time step of both lattices over the whole grid):
-//   * Each warp owns a strip of 32 columns and a segment of rows, and marches along the rows.
-//     A lane owns one column: it loads the 18 streamed populations of its node with coalesced
-//     loads (SoA planes), forms phi = sum f and p* = sum g-bar, and keeps a rolling 3x3 window of
-//     (phi, p*) in registers; the east/west neighbours come from warp shuffles and the two halo
-//     columns of the strip from one distributed load + half-warp reduction per row.  No shared
-//     memory and no block-level synchronisation.
-//   * Row y is updated once phi and p* of row y+1 are known: stencils, forces, corrected p and
-//     u, fluid and interface collisions in registers, then the 18 post-collision populations
-//     are pushed to the neighbours in the other buffer (x + e_a), with half-way bounce-back at
-//     walls.  The state therefore always holds streamed (pre-collision) populations.
-//   * Segments alternate their marching direction so that the two warps sharing a segment
-//     boundary read its halo rows at about the same time (halo re-reads hit L2).
+// State layout ("tiled SoA"): for every row y and every strip of 32 columns, the 18 planes
+// (9 fluid g-bar, then 9 interface f) of those 32 nodes are contiguous: element (a, x, y) sits
+// at ((y * nstrips + x / 32) * 18 + a) * 32 + x % 32.  One warp-row tile is 18 * 32 elements
+// (2304 bytes in FP32), a single contiguous block.
+//
+// Step kernel (one launch = one time step of both lattices over the whole grid):
+//   * Each warp owns one strip of 32 columns and one segment of rows and marches along the rows
+//     (segments alternate direction so that neighbours read a shared boundary row at about the
+//     same time and the re-read hits L2).  Lane l owns column x0 + l.
+//   * Tiles are staged in shared memory by bulk asynchronous copies (cp.async.bulk, one 2304-byte
+//     copy per warp-row, completion on an mbarrier), S stages deep: while row i is collided,
+//     rows i+2 .. i+S-1 are in flight.
+//   * phi = sum f and p* = sum g-bar form a rolling 3x3 window in registers: east/west
+//     neighbours by warp shuffles; the two halo columns of the strip by one load per lane
+//     (lanes 0..8 read the g-bar planes, 16..24 the f planes) and a half-warp reduction,
+//     prefetched one row ahead.
+//   * Row y is updated once its upper and lower rows' (phi, p*) are known: stencils, forces,
+//     corrected p and u, both cascaded collisions in registers, then the 18 post-collision
+//     populations are pushed to x + e_a in the other buffer (half-way bounce-back at walls).
+//     The state therefore always holds streamed (pre-collision) populations.
+//   * Every mbarrier wait is bounded; on timeout the warp records an error code, waits (again
+//     bounded) for its copies in flight and returns.
 #include "lbm_device.cuh"
 
 namespace cmlbm {
 
 static constexpr unsigned FULL = 0xffffffffu;
+static constexpr int TILE = 18 * 32;               // elements per warp-row tile
+static constexpr unsigned WAIT_LIMIT = 1u << 22;   // bounded mbarrier polling
 
 struct StepLaunch {
     int seg_h;     // rows per segment
-    int nstrips;   // ceil(nx / 32)
     int nseg;      // ceil(ny / seg_h)
+    int* err;      // device error word (0 = ok)
 };
+
+template <typename S> struct Stages { static constexpr int value = 4; };
+template <> struct Stages<double> { static constexpr int value = 3; };
+
+// Per-warp shared memory: the stage tiles, then one mbarrier per stage; 128-byte multiple so that
+// every warp's tiles stay 16-byte aligned for the bulk copies.
+template <typename S>
+__host__ __device__ constexpr int warp_smem_bytes()
+{
+    return (Stages<S>::value * (TILE * (int)sizeof(S) + 8) + 127) / 128 * 128;
+}
+
+// ---------------------------------------------------------------------------------------------
+// mbarrier / bulk-copy primitives (inline PTX)
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// Warp-collective bounded wait for phase `parity` of barrier `bar`; false on timeout.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity)
+{
+    for (unsigned it = 0; it < WAIT_LIMIT; ++it)
+        if (__all_sync(FULL, mbar_try_wait(bar, parity))) return true;
+    return false;
+}
 
 template <typename R>
 __device__ __forceinline__ R shfl_up(R v) { return __shfl_up_sync(FULL, v, 1); }
@@ -38,35 +113,33 @@ __device__ __forceinline__ int map_row(int y, const Geometry& G)
     return y;
 }
 
+__device__ __forceinline__ int map_col(int x, const Geometry& G)
+{
+    if (x < 0) return G.wall_x ? 0 : x + G.nx;
+    if (x >= G.nx) return G.wall_x ? G.nx - 1 : x - G.nx;
+    return x;
+}
+
+// Element offset of column x within a row of tiles.
+__device__ __forceinline__ int col_off(int x) { return (x >> 5) * TILE + (x & 31); }
+
 // One (phi, p*) row of the window for this lane: own column, west and east neighbours.
 template <typename R>
 struct Row3 {
     R phw, phc, phe, psw, psc, pse;
 };
 
-// Load the 18 populations of column x in row yy, sum them, and assemble the lane's row of the
-// window including the strip's halo columns xl, xr.
+// Sum the lane's column of a staged tile and assemble its window row; hl/hr are this lane's
+// halo loads (one plane of the left / right halo column, or 0).
 template <typename R, typename S>
-__device__ __forceinline__ void load_row(const S* __restrict__ src, const Geometry& G, int yy,
-                                         int x, int xl, int xr, int lane, int wlast, R gq[9],
-                                         R fq[9], Row3<R>& row)
+__device__ __forceinline__ void window_row(const S* tile, int lane, int wlast, R hl, R hr,
+                                           Row3<R>& row)
 {
-    const S* base = src + (long long)yy * G.pitch + x;
+    R ps = R(0), ph = R(0);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        gq[a] = load_pop<S, R>(base + a * G.plane);
-        fq[a] = load_pop<S, R>(base + (9 + a) * G.plane);
-    }
-    // halo: lanes 0..8 read g-bar planes, lanes 16..24 read f planes, at columns xl and xr
-    const int q = lane & 15;
-    R hl = R(0), hr = R(0);
-    if (q < 9) {
-        const S* hb = src + (long long)((lane >> 4) * 9 + q) * G.plane + (long long)yy * G.pitch;
-        hl = load_pop<S, R>(hb + xl);
-        hr = load_pop<S, R>(hb + xr);
-    }
-    const R phc = ((fq[0] + fq[1]) + (fq[2] + fq[3])) + ((fq[4] + fq[5]) + (fq[6] + fq[7])) + fq[8];
-    const R psc = ((gq[0] + gq[1]) + (gq[2] + gq[3])) + ((gq[4] + gq[5]) + (gq[6] + gq[7])) + gq[8];
+    for (int a = 0; a < 9; ++a) ps += static_cast<R>(tile[a * 32 + lane]);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) ph += static_cast<R>(tile[(9 + a) * 32 + lane]);
 #pragma unroll
     for (int off = 8; off >= 1; off >>= 1) {
         hl += __shfl_xor_sync(FULL, hl, off);
@@ -74,19 +147,19 @@ __device__ __forceinline__ void load_row(const S* __restrict__ src, const Geomet
     }
     const R psl = __shfl_sync(FULL, hl, 0), phl = __shfl_sync(FULL, hl, 16);
     const R psr = __shfl_sync(FULL, hr, 0), phr = __shfl_sync(FULL, hr, 16);
-    row.phc = phc;
-    row.psc = psc;
-    row.phw = shfl_up(phc);
-    row.psw = shfl_up(psc);
-    row.phe = shfl_dn(phc);
-    row.pse = shfl_dn(psc);
+    row.phc = ph;
+    row.psc = ps;
+    row.phw = shfl_up(ph);
+    row.psw = shfl_up(ps);
+    row.phe = shfl_dn(ph);
+    row.pse = shfl_dn(ps);
     if (lane == 0) { row.phw = phl; row.psw = psl; }
     if (lane == wlast) { row.phe = phr; row.pse = psr; }
 }
 
 template <typename R>
-__device__ __forceinline__ void window(const Row3<R>& s, const Row3<R>& c, const Row3<R>& n,
-                                       Win<R>& ph, Win<R>& ps)
+__device__ __forceinline__ void make_window(const Row3<R>& s, const Row3<R>& c,
+                                            const Row3<R>& n, Win<R>& ph, Win<R>& ps)
 {
     ph.sw = s.phw; ph.s = s.phc; ph.se = s.phe;
     ph.w = c.phw;  ph.c = c.phc; ph.e = c.phe;
@@ -96,34 +169,13 @@ __device__ __forceinline__ void window(const Row3<R>& s, const Row3<R>& c, const
     ps.nw = n.psw; ps.n = n.psc; ps.ne = n.pse;
 }
 
-// Push the post-collision populations of node (x, y) to their destinations in dst.
-template <typename R, typename S>
-__device__ __forceinline__ void push_node(S* __restrict__ dst, const Geometry& G, int x, int y,
-                                          const R g[9], const R f[9])
+template <typename S, typename R>
+__device__ __forceinline__ void ld_pops_t(const S* tile, int lane, R g[9], R f[9])
 {
-    // neighbour rows/columns with periodic wrap; bounce flags where a wall is crossed
-    int ym = y - 1, yp = y + 1, xm = x - 1, xp = x + 1;
-    bool bys = false, byn = false, bxw = false, bxe = false;
-    if (ym < 0) { if (G.wall_y) bys = true; else ym += G.ny; }
-    if (yp >= G.ny) { if (G.wall_y) byn = true; else yp -= G.ny; }
-    if (xm < 0) { if (G.wall_x) bxw = true; else xm += G.nx; }
-    if (xp >= G.nx) { if (G.wall_x) bxe = true; else xp -= G.nx; }
-    const long long P = G.plane;
-    const long long rs = (long long)ym * G.pitch, rc = (long long)y * G.pitch,
-                    rn = (long long)yp * G.pitch;
-    const long long self = rc + x;
-    // destination offsets within a plane and bounce flags, alpha = 0..8
-    const long long off[9] = {self, rc + xp, rn + x, rc + xm, rs + x,
-                              rn + xp, rn + xm, rs + xm, rs + xp};
-    const bool bnc[9] = {false, bxe, byn, bxw, bys, bxe || byn, bxw || byn, bxw || bys,
-                         bxe || bys};
-    constexpr int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-        const long long og = bnc[a] ? OPP[a] * P + self : a * P + off[a];
-        const long long of = bnc[a] ? (9 + OPP[a]) * P + self : (9 + a) * P + off[a];
-        store_pop<S, R>(dst + og, g[a]);
-        store_pop<S, R>(dst + of, f[a]);
+        g[a] = static_cast<R>(tile[a * 32 + lane]);
+        f[a] = static_cast<R>(tile[(9 + a) * 32 + lane]);
     }
 }
 
@@ -132,54 +184,165 @@ __global__ void __launch_bounds__(256)
 step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R> K,
             StepLaunch L)
 {
+    constexpr int NS = Stages<S>::value;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    const int strip = warp % L.nstrips;
-    const int seg = warp / L.nstrips;
+    const int strip = warp % G.nstrips;
+    const int seg = warp / G.nstrips;
     if (seg >= L.nseg) return;                       // warp-uniform
+
+    S* tiles = reinterpret_cast<S*>(smem_raw + wib * warp_smem_bytes<S>());
+    const uint32_t bar0 = smem_u32(tiles + NS * TILE);
+    if (lane == 0)
+        for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8 * s, 1);
+    mbar_init_fence();
+    __syncwarp();
+
     const int x0 = strip * 32;
     const int w = min(32, G.nx - x0);
     const int wlast = w - 1;
     const bool active = lane < w;
     const int x = active ? x0 + lane : x0 + wlast;   // idle lanes shadow the last column
-    int xl = x0 - 1;
-    if (xl < 0) xl = G.wall_x ? 0 : G.nx - 1;
-    int xr = x0 + w;
-    if (xr >= G.nx) xr = G.wall_x ? G.nx - 1 : xr - G.nx;
+    const int xl = map_col(x0 - 1, G), xr = map_col(x0 + w, G);
+    const long long row_elems = (long long)G.nstrips * TILE;
 
     const int ys = seg * L.seg_h;
     const int ye = min(ys + L.seg_h, G.ny);
-    const bool up = (seg & 1) == 0;
-    const int dir = up ? 1 : -1;
-    int y = up ? ys : ye - 1;                        // first row updated
     const int nrows = ye - ys;
+    const bool up = (seg & 1) == 0;
+    // row visited at step k (k = -1 .. nrows): behind/current/ahead rows of the march
+    auto row_of = [&](int k) { return map_row(up ? ys + k : ye - 1 - k, G); };
 
-    R gA[9], fA[9], gB[9], fB[9];
-    Row3<R> rb, rc, rn;   // rows behind (y - dir), current (y), ahead (y + dir)
-    load_row<R, S>(src, G, map_row(y - dir, G), x, xl, xr, lane, wlast, gB, fB, rb);
-    load_row<R, S>(src, G, y, x, xl, xr, lane, wlast, gA, fA, rc);
+    // halo: lanes 0..8 load g-bar plane q, lanes 16..24 f plane q, at columns xl and xr
+    const int hq = lane & 15;
+    const bool hlane = hq < 9;
+    const int hplane = (lane >> 4) * 9 + hq;
+    const int hoffl = col_off(xl) + hplane * 32;
+    const int hoffr = col_off(xr) + hplane * 32;
+    auto halo_load = [&](int k, R& hl, R& hr) {
+        hl = R(0);
+        hr = R(0);
+        if (hlane) {
+            const S* rb = src + (long long)row_of(k) * row_elems;
+            hl = static_cast<R>(__ldg(rb + hoffl));
+            hr = static_cast<R>(__ldg(rb + hoffr));
+        }
+    };
+
+    uint32_t phase_bits = 0;   // parity of the next wait, per stage
+    int issued = -2;           // highest k whose tile copy was issued
+    auto stage_of = [&](int k) { return (k + 1) % NS; };
+    auto issue = [&](int k) {
+        if (k > nrows) return;
+        __syncwarp();
+        if (lane == 0) {
+            const int s = stage_of(k);
+            fence_proxy_async();
+            const uint32_t bar = bar0 + 8 * s;
+            mbar_expect_tx(bar, TILE * sizeof(S));
+            bulk_g2s(smem_u32(tiles + s * TILE),
+                     src + (long long)row_of(k) * row_elems + (long long)strip * TILE,
+                     TILE * sizeof(S), bar);
+        }
+        issued = k;
+    };
+    auto wait_k = [&](int k) -> bool {
+        const int s = stage_of(k);
+        if (!warp_wait(bar0 + 8 * s, (phase_bits >> s) & 1u)) return false;
+        phase_bits ^= 1u << s;
+        return true;
+    };
+    // timeout: record the error, wait (bounded) for every copy still in flight, then return
+    auto fail = [&](int k_failed) {
+        if (lane == 0) atomicCAS(L.err, 0, 1);
+        for (int k = k_failed; k <= issued; ++k) wait_k(k);
+    };
+
+    for (int k = -1; k <= NS - 2; ++k) issue(k);
+
+    Row3<R> rb, rc, rn;   // rows behind, current, ahead (in marching order)
+    R hl, hr, hl2, hr2;
+    halo_load(-1, hl, hr);
+    if (!wait_k(-1)) { fail(-1); return; }
+    window_row<R, S>(tiles + stage_of(-1) * TILE, lane, wlast, hl, hr, rb);
+    issue(NS - 1);
+    halo_load(0, hl, hr);
+    if (!wait_k(0)) { fail(0); return; }
+    window_row<R, S>(tiles + stage_of(0) * TILE, lane, wlast, hl, hr, rc);
+    halo_load(1, hl2, hr2);
+
+    // neighbour columns of this lane (periodic wrap; walls handled by bounce flags)
+    int xm = x - 1, xp = x + 1;
+    const bool bxw = xm < 0 && G.wall_x, bxe = xp >= G.nx && G.wall_x;
+    if (xm < 0) xm += G.nx;
+    if (xp >= G.nx) xp -= G.nx;
+    const int cw = col_off(xm), cc = col_off(x), ce = col_off(xp);
+    const bool xwall_warp = __any_sync(FULL, bxw || bxe);
     const R xf = R(x);
 
-    for (int it = 0; it < nrows; ++it, y += dir) {
-        load_row<R, S>(src, G, map_row(y + dir, G), x, xl, xr, lane, wlast, gB, fB, rn);
+    for (int i = 0; i < nrows; ++i) {
+        if (!wait_k(i + 1)) { fail(i + 1); return; }
+        window_row<R, S>(tiles + stage_of(i + 1) * TILE, lane, wlast, hl2, hr2, rn);
+        if (i + 2 <= nrows) halo_load(i + 2, hl2, hr2);
+
+        const int y = up ? ys + i : ye - 1 - i;
         Win<R> ph, ps;
-        if (up) window(rb, rc, rn, ph, ps);
-        else window(rn, rc, rb, ph, ps);
-        const R jgx = (gA[1] - gA[3]) + (gA[5] - gA[6]) - (gA[7] - gA[8]);
-        const R jgy = (gA[2] - gA[4]) + (gA[5] + gA[6]) - (gA[7] + gA[8]);
+        if (up) make_window(rb, rc, rn, ph, ps);
+        else make_window(rn, rc, rb, ph, ps);
+        R g[9], f[9];
+        ld_pops_t<S, R>(tiles + stage_of(i) * TILE, lane, g, f);
+        const R jgx = (g[1] - g[3]) + (g[5] - g[6]) - (g[7] - g[8]);
+        const R jgy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
         Macro<R> m;
         node_macro<R>(ph, ps, jgx, jgy, xf, R(y), K, m);
-        collide_fluid<R>(gA, m);
-        collide_ace<R>(fA, m, K.omega_phi_6);
-        if (active) push_node<R, S>(dst, G, x, y, gA, fA);
+        collide_fluid<R>(g, m);
+        collide_ace<R>(f, ph.c, m, K.omega_phi_6);
+
+        // push to x + e_a: rows y-1, y, y+1 and columns x-1, x, x+1 of the other buffer
+        int ym = y - 1, yp = y + 1;
+        const bool bys = ym < 0 && G.wall_y, byn = yp >= G.ny && G.wall_y;
+        if (ym < 0) ym += G.ny;
+        if (yp >= G.ny) yp -= G.ny;
+        S* rS = dst + (long long)ym * row_elems;
+        S* rC = dst + (long long)y * row_elems;
+        S* rN = dst + (long long)yp * row_elems;
+        S* pc = rC + cc;
+        S* p[9] = {pc, rC + ce, rN + cc, rC + cw, rS + cc, rN + ce, rN + cw, rS + cw, rS + ce};
+        const bool bnc[9] = {false, bxe, byn, bxw, bys, bxe || byn, bxw || byn, bxw || bys,
+                             bxe || bys};
+        constexpr int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+        if (!(bys || byn) && !xwall_warp) {      // warp-uniform: no wall crossed by this row
+            if (active) {
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    p[a][a * 32] = static_cast<S>(g[a]);
+                    p[a][(9 + a) * 32] = static_cast<S>(f[a]);
+                }
+            }
+        } else if (active) {
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                S* q = bnc[a] ? pc + (OPP[a] - a) * 32 : p[a];
+                q[a * 32] = static_cast<S>(g[a]);
+                q[(9 + a) * 32] = static_cast<S>(f[a]);
+            }
+        }
+        issue(i + NS);          // the tile of row i is consumed: refill its stage
         rb = rc;
         rc = rn;
-#pragma unroll
-        for (int a = 0; a < 9; ++a) { gA[a] = gB[a]; fA[a] = fB[a]; }
     }
 }
 
-// Equilibrium initialisation from nodal fields (double, row-major [ny][nx]).
+// ---------------------------------------------------------------------------------------------
+// Initialisation, field extraction, packing (one thread per node; not on the hot path)
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ long long elem_index(const Geometry& G, int a, int x, int y)
+{
+    return ((long long)y * G.nstrips + (x >> 5)) * TILE + a * 32 + (x & 31);
+}
+
 template <typename R, typename S>
 __global__ void init_kernel(const double* __restrict__ phi, const double* __restrict__ p,
                             const double* __restrict__ ux, const double* __restrict__ uy,
@@ -192,11 +355,10 @@ __global__ void init_kernel(const double* __restrict__ phi, const double* __rest
     const R rho = K.rho_b + ph * K.drho;
     R g[9], f[9];
     equilibria<R>(ph, R(p[n]), R(ux[n]), R(uy[n]), rho, g, f);
-    const long long o = (long long)y * G.pitch + x;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-        store_pop<S, R>(state + a * G.plane + o, g[a]);
-        store_pop<S, R>(state + (9 + a) * G.plane + o, f[a]);
+        state[elem_index(G, a, x, y)] = static_cast<S>(g[a]);
+        state[elem_index(G, 9 + a, x, y)] = static_cast<S>(f[a]);
     }
 }
 
@@ -215,29 +377,24 @@ __global__ void fields_kernel(const S* __restrict__ state, Geometry G, Consts<R>
     for (int j = -1; j <= 1; ++j) {
         const int yy = map_row(y + j, G);
         for (int i = -1; i <= 1; ++i) {
-            int xx = x + i;
-            if (xx < 0) xx = G.wall_x ? 0 : xx + G.nx;
-            if (xx >= G.nx) xx = G.wall_x ? G.nx - 1 : xx - G.nx;
-            const S* b = state + (long long)yy * G.pitch + xx;
-            R sg = R(0), sf = R(0);
+            const int xx = map_col(x + i, G);
             R gq[9], fq[9];
             for (int a = 0; a < 9; ++a) {
-                gq[a] = load_pop<S, R>(b + a * G.plane);
-                fq[a] = load_pop<S, R>(b + (9 + a) * G.plane);
+                gq[a] = static_cast<R>(state[elem_index(G, a, xx, yy)]);
+                fq[a] = static_cast<R>(state[elem_index(G, 9 + a, xx, yy)]);
             }
-            sf = ((fq[0] + fq[1]) + (fq[2] + fq[3])) + ((fq[4] + fq[5]) + (fq[6] + fq[7])) + fq[8];
-            sg = ((gq[0] + gq[1]) + (gq[2] + gq[3])) + ((gq[4] + gq[5]) + (gq[6] + gq[7])) + gq[8];
-            vph[j + 1][i + 1] = sf;
-            vps[j + 1][i + 1] = sg;
+            vph[j + 1][i + 1] =
+                ((fq[0] + fq[1]) + (fq[2] + fq[3])) + ((fq[4] + fq[5]) + (fq[6] + fq[7])) + fq[8];
+            vps[j + 1][i + 1] =
+                ((gq[0] + gq[1]) + (gq[2] + gq[3])) + ((gq[4] + gq[5]) + (gq[6] + gq[7])) + gq[8];
         }
     }
     Win<R> ph = {vph[0][0], vph[0][1], vph[0][2], vph[1][0], vph[1][1], vph[1][2],
                  vph[2][0], vph[2][1], vph[2][2]};
     Win<R> ps = {vps[0][0], vps[0][1], vps[0][2], vps[1][0], vps[1][1], vps[1][2],
                  vps[2][0], vps[2][1], vps[2][2]};
-    const S* b = state + (long long)y * G.pitch + x;
     R gq[9];
-    for (int a = 0; a < 9; ++a) gq[a] = load_pop<S, R>(b + a * G.plane);
+    for (int a = 0; a < 9; ++a) gq[a] = static_cast<R>(state[elem_index(G, a, x, y)]);
     const R jgx = (gq[1] - gq[3]) + (gq[5] - gq[6]) - (gq[7] - gq[8]);
     const R jgy = (gq[2] - gq[4]) + (gq[5] + gq[6]) - (gq[7] + gq[8]);
     Macro<R> m;
@@ -249,16 +406,16 @@ __global__ void fields_kernel(const S* __restrict__ state, Geometry G, Consts<R>
     if (rho_o) rho_o[n] = double(m.rho);
 }
 
-// Copy between the padded device state and a dense [18][ny][nx] double array.
+// Copy between the tiled device state and a dense [18][ny][nx] double array.
 template <typename S>
 __global__ void pack_kernel(const S* __restrict__ state, double* __restrict__ out, Geometry G)
 {
     const long long N = (long long)G.nx * G.ny;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 18 * N) return;
-    const long long a = t / N, n = t % N;
-    const int y = (int)(n / G.nx), x = (int)(n % G.nx);
-    out[t] = double(state[a * G.plane + (long long)y * G.pitch + x]);
+    const int a = (int)(t / N);
+    const long long n = t % N;
+    out[t] = double(state[elem_index(G, a, (int)(n % G.nx), (int)(n / G.nx))]);
 }
 
 template <typename S>
@@ -267,28 +424,92 @@ __global__ void unpack_kernel(const double* __restrict__ in, S* __restrict__ sta
     const long long N = (long long)G.nx * G.ny;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 18 * N) return;
-    const long long a = t / N, n = t % N;
-    const int y = (int)(n / G.nx), x = (int)(n % G.nx);
-    state[a * G.plane + (long long)y * G.pitch + x] = static_cast<S>(in[t]);
+    const int a = (int)(t / N);
+    const long long n = t % N;
+    state[elem_index(G, a, (int)(n % G.nx), (int)(n / G.nx))] = static_cast<S>(in[t]);
 }
 
 // ---------------------------------------------------------------------------------------------
 // Host-side launchers (called from lbm_api.cu)
 // ---------------------------------------------------------------------------------------------
+template <typename S>
+size_t step_smem_bytes(int block) { return (size_t)(block / 32) * warp_smem_bytes<S>(); }
+
+// Allow the dynamic shared memory of a block of `block` threads (call once per device).
+template <typename R, typename S>
+cudaError_t configure_step(int block)
+{
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<R, S>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)step_smem_bytes<S>(block));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(step_kernel<R, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+
+// Resident blocks of `block` threads per SM for the step kernel.
+template <typename R, typename S>
+int step_blocks_per_sm(int block)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<R, S>, block,
+                                                      step_smem_bytes<S>(block)) != cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
+}
+
 template <typename R, typename S>
 cudaError_t launch_step(const void* src, void* dst, const Geometry& G, const Consts<R>& K,
-                        int seg_h, int block, cudaStream_t st)
+                        int seg_h, int block, int* err, cudaStream_t st)
 {
     StepLaunch L;
     L.seg_h = seg_h;
-    L.nstrips = (G.nx + 31) / 32;
     L.nseg = (G.ny + seg_h - 1) / seg_h;
-    const long long warps = (long long)L.nstrips * L.nseg;
+    L.err = err;
+    const long long warps = (long long)G.nstrips * L.nseg;
     const int wpb = block / 32;
     const long long grid = (warps + wpb - 1) / wpb;
-    step_kernel<R, S><<<(unsigned)grid, block, 0, st>>>(static_cast<const S*>(src),
-                                                        static_cast<S*>(dst), G, K, L);
+    step_kernel<R, S><<<(unsigned)grid, block, step_smem_bytes<S>(block), st>>>(
+        static_cast<const S*>(src), static_cast<S*>(dst), G, K, L);
     return cudaGetLastError();
+}
+
+// A graph of `chunk` (even) consecutive steps starting from buffer `a` (a -> b -> a -> ...),
+// replayed by lbm_step to cut the per-launch gaps between steps.
+template <typename R, typename S>
+cudaError_t build_step_graph(const void* a, const void* b, const Geometry& G, const Consts<R>& K,
+                             int seg_h, int block, int* err, int chunk, cudaGraphExec_t* out)
+{
+    StepLaunch L;
+    L.seg_h = seg_h;
+    L.nseg = (G.ny + seg_h - 1) / seg_h;
+    L.err = err;
+    const long long warps = (long long)G.nstrips * L.nseg;
+    const int wpb = block / 32;
+    const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphNode_t prev = nullptr;
+    Geometry g = G;
+    Consts<R> k = K;
+    for (int s = 0; s < chunk && e == cudaSuccess; ++s) {
+        const S* src = static_cast<const S*>((s & 1) ? b : a);
+        S* dst = const_cast<S*>(static_cast<const S*>((s & 1) ? a : b));
+        void* args[] = {(void*)&src, (void*)&dst, (void*)&g, (void*)&k, (void*)&L};
+        cudaKernelNodeParams p = {};
+        p.func = (void*)step_kernel<R, S>;
+        p.gridDim = dim3(grid);
+        p.blockDim = dim3(block);
+        p.sharedMemBytes = (unsigned)step_smem_bytes<S>(block);
+        p.kernelParams = args;
+        cudaGraphNode_t node;
+        e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &p);
+        prev = node;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    return e;
 }
 
 template <typename R, typename S>
@@ -329,10 +550,24 @@ cudaError_t launch_unpack(const double* in, void* state, const Geometry& G, cuda
     return cudaGetLastError();
 }
 
+template size_t step_smem_bytes<double>(int);
+template size_t step_smem_bytes<float>(int);
+template cudaError_t configure_step<double, double>(int);
+template int step_blocks_per_sm<double, double>(int);
+template cudaError_t build_step_graph<double, double>(const void*, const void*, const Geometry&,
+                                                      const Consts<double>&, int, int, int*, int,
+                                                      cudaGraphExec_t*);
+template cudaError_t build_step_graph<float, float>(const void*, const void*, const Geometry&,
+                                                    const Consts<float>&, int, int, int*, int,
+                                                    cudaGraphExec_t*);
+template int step_blocks_per_sm<float, float>(int);
+template cudaError_t configure_step<float, float>(int);
 template cudaError_t launch_step<double, double>(const void*, void*, const Geometry&,
-                                                 const Consts<double>&, int, int, cudaStream_t);
+                                                 const Consts<double>&, int, int, int*,
+                                                 cudaStream_t);
 template cudaError_t launch_step<float, float>(const void*, void*, const Geometry&,
-                                               const Consts<float>&, int, int, cudaStream_t);
+                                               const Consts<float>&, int, int, int*,
+                                               cudaStream_t);
 template cudaError_t launch_init<double, double>(const double*, const double*, const double*,
                                                  const double*, void*, const Geometry&,
                                                  const Consts<double>&, cudaStream_t);

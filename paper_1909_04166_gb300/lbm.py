@@ -23,6 +23,7 @@ LBM_ERR_NOMEM = -4
 LBM_ERR_STATE = -5
 LBM_ERR_NONFINITE = -6
 LBM_ERR_UNSUPPORTED = -7
+LBM_ERR_TIMEOUT = -8
 
 LBM_FP64 = 0
 LBM_FP32 = 1
@@ -36,6 +37,7 @@ EXPORTS = [
     "lbm_init_fields_device", "lbm_step", "lbm_get_fields", "lbm_get_populations",
     "lbm_set_populations", "lbm_state_device", "lbm_diagnostics", "lbm_set_launch",
     "lbm_get_launch", "lbm_steps_done", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error",
+    "lbm_check", "lbm_set_graphs",
 ]
 
 
@@ -107,6 +109,8 @@ def lib(build_if_missing: bool = True):
     L.lbm_strerror.argtypes = [ctypes.c_int]
     L.lbm_strerror.restype = ctypes.c_char_p
     L.lbm_last_cuda_error.argtypes = [vp]
+    L.lbm_check.argtypes = [vp]
+    L.lbm_set_graphs.argtypes = [vp, i32]
     _lib = L
     return L
 
@@ -193,10 +197,18 @@ def lbm_set_populations(ctx, g, f) -> None:
 
 
 def lbm_state_device(ctx):
-    ptr, pitch, plane = ctypes.c_void_p(), ctypes.c_int32(), ctypes.c_int64()
-    _check(lib().lbm_state_device(ctx, ctypes.byref(ptr), ctypes.byref(pitch),
-                                  ctypes.byref(plane)), "lbm_state_device")
-    return int(ptr.value or 0), int(pitch.value), int(plane.value)
+    ptr, nstrips, elems = ctypes.c_void_p(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().lbm_state_device(ctx, ctypes.byref(ptr), ctypes.byref(nstrips),
+                                  ctypes.byref(elems)), "lbm_state_device")
+    return int(ptr.value or 0), int(nstrips.value), int(elems.value)
+
+
+def lbm_set_graphs(ctx, enable: bool) -> None:
+    _check(lib().lbm_set_graphs(ctx, int(bool(enable))), "lbm_set_graphs")
+
+
+def lbm_check(ctx) -> None:
+    _check(lib().lbm_check(ctx), "lbm_check")
 
 
 def lbm_diagnostics(ctx, xc=0.0, yc=0.0, r_in=-1.0, r_out=0.0, allow_nonfinite=True) -> dict:

@@ -97,6 +97,18 @@ def test_launch_shape_does_not_change_results():
         assert np.array_equal(g, outs[0][0]) and np.array_equal(f, outs[0][1])
 
 
+def test_graph_replays_match_single_launches():
+    case = W.random_drop(64, 48, seed=12, wall_y=True, rho_ratio=100.0)
+    outs = []
+    for graphs in (False, True):
+        with lbm.Simulation(case, precision="fp32") as sim:
+            sim.init_case()
+            lbm.lbm_set_graphs(sim.ctx, graphs)
+            sim.step(70).step(33)
+            outs.append(sim.populations())
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
 def test_checkpoint_restart_is_exact():
     case = W.random_drop(48, 40, seed=8, wall_x=True, rho_ratio=50.0)
     for prec in ("fp64", "fp32"):
