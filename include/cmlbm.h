@@ -177,6 +177,31 @@ const char* lbm_strerror(int status);
 /* The last CUDA error code the context saw (cudaError_t as int), 0 if none. */
 int lbm_last_cuda_error(const lbm_ctx* ctx);
 
+/* Allocation-free variant of the diagnostics reduction (the paper has no counterpart; this is a
+ * service entry point).  It serves callers that must not allocate device memory at this point:
+ * code running while a CUDA graph is being captured (cudaMalloc is not capturable), real-time or
+ * embedded loops that pre-size every buffer, and hosts whose allocator is owned by another
+ * framework.  Unlike lbm_diagnostics it needs no context and allocates nothing: the per-block
+ * partial sums go to a fixed device array inside the library (4097 x 8 doubles, 262 KB, held by
+ * every GPU that loads the library until the process exits).
+ *
+ * Inputs: device arrays phi, p, ux, uy of nx * ny doubles, row-major [ny][nx] (for instance
+ * the fields lbm_get_fields returns, copied to the device), the boundary kinds of the two axes
+ * (lbm_bc, used for periodic distances) and the Laplace regions as in lbm_diagnostics.
+ * Output: *out, an lbm_diag in DEVICE memory, written asynchronously on `stream` (cudaStream_t,
+ * NULL = legacy default stream); read it after synchronising.  The call itself does not
+ * synchronise and does not report LBM_ERR_NONFINITE: inspect out->nonfinite.
+ * Limit: nx * ny <= 8,388,608 nodes (4096 partial blocks of 2048 nodes); larger grids return
+ * LBM_ERR_ARG.  The first call on a device looks up the array's device address with the device
+ * current (make that first call before any stream capture begins); the address is cached per
+ * device ordinal (0..63).  Every call reuses the same array: calls that overlap on the GPU (on
+ * different streams, or on other host threads) race and give wrong results; serialise them.
+ * Each call writes every partial slot it reads, so nothing needs clearing between calls. */
+int lbm_diagnostics_noalloc(const double* phi, const double* p, const double* ux,
+                            const double* uy, int32_t nx, int32_t ny, int32_t bc_x, int32_t bc_y,
+                            double xc, double yc, double r_in, double r_out, lbm_diag* out,
+                            void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "../../include/cmlbm.h"
@@ -343,6 +344,37 @@ __global__ void diag_final_kernel(double* __restrict__ part, int nblocks)
     part[(size_t)nblocks * kReduceSlots + k] = r;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Allocation-free diagnostics: the block partials live in a fixed device array instead of
+// context scratch.  The array is part of the library image, so every GPU that loads the library
+// holds it until the process exits.
+// ---------------------------------------------------------------------------------------------
+constexpr int kNoAllocMaxBlocks = 4096;          // partial-sum slots in the fixed array
+constexpr int kNoAllocThreads = 256;
+constexpr long long kNoAllocNodesPerBlock = 2048; // 8 nodes per thread
+static __device__ __align__(256) double g_noalloc_partials[(kNoAllocMaxBlocks + 1) * kReduceSlots];
+
+// Device address of g_noalloc_partials per device ordinal, looked up once per device.
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[64] = {};
+
+__global__ void diag_store_kernel(const double* __restrict__ part, int nblocks, lbm_diag* out)
+{
+    if (threadIdx.x != 0) return;
+    double r[kReduceSlots];
+    for (int k = 0; k < kReduceSlots; ++k) r[k] = 0.0;
+    for (int b = 0; b < nblocks; ++b)
+        for (int k = 0; k < kReduceSlots; ++k) {
+            const double v = part[(size_t)b * kReduceSlots + k];
+            r[k] = (k == 2) ? fmax(r[k], v) : r[k] + v;
+        }
+    out->sum_phi = r[0];
+    out->sum_p = r[1];
+    out->max_speed = r[2];
+    out->dp_laplace = (r[4] > 0 && r[6] > 0) ? r[3] / r[4] - r[5] / r[6] : 0.0;
+    out->nonfinite = (int64_t)r[7];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -616,5 +648,36 @@ const char* lbm_strerror(int s)
 }
 
 int lbm_last_cuda_error(const lbm_ctx* c) { return c ? c->last_cuda : 0; }
+
+int lbm_diagnostics_noalloc(const double* phi, const double* p, const double* ux,
+                            const double* uy, int32_t nx, int32_t ny, int32_t bc_x, int32_t bc_y,
+                            double xc, double yc, double r_in, double r_out, lbm_diag* out,
+                            void* stream)
+{
+    if (!phi || !p || !ux || !uy || !out || nx < 1 || ny < 1) return LBM_ERR_ARG;
+    if ((bc_x != LBM_PERIODIC && bc_x != LBM_WALL) || (bc_y != LBM_PERIODIC && bc_y != LBM_WALL))
+        return LBM_ERR_ARG;
+    const long long N = (long long)nx * ny;
+    if (N > (long long)kNoAllocMaxBlocks * kNoAllocNodesPerBlock) return LBM_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LBM_ERR_CUDA;
+    double* part = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void* addr = nullptr;
+            if (cudaGetSymbolAddress(&addr, g_noalloc_partials) != cudaSuccess || !addr)
+                return LBM_ERR_CUDA;
+            g_noalloc_ptr[dev] = static_cast<double*>(addr);
+        }
+        part = g_noalloc_ptr[dev];
+    }
+    const int nb = (int)((N + kNoAllocNodesPerBlock - 1) / kNoAllocNodesPerBlock);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DiagArgs A{nx, ny, bc_x == LBM_WALL, bc_y == LBM_WALL, xc, yc, r_in, r_out};
+    diag_partial_kernel<<<nb, kNoAllocThreads, 0, st>>>(phi, p, ux, uy, A, part);
+    diag_store_kernel<<<1, 32, 0, st>>>(part, nb, out);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
 
 }  // extern "C"

@@ -37,7 +37,7 @@ EXPORTS = [
     "lbm_init_fields_device", "lbm_step", "lbm_get_fields", "lbm_get_populations",
     "lbm_set_populations", "lbm_state_device", "lbm_diagnostics", "lbm_set_launch",
     "lbm_get_launch", "lbm_steps_done", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error",
-    "lbm_check", "lbm_set_graphs",
+    "lbm_check", "lbm_set_graphs", "lbm_diagnostics_noalloc",
 ]
 
 
@@ -111,6 +111,9 @@ def lib(build_if_missing: bool = True):
     L.lbm_last_cuda_error.argtypes = [vp]
     L.lbm_check.argtypes = [vp]
     L.lbm_set_graphs.argtypes = [vp, i32]
+    dd = ctypes.c_double
+    L.lbm_diagnostics_noalloc.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, dd, dd, dd, dd,
+                                          vp, vp]
     _lib = L
     return L
 
@@ -201,6 +204,18 @@ def lbm_state_device(ctx):
     _check(lib().lbm_state_device(ctx, ctypes.byref(ptr), ctypes.byref(nstrips),
                                   ctypes.byref(elems)), "lbm_state_device")
     return int(ptr.value or 0), int(nstrips.value), int(elems.value)
+
+
+def lbm_diagnostics_noalloc(phi_ptr: int, p_ptr: int, ux_ptr: int, uy_ptr: int, nx: int,
+                            ny: int, bc_x: int, bc_y: int, xc: float, yc: float, r_in: float,
+                            r_out: float, out_ptr: int, stream: int = 0) -> None:
+    """Allocation-free diagnostics of device nodal fields into a device lbm_diag (see the C
+    header); asynchronous on `stream`."""
+    v = ctypes.c_void_p
+    _check(lib().lbm_diagnostics_noalloc(v(phi_ptr), v(p_ptr), v(ux_ptr), v(uy_ptr), int(nx),
+                                         int(ny), int(bc_x), int(bc_y), float(xc), float(yc),
+                                         float(r_in), float(r_out), v(out_ptr), v(int(stream))),
+           "lbm_diagnostics_noalloc")
 
 
 def lbm_set_graphs(ctx, enable: bool) -> None:
