@@ -78,7 +78,10 @@ def kernel_source_hash() -> str:
 
 # DRAM traffic per launch of the step kernel from an ncu capture (profiles/), keyed by the
 # hash of the kernel sources it was taken on; scaled by node count to the bench workload.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/step_kernel_impact_2048x1024_fp32.md
+    ("05c45a952a1406ca", "impact", "fp32"): 252_489_728,
+}
 
 
 class Clocks:
