@@ -106,7 +106,7 @@ Consts<R> make_consts(const lbm_params& P)
     K.mob = R(P.mobility);
     K.four_over_w = R(4.0 / P.width);
     // M_phi = c^2 (1/omega - 1/2) -> omega = 1 / (3 M_phi + 1/2)
-    K.omega_phi_6 = R(1.0 / (3.0 * P.mobility + 0.5) / 6.0);
+    K.omega_phi = R(1.0 / (3.0 * P.mobility + 0.5));
     K.gx = R(P.gx);
     K.gy = R(P.gy);
     K.rho_ref = R(P.rho_ref);

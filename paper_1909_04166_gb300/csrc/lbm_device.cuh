@@ -26,7 +26,7 @@ struct Consts {
     R kt0, dktx, dkty;   // kappa-tilde(x, y) = kt0 + dktx x + dkty y   (kappa-tilde = 3/2 sigma W)
     R mob;               // M_phi
     R four_over_w;       // theta = (4/W) phi (1 - phi)                 (Sec. 2 Eq. thetavariable)
-    R omega_phi_6;       // omega^phi_{1,2} / 6, from M_phi = c^2 (1/omega - 1/2)   (Sec. 5)
+    R omega_phi;         // omega^phi_{1,2}, from M_phi = c^2 (1/omega - 1/2)   (Sec. 5)
     R gx, gy, rho_ref;   // F_ext = (rho - rho_ref) g
     R cs2_drho;          // c_s^2 (rho_A - rho_B), the factor of grad rho in F_p
 };
@@ -133,137 +133,117 @@ __device__ __forceinline__ void node_macro(const Win<R>& ph, const Win<R>& ps, R
     m.jy = theta_m * ny;
 }
 
-// Apply the moment-change vector c (coefficients of the orthogonal basis K_0..K_8 of Sec. 4
-// Eq. orthogonalbasisvectors) to nine populations: q_a += sum_j K_j(a) c_j.
+// Populations from the nine raw moments (00,10,01,20,02,11,21,12,22) of D2Q9: the closed-form
+// inverse of the moment matrix, with shared partial sums.
 template <typename R>
-__device__ __forceinline__ void apply_basis(R q[9], const R c[9])
+__device__ __forceinline__ void raw_to_pop_fast(R r00, R r10, R r01, R r20, R r02, R r11, R r21,
+                                                R r12, R r22, R q[9])
 {
-    const R A = c[0] - c[3] - R(2) * c[8];
-    const R B = c[0] + R(2) * c[3] + c[8];
-    const R s1 = c[1] - c[7], s2 = c[2] - c[6];
-    q[0] += c[0] - R(4) * c[3] + R(4) * c[8];
-    q[1] += A + c[1] + c[4] + R(2) * c[7];
-    q[3] += A - c[1] + c[4] - R(2) * c[7];
-    q[2] += A + c[2] - c[4] + R(2) * c[6];
-    q[4] += A - c[2] - c[4] - R(2) * c[6];
-    q[5] += B + s1 + s2 + c[5];
-    q[6] += B - s1 + s2 - c[5];
-    q[7] += B - s1 - s2 + c[5];
-    q[8] += B + s1 - s2 - c[5];
+    const R a = r20 - r22, b = r02 - r22;
+    const R sx = r10 - r12, sy = r01 - r21;
+    q[0] = (r00 - a) - (b + r22);
+    q[1] = R(0.5) * (a + sx);
+    q[3] = R(0.5) * (a - sx);
+    q[2] = R(0.5) * (b + sy);
+    q[4] = R(0.5) * (b - sy);
+    const R s = r22 + r21, t = r22 - r21, u = r11 + r12, v = r12 - r11;
+    q[5] = R(0.25) * (s + u);
+    q[6] = R(0.25) * (s - u);
+    q[7] = R(0.25) * (t - v);
+    q[8] = R(0.25) * (t + v);
 }
 
-// Fluid-lattice collision (Sec. 4): h-hat of Eq. cascadedcollisionoperator plus the cumulative
-// source delta g^s = K^-1 (I - Lambda/2) K S, combined into one moment-change vector.  All
-// fluid relaxation rates are 1 except omega_4 = omega_5 = m.omega.
+// Fluid-lattice collision (Sec. 4), evaluated in raw-moment space.  The printed update
+// g-bar-tilde = g-bar + K h-hat + delta g^s is rewritten exactly as follows:
+//  * K (h-hat_3 .. h-hat_8) relaxes the central moments (about u) of the state V whose raw
+//    moments are those of g-bar with the zeroth and first replaced by p and rho c^2 u (the
+//    printed h-hat_3..8 use exactly these); with omega = 1 for the trace, 21, 12 and 22 moments
+//    those become their equilibria (Sec. 3 Eq. centralmomentsgeqcomponents) and only the
+//    deviator and the 11 moment keep a memory of g-bar, relaxed at omega_4 = omega_5;
+//  * K (h-hat_0, h-hat_1, h-hat_2) and delta g^s = (1/2) S + (1/2 - omega/2)(K_4, K_5 parts of S)
+//    (Sec. 4 Eqs. sourcetermcumulativetransformed, cumulativesourcetermcomponents) add known
+//    raw moments;
+//  * g-bar itself differs from V only in the zeroth and first raw moments.
+// The nine raw moments of the result are assembled and inverted once.  Inputs: the streamed
+// g-bar (overwritten with the post-collision populations) and p* = sum g-bar.
 template <typename R>
-__device__ __forceinline__ void collide_fluid(R g[9], const Macro<R>& m)
+__device__ __forceinline__ void collide_fluid(R g[9], R pstar, const Macro<R>& m)
 {
-    const R third = R(1) / R(3);
+    const R third = R(1) / R(3), ninth = R(1) / R(9);
     const R ux = m.ux, uy = m.uy, p = m.p, rho = m.rho, om = m.omega;
-    const R ux2 = ux * ux, uy2 = uy * uy;
-    // raw moments of the streamed g-bar
-    const R d = (g[5] + g[6]) + (g[7] + g[8]);   // eta'_22
-    const R e20 = g[1] + g[3] + d;
-    const R e02 = g[2] + g[4] + d;
+    const R ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const R rc2 = rho * third;                 // rho c^2
+    const R psi = p - rc2;                     // p - rho c^2
+    // second-order raw moments of g-bar that survive the collision (deviator and 11)
+    const R dev = (g[1] + g[3]) - (g[2] + g[4]);
     const R e11 = (g[5] - g[6]) + (g[7] - g[8]);
-    const R e21 = (g[5] + g[6]) - (g[7] + g[8]);
-    const R e12 = (g[5] - g[6]) - (g[7] - g[8]);
-    const R e22 = d;
-    const R psi = p - rho * third;
-    const R rc2 = rho * third;
-
-    // source raw moments sigma' (Gamma^t, Gamma^p matched, second order and above of the
-    // cumulative source truncated as in Sec. 4)
+    // central moments of V: deviator and 11, relaxed at omega
+    const R a2 = p - R(2) * rc2;
+    const R dV = dev + a2 * (ux2 - uy2);
+    const R cV = e11 + a2 * uxy;
+    const R dP = dV + om * (psi * (ux2 - uy2) - dV);
+    const R cP = cV + om * (psi * uxy - cV);
+    // post-collision central moments of order >= 2 (equilibria except dP, cP)
+    const R tP = R(2) * p * third + psi * (ux2 + uy2);
+    const R c20 = R(0.5) * (tP + dP), c02 = R(0.5) * (tP - dP);
+    const R c21 = -psi * (third + ux2) * uy;
+    const R c12 = -psi * (third + uy2) * ux;
+    const R c22 = ninth * p + third * psi * (ux2 + uy2) + psi * ux2 * uy2;
+    // back to raw moments about 0 (lower central moments: p, -psi u)
+    const R b2 = p - R(2) * psi, b3 = p - R(3) * psi, b4 = p - R(4) * psi;
+    R r20 = c20 + ux2 * b2;
+    R r02 = c02 + uy2 * b2;
+    R r11 = cP + uxy * b2;
+    R r21 = c21 + uy * c20 + R(2) * ux * cP + ux2 * uy * b3;
+    R r12 = c12 + ux * c02 + R(2) * uy * cP + ux * uy2 * b3;
+    R r22 = c22 + R(2) * (uy * c21 + ux * c12) + uy2 * c20 + ux2 * c02 + R(4) * uxy * cP
+            + ux2 * uy2 * b4;
+    // sources: sigma' (Gamma^t + Gamma^p matched, truncated), h-hat_0..2 and delta g^s
     const R G00 = m.Fpx * ux + m.Fpy * uy;
-    const R s10 = m.Ftx * third, s01 = m.Fty * third;
-    const R s20 = R(2) * third * (m.Ftx + m.Fpx) * ux + third * G00;
-    const R s02 = R(2) * third * (m.Fty + m.Fpy) * uy + third * G00;
-    const R s11 = third * ((m.Ftx + m.Fpx) * uy + (m.Fty + m.Fpy) * ux);
-    const R half_om = R(1) - R(0.5) * om;
-
-    R c[9];
-    // h-hat_0..2 with omega = 1, plus m-hat^s'_j / |K_j|^2 (|K|^2 = 9, 6, 6, 36, 4, 4, 12, 12, 36)
-    const R h0 = G00 * R(1.0 / 18.0);
-    const R h1 = s10 * R(1.0 / 12.0);
-    const R h2 = s01 * R(1.0 / 12.0);
-    const R h3 = (R(2) * p * third + rc2 * (ux2 + uy2) - (e20 + e02)) * R(1.0 / 12.0);
-    const R h4 = R(0.25) * om * (rc2 * (ux2 - uy2) - (e20 - e02));
-    const R h5 = R(0.25) * om * (rc2 * ux * uy - e11);
-    const R h6 = R(0.25) * (third * uy * (psi + R(2) * rho * ux2) + e21 - uy * e20 - R(2) * ux * e11)
-                 - uy * (R(1.5) * h3 + R(0.5) * h4) - R(2) * ux * h5;
-    const R h7 = R(0.25) * (third * ux * (psi + R(2) * rho * uy2) + e12 - R(2) * uy * e11 - ux * e02)
-                 - ux * (R(1.5) * h3 - R(0.5) * h4) - R(2) * uy * h5;
-    const R eq22 = third * third * p + third * psi * (ux2 + uy2) + R(3) * rc2 * ux2 * uy2;
-    const R h8 = R(0.25) * (eq22 - e22 + R(2) * (uy * e21 + ux * e12) - (uy2 * e20 + ux2 * e02)
-                            - R(4) * ux * uy * e11)
-                 - R(2) * h3 - R(0.5) * uy2 * (R(3) * h3 + h4) - R(0.5) * ux2 * (R(3) * h3 - h4)
-                 - R(4) * ux * uy * h5 - R(2) * uy * h6 - R(2) * ux * h7;
-
-    const R m0 = R(0.5) * G00;
-    const R m1 = R(0.5) * s10;
-    const R m2 = R(0.5) * s01;
-    const R m3 = R(0.5) * (R(3) * (s20 + s02) - R(4) * G00);
-    const R m4 = half_om * (s20 - s02);
-    const R m5 = half_om * s11;
-    const R m6 = s01;   // (1 - 1/2)(2 sigma'_01), sigma'_21 = 0
-    const R m7 = s10;
-    const R m8 = R(0.5) * (R(4) * G00 - R(6) * (s20 + s02));
-    c[0] = h0 + m0 * R(1.0 / 9.0);
-    c[1] = h1 + m1 * R(1.0 / 6.0);
-    c[2] = h2 + m2 * R(1.0 / 6.0);
-    c[3] = h3 + m3 * R(1.0 / 36.0);
-    c[4] = h4 + m4 * R(0.25);
-    c[5] = h5 + m5 * R(0.25);
-    c[6] = h6 + m6 * R(1.0 / 12.0);
-    c[7] = h7 + m7 * R(1.0 / 12.0);
-    c[8] = h8 + m8 * R(1.0 / 36.0);
-    apply_basis(g, c);
+    const R Ftx = m.Ftx, Fty = m.Fty;
+    const R s20 = R(2) * third * (Ftx + m.Fpx) * ux + third * G00;
+    const R s02 = R(2) * third * (Fty + m.Fpy) * uy + third * G00;
+    const R s11 = third * ((Ftx + m.Fpx) * uy + (Fty + m.Fpy) * ux);
+    const R kq = R(0.25) * (R(1) - om) * (s20 - s02);   // (1/2 - omega/2)(s20 - s02)/2
+    r20 += third * G00 + R(0.5) * s20 + kq;
+    r02 += third * G00 + R(0.5) * s02 - kq;
+    r11 += (R(1) - R(0.5) * om) * s11;
+    r21 += third * third * Fty;
+    r12 += third * third * Ftx;
+    r22 += R(2) * ninth * G00;
+    const R r00 = pstar + G00;
+    const R r10 = rc2 * ux + R(0.5) * third * Ftx;
+    const R r01 = rc2 * uy + R(0.5) * third * Fty;
+    raw_to_pop_fast(r00, r10, r01, r20, r02, r11, r21, r12, r22, g);
 }
 
-// Interface-lattice collision (Sec. 5): g-hat_1..8 with the sharpening flux M_phi theta n in the
-// first-order equilibria; omega^phi_{1,2} from M_phi, all other rates 1.  phi = sum f (the
-// node's zeroth moment, already formed for the stencil window).
+// Interface-lattice collision (Sec. 5), evaluated in raw-moment space: the cascaded operator
+// relaxes the first-order central moments towards M_phi theta n at omega^phi_{1,2} and sets all
+// higher central moments to their equilibria (rates 1): c20 = c02 = c^2 phi, c22 = c^4 phi,
+// c11 = c21 = c12 = 0.  The closed-form g-hat of Sec. 5 is exactly this relaxation.  phi = sum f
+// (the node's zeroth moment, already formed for the stencil window).
 template <typename R>
-__device__ __forceinline__ void collide_ace(R f[9], R phi, const Macro<R>& m, R omega_phi_6)
+__device__ __forceinline__ void collide_ace(R f[9], R phi, const Macro<R>& m, R omega_phi)
 {
-    const R third = R(1) / R(3);
+    const R third = R(1) / R(3), ninth = R(1) / R(9);
     const R ux = m.ux, uy = m.uy;
     const R ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
-    const R d = (f[5] + f[6]) + (f[7] + f[8]);
     const R k10 = (f[1] - f[3]) + (f[5] - f[6]) - (f[7] - f[8]);
     const R k01 = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-    const R k20 = f[1] + f[3] + d;
-    const R k02 = f[2] + f[4] + d;
-    const R k11 = (f[5] - f[6]) + (f[7] - f[8]);
-    const R k21 = (f[5] + f[6]) - (f[7] + f[8]);
-    const R k12 = (f[5] - f[6]) - (f[7] - f[8]);
-    const R k22 = d;
-
-    R g[9];
-    g[0] = R(0);
-    g[1] = omega_phi_6 * (phi * ux + m.jx - k10);
-    g[2] = omega_phi_6 * (phi * uy + m.jy - k01);
-    g[3] = (R(2) * third * phi - (ux2 + uy2) * phi - (k20 + k02) + R(2) * (ux * k10 + uy * k01))
-               * R(1.0 / 12.0)
-           + ux * g[1] + uy * g[2];
-    g[4] = R(0.25) * (-(ux2 - uy2) * phi - (k20 - k02) + R(2) * (ux * k10 - uy * k01))
-           + R(3) * (ux * g[1] - uy * g[2]);
-    g[5] = R(0.25) * (-uxy * phi - k11 + ux * k01 + uy * k10) + R(1.5) * (ux * g[2] + uy * g[1]);
-    g[6] = R(0.25) * (-ux * uxy * phi + k21 - uy * k20 - R(2) * ux * k11 + R(2) * uxy * k10
-                      + ux2 * k01)
-           + R(3) * uxy * g[1] + (R(1.5) * ux2 + R(1)) * g[2] - R(1.5) * uy * g[3]
-           - R(0.5) * uy * g[4] - R(2) * ux * g[5];
-    g[7] = R(0.25) * (-uxy * uy * phi + k12 - ux * k02 - R(2) * uy * k11 + R(2) * uxy * k01
-                      + uy2 * k10)
-           + (R(1.5) * uy2 + R(1)) * g[1] + R(3) * uxy * g[2] - R(1.5) * ux * g[3]
-           + R(0.5) * ux * g[4] - R(2) * uy * g[5];
-    g[8] = R(0.25) * (third * third * phi - k22 + R(2) * (ux * k12 + uy * k21)
-                      - (uy2 * k20 + ux2 * k02) - R(4) * uxy * k11
-                      + R(2) * uxy * (uy * k10 + ux * k01) - uxy * uxy * phi)
-           + ux * (R(2) + R(3) * uy2) * g[1] + uy * (R(2) + R(3) * ux2) * g[2]
-           - (R(2) + R(1.5) * (ux2 + uy2)) * g[3] + R(0.5) * (ux2 - uy2) * g[4]
-           - R(4) * uxy * g[5] - R(2) * uy * g[6] - R(2) * ux * g[7];
-    apply_basis(f, g);
+    const R c10 = k10 - ux * phi, c01 = k01 - uy * phi;
+    const R a = c10 + omega_phi * (m.jx - c10);
+    const R b = c01 + omega_phi * (m.jy - c01);
+    const R cp = third * phi;
+    const R r10 = a + ux * phi;
+    const R r01 = b + uy * phi;
+    const R r20 = cp + R(2) * ux * a + ux2 * phi;
+    const R r02 = cp + R(2) * uy * b + uy2 * phi;
+    const R r11 = ux * b + uy * a + uxy * phi;
+    const R r21 = uy * cp + R(2) * uxy * a + ux2 * b + ux2 * uy * phi;
+    const R r12 = ux * cp + R(2) * uxy * b + uy2 * a + ux * uy2 * phi;
+    const R r22 = ninth * phi + (ux2 + uy2) * cp + R(2) * uxy * (uy * a + ux * b)
+                  + ux2 * uy2 * phi;
+    raw_to_pop_fast(phi, r10, r01, r20, r02, r11, r21, r12, r22, f);
 }
 
 // Populations from the nine raw moments (00,10,01,20,02,11,21,12,22) of D2Q9, closed form.

@@ -297,8 +297,8 @@ step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R
         const R jgy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
         Macro<R> m;
         node_macro<R>(ph, ps, jgx, jgy, xf, R(y), K, m);
-        collide_fluid<R>(g, m);
-        collide_ace<R>(f, ph.c, m, K.omega_phi_6);
+        collide_fluid<R>(g, ps.c, m);
+        collide_ace<R>(f, ph.c, m, K.omega_phi);
 
         // push to x + e_a: rows y-1, y, y+1 and columns x-1, x, x+1 of the other buffer
         int ym = y - 1, yp = y + 1;
