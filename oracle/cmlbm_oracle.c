@@ -28,7 +28,10 @@
  *   R4  kappa-tilde = (3/2) sigma W (the coefficient that makes the integral of
  *       kappa-tilde |grad phi|^2 across the tanh profile equal sigma; Sec. 2).
  *   R5  curvature: |grad phi|^2 div n = |grad phi| (lap phi - n.H.n), H the Hessian of phi.
- *   R6  where |grad phi|^2 <= 1e-24, n = 0 and F_s = 0.
+ *   R6  n = grad phi / (|grad phi| + 1e-6): Sec. 2 leaves n undefined where grad phi vanishes;
+ *       the regularisation keeps rounding noise in the bulk phases (|grad phi| ~ 1e-7) from
+ *       setting the direction of the sharpening flux M theta n and of F_s, and changes n by
+ *       less than 1e-3 wherever |grad phi| > 1e-3.
  *   R7  F_p = -grad p* + c_s^2 (rho_A - rho_B) grad phi with p* = sum of the streamed g-bar
  *       (Sec. 3 Eq. netgradientpressureforce, Sec. 4 remark on grad rho).
  *   R8  no-slip walls: half-way bounce-back on both lattices; stencils use mirror ghosts.
@@ -52,6 +55,9 @@ static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
 /* c_s^2 = c_sphi^2 = 1/3, Sec. 5. */
 #define CS2 (1.0 / 3.0)
+
+/* Regularisation of the interface normal (reading R6). */
+#define NORMAL_EPS 1e-6
 
 typedef struct {
     int nx, ny;
@@ -419,14 +425,10 @@ static void node_macros(const orc_case* c, const double* phi, const double* pst,
 
     const double g2 = o->dphix * o->dphix + o->dphiy * o->dphiy;
     o->theta = 4.0 * ph * (1.0 - ph) / c->width;
-    o->Fsx = 0.0;
-    o->Fsy = 0.0;
-    o->nx = 0.0;
-    o->ny = 0.0;
-    if (g2 > 1e-24) {   /* R6 */
+    {   /* R6: regularised normal */
         const double gm = sqrt(g2);
-        o->nx = o->dphix / gm;
-        o->ny = o->dphiy / gm;
+        o->nx = o->dphix / (gm + NORMAL_EPS);
+        o->ny = o->dphiy / (gm + NORMAL_EPS);
         const double nHn = o->nx * o->nx * o->hxx + 2.0 * o->nx * o->ny * o->hxy
                            + o->ny * o->ny * o->hyy;
         const double T = c->T0 + c->gradT_x * x + c->gradT_y * y;

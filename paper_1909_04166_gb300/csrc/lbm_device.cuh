@@ -77,6 +77,12 @@ template <typename R> __device__ __forceinline__ R rcp_(R v) { return R(1) / v; 
 template <> __device__ __forceinline__ float rcp_<float>(float v) { return __fdividef(1.0f, v); }
 template <typename R> __device__ __forceinline__ R rsqrt_(R v) { return R(1) / sqrt(v); }
 template <> __device__ __forceinline__ float rsqrt_<float>(float v) { return rsqrtf(v); }
+// sqrt(v) for v >= 0: exact in double; v * rsqrt(v) in float (0 for v = 0)
+template <typename R> __device__ __forceinline__ R norm_(R v) { return sqrt(v); }
+template <> __device__ __forceinline__ float norm_<float>(float v)
+{
+    return v * rsqrtf(fmaxf(v, 1e-37f));
+}
 
 // Macroscopic quantities of one node that the collisions need.
 template <typename R>
@@ -106,19 +112,18 @@ __device__ __forceinline__ void node_macro(const Win<R>& ph, const Win<R>& ps, R
     lap_hess(ph, lap, hxx, hyy, hxy);
     grad_iso(ps, dpx, dpy);
 
-    // where |grad phi|^2 <= 1e-24 the normal and the surface force are zero (branch-free)
+    // regularised normal n = grad phi / (|grad phi| + 1e-6): defined everywhere, and rounding
+    // noise in the bulk phases cannot set its direction
     const R g2 = dphx * dphx + dphy * dphy;
-    const bool has_n = g2 > R(1e-24);
-    const R ig = has_n ? rsqrt_(g2) : R(0);
-    const R g2m = has_n ? g2 : R(0);
-    const R gm = g2m * ig;
+    const R gm = norm_(g2);
+    const R ig = rcp_(gm + R(1e-6));
     const R nx = dphx * ig, ny = dphy * ig;
     const R nHn = nx * nx * hxx + R(2) * nx * ny * hxy + ny * ny * hyy;
     const R kt = K.kt0 + K.dktx * xf + K.dkty * yf;
     const R cap = -kt * gm * (lap - nHn);          // -kappa-tilde |grad phi|^2 div n
     const R nd = nx * K.dktx + ny * K.dkty;         // n . grad kappa-tilde
-    const R Fsx = cap * nx + g2m * (K.dktx - nx * nd);   // + |grad phi|^2 (I - n n) grad kappa-tilde
-    const R Fsy = cap * ny + g2m * (K.dkty - ny * nd);
+    const R Fsx = cap * nx + g2 * (K.dktx - nx * nd);   // + |grad phi|^2 (I - n n) grad kappa-tilde
+    const R Fsy = cap * ny + g2 * (K.dkty - ny * nd);
     const R dr = m.rho - K.rho_ref;
     m.Ftx = Fsx + dr * K.gx;
     m.Fty = Fsy + dr * K.gy;

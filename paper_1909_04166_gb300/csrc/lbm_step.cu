@@ -206,7 +206,8 @@ step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R
     const bool active = lane < w;
     const int x = active ? x0 + lane : x0 + wlast;   // idle lanes shadow the last column
     const int xl = map_col(x0 - 1, G), xr = map_col(x0 + w, G);
-    const long long row_elems = (long long)G.nstrips * TILE;
+    const int row_elems = G.nstrips * TILE;          // < 2^31 for nx <= 65536
+    auto row_ptr = [&](const S* base, int row) { return base + (long long)row * row_elems; };
 
     const int ys = seg * L.seg_h;
     const int ye = min(ys + L.seg_h, G.ny);
@@ -225,52 +226,47 @@ step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R
         hl = R(0);
         hr = R(0);
         if (hlane) {
-            const S* rb = src + (long long)row_of(k) * row_elems;
+            const S* rb = row_ptr(src, row_of(k));
             hl = static_cast<R>(__ldg(rb + hoffl));
             hr = static_cast<R>(__ldg(rb + hoffr));
         }
     };
 
-    uint32_t phase_bits = 0;   // parity of the next wait, per stage
+    // stage of row k is (k + 1) % NS; its barrier completes one phase per use, so the wait for
+    // row k expects parity ((k + 1) / NS) & 1
     int issued = -2;           // highest k whose tile copy was issued
-    auto stage_of = [&](int k) { return (k + 1) % NS; };
-    auto issue = [&](int k) {
+    auto issue = [&](int k, int st) {
         if (k > nrows) return;
         __syncwarp();
         if (lane == 0) {
-            const int s = stage_of(k);
             fence_proxy_async();
-            const uint32_t bar = bar0 + 8 * s;
+            const uint32_t bar = bar0 + 8 * st;
             mbar_expect_tx(bar, TILE * sizeof(S));
-            bulk_g2s(smem_u32(tiles + s * TILE),
-                     src + (long long)row_of(k) * row_elems + (long long)strip * TILE,
+            bulk_g2s(smem_u32(tiles + st * TILE), row_ptr(src, row_of(k)) + strip * TILE,
                      TILE * sizeof(S), bar);
         }
         issued = k;
     };
-    auto wait_k = [&](int k) -> bool {
-        const int s = stage_of(k);
-        if (!warp_wait(bar0 + 8 * s, (phase_bits >> s) & 1u)) return false;
-        phase_bits ^= 1u << s;
-        return true;
+    auto wait_k = [&](int k, int st) -> bool {
+        return warp_wait(bar0 + 8 * st, (uint32_t)(((k + 1) / NS) & 1));
     };
     // timeout: record the error, wait (bounded) for every copy still in flight, then return
     auto fail = [&](int k_failed) {
         if (lane == 0) atomicCAS(L.err, 0, 1);
-        for (int k = k_failed; k <= issued; ++k) wait_k(k);
+        for (int k = k_failed; k <= issued; ++k) wait_k(k, (k + 1) % NS);
     };
 
-    for (int k = -1; k <= NS - 2; ++k) issue(k);
+    for (int k = -1; k <= NS - 2; ++k) issue(k, (k + 1) % NS);
 
     Row3<R> rb, rc, rn;   // rows behind, current, ahead (in marching order)
     R hl, hr, hl2, hr2;
     halo_load(-1, hl, hr);
-    if (!wait_k(-1)) { fail(-1); return; }
-    window_row<R, S>(tiles + stage_of(-1) * TILE, lane, wlast, hl, hr, rb);
-    issue(NS - 1);
+    if (!wait_k(-1, 0)) { fail(-1); return; }
+    window_row<R, S>(tiles, lane, wlast, hl, hr, rb);
+    issue(NS - 1, 0);
     halo_load(0, hl, hr);
-    if (!wait_k(0)) { fail(0); return; }
-    window_row<R, S>(tiles + stage_of(0) * TILE, lane, wlast, hl, hr, rc);
+    if (!wait_k(0, 1)) { fail(0); return; }
+    window_row<R, S>(tiles + TILE, lane, wlast, hl, hr, rc);
     halo_load(1, hl2, hr2);
 
     // neighbour columns of this lane (periodic wrap; walls handled by bounce flags)
@@ -281,10 +277,13 @@ step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R
     const int cw = col_off(xm), cc = col_off(x), ce = col_off(xp);
     const bool xwall_warp = __any_sync(FULL, bxw || bxe);
     const R xf = R(x);
+    bool ok = true;
 
-    for (int i = 0; i < nrows; ++i) {
-        if (!wait_k(i + 1)) { fail(i + 1); return; }
-        window_row<R, S>(tiles + stage_of(i + 1) * TILE, lane, wlast, hl2, hr2, rn);
+    // one row of the march; st = stage of row i
+    auto body = [&](int i, int st) {
+        const int st1 = st + 1 == NS ? 0 : st + 1;       // stage of row i + 1
+        if (!wait_k(i + 1, st1)) { fail(i + 1); ok = false; return; }
+        window_row<R, S>(tiles + st1 * TILE, lane, wlast, hl2, hr2, rn);
         if (i + 2 <= nrows) halo_load(i + 2, hl2, hr2);
 
         const int y = up ? ys + i : ye - 1 - i;
@@ -292,7 +291,7 @@ step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R
         if (up) make_window(rb, rc, rn, ph, ps);
         else make_window(rn, rc, rb, ph, ps);
         R g[9], f[9];
-        ld_pops_t<S, R>(tiles + stage_of(i) * TILE, lane, g, f);
+        ld_pops_t<S, R>(tiles + st * TILE, lane, g, f);
         const R jgx = (g[1] - g[3]) + (g[5] - g[6]) - (g[7] - g[8]);
         const R jgy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
         Macro<R> m;
@@ -305,9 +304,9 @@ step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R
         const bool bys = ym < 0 && G.wall_y, byn = yp >= G.ny && G.wall_y;
         if (ym < 0) ym += G.ny;
         if (yp >= G.ny) yp -= G.ny;
-        S* rS = dst + (long long)ym * row_elems;
-        S* rC = dst + (long long)y * row_elems;
-        S* rN = dst + (long long)yp * row_elems;
+        S* rS = const_cast<S*>(row_ptr(dst, ym));
+        S* rC = const_cast<S*>(row_ptr(dst, y));
+        S* rN = const_cast<S*>(row_ptr(dst, yp));
         S* pc = rC + cc;
         S* p[9] = {pc, rC + ce, rN + cc, rC + cw, rS + cc, rN + ce, rN + cw, rS + cw, rS + ce};
         const bool bnc[9] = {false, bxe, byn, bxw, bys, bxe || byn, bxw || byn, bxw || bys,
@@ -329,9 +328,16 @@ step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R
                 q[(9 + a) * 32] = static_cast<S>(f[a]);
             }
         }
-        issue(i + NS);          // the tile of row i is consumed: refill its stage
+        issue(i + NS, st);      // the tile of row i is consumed: refill its stage
         rb = rc;
         rc = rn;
+    };
+
+    // a rolled loop: unrolling by the stage count makes the stages literals but the larger body
+    // misses in the instruction cache (measured slower)
+    for (int i = 0, st = 1; i < nrows; ++i, st = (st + 1 == NS ? 0 : st + 1)) {
+        body(i, st);
+        if (!ok) return;
     }
 }
 

@@ -67,7 +67,7 @@ def test_flat_interface_keeps_tanh_profile():
     the steady deviation falls like 1/W^2 and the slab stays at rest."""
     errs = []
     for width in (4.0, 8.0):
-        case = W.flat(nx=4, ny=64, width=width, mobility=0.05, rho_ratio=10.0)
+        case = W.flat(nx=4, ny=int(16 * width), width=width, mobility=0.05, rho_ratio=10.0)
         _, _, _, fl = run_case(case, 2000)
         errs.append(np.abs(fl["phi"] - case["fields"]["phi"]).max())
         assert errs[-1] < 0.11 / width ** 2
