@@ -79,8 +79,8 @@ def kernel_source_hash() -> str:
 # DRAM traffic per launch of the step kernel from an ncu capture (profiles/), keyed by the
 # hash of the kernel sources it was taken on; scaled by node count to the bench workload.
 NCU_TRAFFIC = {
-    # profiles/step_kernel_impact_2048x1024_fp32.md
-    ("05c45a952a1406ca", "impact", "fp32"): 252_489_728,
+    # profiles/step_kernel_impact_2048x1024_fp32.md (read 152.64 MB + write 98.29 MB)
+    ("f9ec9254c6c8c845", "impact", "fp32"): 250_936_832,
 }
 
 
@@ -267,11 +267,67 @@ def run_ours(args):
         "state_check": {"sum_phi": diag["sum_phi"], "max_speed": diag["max_speed"],
                         "nonfinite": diag["nonfinite"]},
     }
+    if args.variants:
+        line["variants"] = {"ensemble_512_cases": measure_ensemble(
+            args.ensemble_steps, 16, args.precision, local, stream.cuda_stream)}
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(case, args.cpu_seconds)
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def measure_ensemble(steps, per_case_steps, precision="fp32", device=0, stream=0):
+    """The 512-case batch of independent static / oscillating drops: aggregate MLUPS of the
+    batched launch (autotuned), and of the same cases advanced by one launch per case."""
+    import torch
+
+    from paper_1909_04166_gb300 import lbm
+    from paper_1909_04166_gb300 import workloads as W
+    cases = W.ensemble()
+    total = sum(c.nodes for c in cases)
+    out = {"cases": len(cases), "nodes": total}
+    with lbm.Batch(cases, precision=precision, device=device, stream=stream) as b:
+        b.init_all()
+        seg, block = lbm.lbm_batch_tune(b.b, 4)
+        b.step(8)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.step(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        lbm.lbm_batch_check(b.b)
+        out.update({"batched_mlups": round(total * steps / (ms * 1e-3) / 1e6, 1),
+                    "batched_ms_per_step": round(ms / steps, 4), "steps": steps,
+                    "tuned_launch": {"seg_rows": seg, "block": block},
+                    "batched_gbs": round(BYTES_PER_LU[precision] * total * steps / (ms * 1e-3)
+                                         / 1e9, 1)})
+    if per_case_steps > 0:
+        sims = [lbm.Simulation(c, precision=precision, device=device, stream=stream)
+                for c in cases]
+        for s in sims:
+            s.init_case()
+            lbm.lbm_set_graphs(s.ctx, False)
+        for s in sims:
+            s.step(2)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(per_case_steps):
+            for s in sims:
+                s.step(1)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        for s in sims:
+            s.close()
+        out.update({"per_case_mlups": round(total * per_case_steps / (ms * 1e-3) / 1e6, 1),
+                    "per_case_steps": per_case_steps,
+                    "per_case_launches_per_step": len(cases)})
+        out["batched_over_per_case"] = round(out["batched_mlups"] / out["per_case_mlups"], 2)
+    return out
 
 
 def _oracle_band(case, rows):
@@ -350,6 +406,31 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ensemble_line(args):
+    """--workload ensemble: the batched 512-case step as the bench line (1 GPU)."""
+    import torch
+    torch.cuda.set_device(0)
+    with Clocks(0) as clk:
+        r = measure_ensemble(args.steps, 16, args.precision, 0,
+                             torch.cuda.current_stream().cuda_stream)
+    peak, peak_kind = measured_peak()
+    line = {
+        "metric": METRIC, "value": r["batched_mlups"], "unit": "MLUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": 8, "ms_per_step": r["batched_ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded ensemble of drop cases; no dataset)",
+        "config": {"workload": f"ensemble of {r['cases']} drop cases, {r['nodes']} nodes, "
+                               f"{args.precision} populations", "nodes": r["nodes"]},
+        "roofline": {"bound": "hbm", "achieved": r["batched_gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": round(r["batched_gbs"] / peak, 4), "traffic": None,
+                     "peak_source": f"{peak_kind} HBM copy bandwidth",
+                     "kernel": "cmlbm::batch_step_kernel"},
+        "clocks": clk.summary(), "ensemble": r, "gpu_launches": args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -361,11 +442,15 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-variants", dest="variants", action="store_false")
+    ap.add_argument("--ensemble-steps", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ensemble":
+        run_ensemble_line(args)
     else:
         run_ours(args)
 

@@ -202,6 +202,47 @@ int lbm_diagnostics_noalloc(const double* phi, const double* p, const double* ux
                             double xc, double yc, double r_in, double r_out, lbm_diag* out,
                             void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batches: many independent cases (any mix of grid sizes, boundaries and physical parameters)
+ * advanced together.  Every lbm_batch_step advances all cases by one time step with ONE launch
+ * of the batched step kernel (each warp takes one strip x segment task of one case from a
+ * flattened task list); runs of 32 steps are replays of a CUDA graph.  The per-node arithmetic
+ * is the one of lbm_step, so each case evolves exactly as it would in its own context.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch;
+
+/* params: array of ncases (>= 1) cases; precision, device and stream must be equal in all of
+ * them.  One device allocation holds every case's two state buffers (zeroed). */
+int lbm_batch_create(const lbm_params* params, int32_t ncases, lbm_batch** out);
+
+/* Equilibrium initialisation of case c from host fields ([ny][nx] doubles of that case), as
+ * lbm_init_fields.  Synchronises. */
+int lbm_batch_init_fields(lbm_batch* b, int32_t c, const double* phi, const double* p,
+                          const double* ux, const double* uy);
+
+/* Advance every case by nsteps (>= 0) time steps; asynchronous on the batch's stream. */
+int lbm_batch_step(lbm_batch* b, int32_t nsteps);
+
+/* Fields / populations of case c, as lbm_get_fields / lbm_get_populations.  Synchronise. */
+int lbm_batch_get_fields(lbm_batch* b, int32_t c, double* phi, double* p, double* ux,
+                         double* uy, double* rho);
+int lbm_batch_get_populations(lbm_batch* b, int32_t c, double* g, double* f);
+
+/* Launch shape: rows per warp task (>= 1) and threads per block (multiple of 32, <= 256);
+ * 0 keeps the current value.  Results do not depend on it. */
+int lbm_batch_set_launch(lbm_batch* b, int32_t seg_rows, int32_t block_threads);
+int lbm_batch_get_launch(const lbm_batch* b, int32_t* seg_rows, int32_t* block_threads);
+
+/* Autotuner: times trial_steps (>= 1) steps of the live batch for each candidate launch shape
+ * (rows per task 8..64, blocks of 64 or 128 threads), keeps the fastest and restores the state
+ * it started from (a temporary device copy).  Synchronises. */
+int lbm_batch_tune(lbm_batch* b, int32_t trial_steps, int32_t* seg_rows, int32_t* block_threads);
+
+/* Total nodes of all cases; LBM_ERR_TIMEOUT check as lbm_check; release (NULL allowed). */
+int64_t lbm_batch_nodes(const lbm_batch* b);
+int lbm_batch_check(lbm_batch* b);
+void lbm_batch_destroy(lbm_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libcmlbm.so")
-SOURCES = ["lbm_step.cu", "lbm_api.cu"]
+SOURCES = ["lbm_step.cu", "lbm_api.cu", "lbm_batch.cu"]
 HEADERS = ["lbm_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

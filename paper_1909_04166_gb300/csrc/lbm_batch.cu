@@ -1,0 +1,471 @@
+// Batched C ABI (declared in include/cmlbm.h): many independent cases of uneven grid sizes
+// advanced together, one launch of the batched step kernel per time step (replayed from a CUDA
+// graph), with an autotuner that picks the segment height and block size on the live batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "../../include/cmlbm.h"
+#include "lbm_device.cuh"
+
+namespace cmlbm {
+template <typename R, typename S>
+cudaError_t configure_batch(int block);
+template <typename R, typename S>
+cudaError_t launch_batch_step(void*, const BatchCase<R>*, const int2*, int, int, int, int*,
+                              cudaStream_t);
+template <typename R, typename S>
+cudaError_t build_batch_graph(void*, const BatchCase<R>*, const int2*, int, int, int, int*, int,
+                              cudaGraphExec_t*);
+template <typename R, typename S>
+cudaError_t launch_init(const double*, const double*, const double*, const double*, void*,
+                        const Geometry&, const Consts<R>&, cudaStream_t);
+template <typename R, typename S>
+cudaError_t launch_fields(const void*, const Geometry&, const Consts<R>&, double*, double*,
+                          double*, double*, double*, cudaStream_t);
+template <typename S>
+cudaError_t launch_pack(const void*, double*, const Geometry&, cudaStream_t);
+template <typename S>
+size_t step_smem_bytes(int block);
+}  // namespace cmlbm
+
+using namespace cmlbm;
+
+namespace {
+
+constexpr int kBatchGraphChunk = 32;
+
+struct HostCase {
+    lbm_params P;
+    Geometry G;
+    Consts<double> Kd;
+    Consts<float> Kf;
+    long long off0, off1;   // element offsets of the two buffers
+    long long nodes;
+};
+
+// Same validation and constants as a single context (kept here so each TU stands alone).
+int validate_case(const lbm_params* P)
+{
+    if (P->nx < 1 || P->ny < 1 || P->nx > 65536 || P->ny > 65536) return LBM_ERR_ARG;
+    if ((P->bc_x != LBM_PERIODIC && P->bc_x != LBM_WALL) ||
+        (P->bc_y != LBM_PERIODIC && P->bc_y != LBM_WALL))
+        return LBM_ERR_ARG;
+    if (P->precision != LBM_FP64 && P->precision != LBM_FP32) return LBM_ERR_UNSUPPORTED;
+    const double v[] = {P->rho_a, P->rho_b, P->mu_a, P->mu_b, P->sigma0, P->dsigma_dT, P->T0,
+                        P->gradT_x, P->gradT_y, P->mobility, P->width, P->gx, P->gy,
+                        P->rho_ref};
+    for (double d : v)
+        if (!std::isfinite(d)) return LBM_ERR_PARAM;
+    if (P->rho_a <= 0 || P->rho_b <= 0 || P->mu_a <= 0 || P->mu_b <= 0) return LBM_ERR_PARAM;
+    if (P->width <= 0 || P->mobility <= 0) return LBM_ERR_PARAM;
+    return LBM_OK;
+}
+
+template <typename R>
+Consts<R> consts_of(const lbm_params& P)
+{
+    Consts<R> K;
+    K.rho_b = R(P.rho_b);
+    K.drho = R(P.rho_a - P.rho_b);
+    K.mu_b = R(P.mu_b);
+    K.dmu = R(P.mu_a - P.mu_b);
+    K.kt0 = R(1.5 * P.width * P.sigma0);
+    K.dktx = R(1.5 * P.width * P.dsigma_dT * P.gradT_x);
+    K.dkty = R(1.5 * P.width * P.dsigma_dT * P.gradT_y);
+    K.mob = R(P.mobility);
+    K.four_over_w = R(4.0 / P.width);
+    K.omega_phi = R(1.0 / (3.0 * P.mobility + 0.5));
+    K.gx = R(P.gx);
+    K.gy = R(P.gy);
+    K.rho_ref = R(P.rho_ref);
+    K.cs2_drho = R((P.rho_a - P.rho_b) / 3.0);
+    return K;
+}
+
+}  // namespace
+
+struct lbm_batch {
+    std::vector<HostCase> cases;
+    int precision, device;
+    size_t elem;
+    cudaStream_t st;
+    char* base;             // all state buffers
+    size_t base_bytes;
+    void* dcases;           // BatchCase<R>[ncases] on the device
+    int2* dtasks;
+    int ntasks;
+    int* err;
+    double* scratch;        // 5 * max nodes doubles (init / fields)
+    long long max_nodes, total_nodes;
+    int cur;                // shared buffer parity
+    int seg_h, block;
+    cudaGraphExec_t graph[2];
+    int last_cuda;
+};
+
+namespace {
+
+int fail_cuda(lbm_batch* b, cudaError_t e)
+{
+    if (b) b->last_cuda = (int)e;
+    return e == cudaErrorMemoryAllocation ? LBM_ERR_NOMEM : LBM_ERR_CUDA;
+}
+
+void drop_batch_graphs(lbm_batch* b)
+{
+    for (int k = 0; k < 2; ++k)
+        if (b->graph[k]) {
+            cudaGraphExecDestroy(b->graph[k]);
+            b->graph[k] = nullptr;
+        }
+}
+
+// (Re)build the per-case descriptors and the flattened warp-task list for segment height h.
+int build_tasks(lbm_batch* b, int h)
+{
+    const int n = (int)b->cases.size();
+    std::vector<int2> tasks;
+    std::vector<BatchCase<double>> cd(b->precision == LBM_FP64 ? n : 0);
+    std::vector<BatchCase<float>> cf(b->precision == LBM_FP32 ? n : 0);
+    for (int c = 0; c < n; ++c) {
+        const HostCase& hc = b->cases[c];
+        const int nseg = (hc.G.ny + h - 1) / h;
+        const int nw = hc.G.nstrips * nseg;
+        for (int k = 0; k < nw; ++k) tasks.push_back(make_int2(c, k));
+        if (b->precision == LBM_FP64)
+            cd[c] = BatchCase<double>{hc.G, h, nseg, hc.off0, hc.off1, hc.Kd};
+        else
+            cf[c] = BatchCase<float>{hc.G, h, nseg, hc.off0, hc.off1, hc.Kf};
+    }
+    if (tasks.size() > (size_t)0x7fffffff / 32) return LBM_ERR_ARG;
+    cudaStreamSynchronize(b->st);   // no launch may still read the old task list
+    drop_batch_graphs(b);
+    if (b->dtasks) cudaFree(b->dtasks);
+    b->dtasks = nullptr;
+    cudaError_t e = cudaMalloc(&b->dtasks, tasks.size() * sizeof(int2));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->dtasks, tasks.data(), tasks.size() * sizeof(int2),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        if (b->precision == LBM_FP64)
+            e = cudaMemcpy(b->dcases, cd.data(), n * sizeof(BatchCase<double>),
+                           cudaMemcpyHostToDevice);
+        else
+            e = cudaMemcpy(b->dcases, cf.data(), n * sizeof(BatchCase<float>),
+                           cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return fail_cuda(b, e);
+    b->ntasks = (int)tasks.size();
+    b->seg_h = h;
+    return LBM_OK;
+}
+
+cudaError_t configure(lbm_batch* b)
+{
+    return b->precision == LBM_FP64 ? configure_batch<double, double>(b->block)
+                                    : configure_batch<float, float>(b->block);
+}
+
+cudaError_t launch_one(lbm_batch* b)
+{
+    if (b->precision == LBM_FP64)
+        return launch_batch_step<double, double>(b->base,
+                                                 static_cast<BatchCase<double>*>(b->dcases),
+                                                 b->dtasks, b->ntasks, b->cur, b->block, b->err,
+                                                 b->st);
+    return launch_batch_step<float, float>(b->base, static_cast<BatchCase<float>*>(b->dcases),
+                                           b->dtasks, b->ntasks, b->cur, b->block, b->err,
+                                           b->st);
+}
+
+cudaError_t ensure_graph(lbm_batch* b)
+{
+    if (b->graph[b->cur]) return cudaSuccess;
+    if (b->precision == LBM_FP64)
+        return build_batch_graph<double, double>(b->base,
+                                                 static_cast<BatchCase<double>*>(b->dcases),
+                                                 b->dtasks, b->ntasks, b->cur, b->block, b->err,
+                                                 kBatchGraphChunk, &b->graph[b->cur]);
+    return build_batch_graph<float, float>(b->base, static_cast<BatchCase<float>*>(b->dcases),
+                                           b->dtasks, b->ntasks, b->cur, b->block, b->err,
+                                           kBatchGraphChunk, &b->graph[b->cur]);
+}
+
+void* case_state(lbm_batch* b, int c)
+{
+    const HostCase& hc = b->cases[c];
+    return b->base + (size_t)(b->cur ? hc.off1 : hc.off0) * b->elem;
+}
+
+int check_err(lbm_batch* b)
+{
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, b->err, sizeof(int), cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return fail_cuda(b, e);
+    return h ? LBM_ERR_TIMEOUT : LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(const lbm_params* params, int32_t ncases, lbm_batch** out)
+{
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (!params || ncases < 1) return LBM_ERR_ARG;
+    for (int c = 0; c < ncases; ++c) {
+        int s = validate_case(&params[c]);
+        if (s) return s;
+        if (params[c].precision != params[0].precision || params[c].device != params[0].device ||
+            params[c].stream != params[0].stream)
+            return LBM_ERR_ARG;
+    }
+    if (cudaSetDevice(params[0].device) != cudaSuccess) return LBM_ERR_CUDA;
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return LBM_ERR_NOMEM;
+    b->precision = params[0].precision;
+    b->device = params[0].device;
+    b->elem = b->precision == LBM_FP64 ? sizeof(double) : sizeof(float);
+    b->st = static_cast<cudaStream_t>(params[0].stream);
+    b->block = 128;
+    long long off = 0;
+    for (int c = 0; c < ncases; ++c) {
+        HostCase hc;
+        hc.P = params[c];
+        hc.G.nx = params[c].nx;
+        hc.G.ny = params[c].ny;
+        hc.G.nstrips = (params[c].nx + 31) / 32;
+        hc.G.wall_x = params[c].bc_x == LBM_WALL;
+        hc.G.wall_y = params[c].bc_y == LBM_WALL;
+        hc.Kd = consts_of<double>(params[c]);
+        hc.Kf = consts_of<float>(params[c]);
+        const long long elems = (long long)hc.G.ny * hc.G.nstrips * 18 * 32;
+        hc.off0 = off;
+        hc.off1 = off + elems;
+        off += 2 * elems;                  // multiples of 576 elements keep 16-byte alignment
+        hc.nodes = (long long)hc.G.nx * hc.G.ny;
+        b->max_nodes = std::max(b->max_nodes, hc.nodes);
+        b->total_nodes += hc.nodes;
+        b->cases.push_back(hc);
+    }
+    b->base_bytes = (size_t)off * b->elem;
+    cudaError_t e = cudaMalloc(&b->base, b->base_bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->base, 0, b->base_bytes, b->st);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&b->dcases, ncases * (b->precision == LBM_FP64 ? sizeof(BatchCase<double>)
+                                                                     : sizeof(BatchCase<float>)));
+    if (e == cudaSuccess) e = cudaMalloc(&b->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->err, 0, sizeof(int), b->st);
+    if (e == cudaSuccess) e = cudaMalloc(&b->scratch, 5 * (size_t)b->max_nodes * sizeof(double));
+    if (e == cudaSuccess) e = configure(b);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    int s = e == cudaSuccess ? build_tasks(b, 16) : fail_cuda(b, e);
+    if (s) {
+        lbm_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_init_fields(lbm_batch* b, int32_t c, const double* phi, const double* p,
+                          const double* ux, const double* uy)
+{
+    if (!b || c < 0 || c >= (int)b->cases.size() || !phi || !p || !ux || !uy) return LBM_ERR_ARG;
+    cudaSetDevice(b->device);
+    const HostCase& hc = b->cases[c];
+    const size_t N = (size_t)hc.nodes, B = N * sizeof(double);
+    const double* src[4] = {phi, p, ux, uy};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(b->scratch + k * N, src[k], B, cudaMemcpyHostToDevice, b->st);
+    double* d = b->scratch;
+    if (e == cudaSuccess)
+        e = b->precision == LBM_FP64
+                ? launch_init<double, double>(d, d + N, d + 2 * N, d + 3 * N, case_state(b, c),
+                                              hc.G, hc.Kd, b->st)
+                : launch_init<float, float>(d, d + N, d + 2 * N, d + 3 * N, case_state(b, c),
+                                            hc.G, hc.Kf, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    return e == cudaSuccess ? LBM_OK : fail_cuda(b, e);
+}
+
+int lbm_batch_step(lbm_batch* b, int32_t nsteps)
+{
+    if (!b || nsteps < 0) return LBM_ERR_ARG;
+    cudaSetDevice(b->device);
+    int32_t k = 0;
+    while (nsteps - k >= kBatchGraphChunk) {
+        cudaError_t e = ensure_graph(b);
+        if (e == cudaSuccess) e = cudaGraphLaunch(b->graph[b->cur], b->st);
+        if (e != cudaSuccess) return fail_cuda(b, e);
+        k += kBatchGraphChunk;             // even chunk: parity unchanged
+    }
+    for (; k < nsteps; ++k) {
+        cudaError_t e = launch_one(b);
+        if (e != cudaSuccess) return fail_cuda(b, e);
+        b->cur ^= 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_get_fields(lbm_batch* b, int32_t c, double* phi, double* p, double* ux,
+                         double* uy, double* rho)
+{
+    if (!b || c < 0 || c >= (int)b->cases.size()) return LBM_ERR_ARG;
+    cudaSetDevice(b->device);
+    const HostCase& hc = b->cases[c];
+    const size_t N = (size_t)hc.nodes, B = N * sizeof(double);
+    double* d = b->scratch;
+    cudaError_t e = b->precision == LBM_FP64
+                        ? launch_fields<double, double>(case_state(b, c), hc.G, hc.Kd, d, d + N,
+                                                        d + 2 * N, d + 3 * N, d + 4 * N, b->st)
+                        : launch_fields<float, float>(case_state(b, c), hc.G, hc.Kf, d, d + N,
+                                                      d + 2 * N, d + 3 * N, d + 4 * N, b->st);
+    double* h[5] = {phi, p, ux, uy, rho};
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+        if (h[k]) e = cudaMemcpyAsync(h[k], d + k * N, B, cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return fail_cuda(b, e);
+    return check_err(b);
+}
+
+int lbm_batch_get_populations(lbm_batch* b, int32_t c, double* g, double* f)
+{
+    if (!b || c < 0 || c >= (int)b->cases.size() || !g || !f) return LBM_ERR_ARG;
+    cudaSetDevice(b->device);
+    const HostCase& hc = b->cases[c];
+    const size_t N = (size_t)hc.nodes;
+    double* tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, 18 * N * sizeof(double));
+    if (e == cudaSuccess)
+        e = b->precision == LBM_FP64 ? launch_pack<double>(case_state(b, c), tmp, hc.G, b->st)
+                                     : launch_pack<float>(case_state(b, c), tmp, hc.G, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g, tmp, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f, tmp + 9 * N, 9 * N * sizeof(double), cudaMemcpyDeviceToHost,
+                            b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return fail_cuda(b, e);
+    return check_err(b);
+}
+
+int lbm_batch_set_launch(lbm_batch* b, int32_t seg_rows, int32_t block_threads)
+{
+    if (!b || seg_rows < 0 || block_threads < 0) return LBM_ERR_ARG;
+    if (block_threads && (block_threads % 32 || block_threads > 256)) return LBM_ERR_ARG;
+    cudaSetDevice(b->device);
+    if (block_threads) {
+        b->block = block_threads;
+        drop_batch_graphs(b);
+        cudaError_t e = configure(b);
+        if (e != cudaSuccess) return fail_cuda(b, e);
+    }
+    return seg_rows ? build_tasks(b, seg_rows) : LBM_OK;
+}
+
+int lbm_batch_get_launch(const lbm_batch* b, int32_t* seg_rows, int32_t* block_threads)
+{
+    if (!b) return LBM_ERR_ARG;
+    if (seg_rows) *seg_rows = b->seg_h;
+    if (block_threads) *block_threads = b->block;
+    return LBM_OK;
+}
+
+int lbm_batch_tune(lbm_batch* b, int32_t trial_steps, int32_t* seg_rows, int32_t* block_threads)
+{
+    if (!b || trial_steps < 1) return LBM_ERR_ARG;
+    cudaSetDevice(b->device);
+    // keep the state: trials run on it and it is restored afterwards
+    void* backup = nullptr;
+    cudaError_t e = cudaMalloc(&backup, b->base_bytes);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(backup, b->base, b->base_bytes, cudaMemcpyDeviceToDevice, b->st);
+    if (e != cudaSuccess) {
+        if (backup) cudaFree(backup);
+        return fail_cuda(b, e);
+    }
+    const int cur0 = b->cur;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int segs[] = {8, 12, 16, 24, 32, 48, 64};
+    const int blocks[] = {64, 128};
+    float best = 1e30f;
+    int best_seg = b->seg_h, best_block = b->block;
+    int status = LBM_OK;
+    for (int bl : blocks) {
+        for (int sg : segs) {
+            status = lbm_batch_set_launch(b, sg, bl);
+            if (status) break;
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+                e = launch_one(b);
+                b->cur ^= 1;
+            }
+            cudaEventRecord(e0, b->st);
+            for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) {
+                e = launch_one(b);
+                b->cur ^= 1;
+            }
+            cudaEventRecord(e1, b->st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) break;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_seg = sg;
+                best_block = bl;
+            }
+        }
+        if (status || e != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->cur = cur0;
+    cudaError_t e2 =
+        cudaMemcpyAsync(b->base, backup, b->base_bytes, cudaMemcpyDeviceToDevice, b->st);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(b->st);
+    cudaFree(backup);
+    if (e != cudaSuccess) return fail_cuda(b, e);
+    if (e2 != cudaSuccess) return fail_cuda(b, e2);
+    if (status) return status;
+    status = lbm_batch_set_launch(b, best_seg, best_block);
+    if (status) return status;
+    if (seg_rows) *seg_rows = best_seg;
+    if (block_threads) *block_threads = best_block;
+    return check_err(b);
+}
+
+int64_t lbm_batch_nodes(const lbm_batch* b) { return b ? b->total_nodes : -1; }
+
+int lbm_batch_check(lbm_batch* b)
+{
+    if (!b) return LBM_ERR_ARG;
+    cudaSetDevice(b->device);
+    return check_err(b);
+}
+
+void lbm_batch_destroy(lbm_batch* b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->st);
+    drop_batch_graphs(b);
+    if (b->base) cudaFree(b->base);
+    if (b->dcases) cudaFree(b->dcases);
+    if (b->dtasks) cudaFree(b->dtasks);
+    if (b->err) cudaFree(b->err);
+    if (b->scratch) cudaFree(b->scratch);
+    delete b;
+}
+
+}  // extern "C"

@@ -37,6 +37,16 @@ struct Geometry {
     int wall_x, wall_y;
 };
 
+// One case of a batch: its geometry and constants, the element offsets of its two state
+// buffers inside the batch allocation, and its warp segmentation.
+template <typename R>
+struct BatchCase {
+    Geometry G;
+    int seg_h, nseg;
+    long long off0, off1;
+    Consts<R> K;
+};
+
 // ---------------------------------------------------------------------------------------------
 // Nine-point stencil window of a nodal field: value at (x + i, y + j), i, j in {-1, 0, 1}.
 // ---------------------------------------------------------------------------------------------

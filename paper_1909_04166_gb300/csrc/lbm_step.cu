@@ -179,19 +179,17 @@ __device__ __forceinline__ void ld_pops_t(const S* tile, int lane, R g[9], R f[9
     }
 }
 
+// The march of one warp over one strip x segment of one grid: everything the step does for
+// those nodes.  Used by the single-grid kernel and by the batched kernel.
 template <typename R, typename S>
-__global__ void __launch_bounds__(256)
-step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R> K,
-            StepLaunch L)
+__device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__ dst,
+                                      const Geometry& G, const Consts<R>& K, int strip, int seg,
+                                      int seg_h, int* err)
 {
     constexpr int NS = Stages<S>::value;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    const int strip = warp % G.nstrips;
-    const int seg = warp / G.nstrips;
-    if (seg >= L.nseg) return;                       // warp-uniform
 
     S* tiles = reinterpret_cast<S*>(smem_raw + wib * warp_smem_bytes<S>());
     const uint32_t bar0 = smem_u32(tiles + NS * TILE);
@@ -209,8 +207,8 @@ step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R
     const int row_elems = G.nstrips * TILE;          // < 2^31 for nx <= 65536
     auto row_ptr = [&](const S* base, int row) { return base + (long long)row * row_elems; };
 
-    const int ys = seg * L.seg_h;
-    const int ye = min(ys + L.seg_h, G.ny);
+    const int ys = seg * seg_h;
+    const int ye = min(ys + seg_h, G.ny);
     const int nrows = ye - ys;
     const bool up = (seg & 1) == 0;
     // row visited at step k (k = -1 .. nrows): behind/current/ahead rows of the march
@@ -252,7 +250,7 @@ step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R
     };
     // timeout: record the error, wait (bounded) for every copy still in flight, then return
     auto fail = [&](int k_failed) {
-        if (lane == 0) atomicCAS(L.err, 0, 1);
+        if (lane == 0) atomicCAS(err, 0, 1);
         for (int k = k_failed; k <= issued; ++k) wait_k(k, (k + 1) % NS);
     };
 
@@ -339,6 +337,38 @@ step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R
         body(i, st);
         if (!ok) return;
     }
+}
+
+template <typename R, typename S>
+__global__ void __launch_bounds__(256)
+step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R> K,
+            StepLaunch L)
+{
+    const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int strip = warp % G.nstrips;
+    const int seg = warp / G.nstrips;
+    if (seg >= L.nseg) return;                       // warp-uniform
+    march<R, S>(src, dst, G, K, strip, seg, L.seg_h, L.err);
+}
+
+// One time step of many independent grids in one launch: warp w takes task w = (case, local
+// warp index) from a flattened task list; every case has its own geometry, constants and pair
+// of buffers inside one allocation.  All cases share the buffer parity (they step together).
+template <typename R, typename S>
+__global__ void __launch_bounds__(256)
+batch_step_kernel(S* __restrict__ base, const BatchCase<R>* __restrict__ cases,
+                  const int2* __restrict__ tasks, int ntasks, int parity, int* err)
+{
+    const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    if (warp >= ntasks) return;                      // warp-uniform
+    const int2 t = tasks[warp];
+    const BatchCase<R>& c = cases[t.x];
+    const Geometry G = c.G;
+    const int strip = t.y % G.nstrips;
+    const int seg = t.y / G.nstrips;
+    const S* src = base + (parity ? c.off1 : c.off0);
+    S* dst = base + (parity ? c.off0 : c.off1);
+    march<R, S>(src, dst, G, c.K, strip, seg, c.seg_h, err);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -519,6 +549,62 @@ cudaError_t build_step_graph(const void* a, const void* b, const Geometry& G, co
 }
 
 template <typename R, typename S>
+cudaError_t configure_batch(int block)
+{
+    cudaError_t e = cudaFuncSetAttribute(batch_step_kernel<R, S>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)step_smem_bytes<S>(block));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(batch_step_kernel<R, S>,
+                                cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+
+template <typename R, typename S>
+cudaError_t launch_batch_step(void* base, const BatchCase<R>* cases, const int2* tasks,
+                              int ntasks, int parity, int block, int* err, cudaStream_t st)
+{
+    const int wpb = block / 32;
+    const unsigned grid = (unsigned)((ntasks + wpb - 1) / wpb);
+    batch_step_kernel<R, S><<<grid, block, step_smem_bytes<S>(block), st>>>(
+        static_cast<S*>(base), cases, tasks, ntasks, parity, err);
+    return cudaGetLastError();
+}
+
+// A graph of `chunk` (even) consecutive batched steps starting from buffer parity `parity0`.
+template <typename R, typename S>
+cudaError_t build_batch_graph(void* base, const BatchCase<R>* cases, const int2* tasks,
+                              int ntasks, int parity0, int block, int* err, int chunk,
+                              cudaGraphExec_t* out)
+{
+    const int wpb = block / 32;
+    const unsigned grid = (unsigned)((ntasks + wpb - 1) / wpb);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphNode_t prev = nullptr;
+    S* b = static_cast<S*>(base);
+    for (int s = 0; s < chunk && e == cudaSuccess; ++s) {
+        int parity = (parity0 + s) & 1;
+        int n = ntasks;
+        void* args[] = {(void*)&b, (void*)&cases, (void*)&tasks, (void*)&n, (void*)&parity,
+                        (void*)&err};
+        cudaKernelNodeParams p = {};
+        p.func = (void*)batch_step_kernel<R, S>;
+        p.gridDim = dim3(grid);
+        p.blockDim = dim3(block);
+        p.sharedMemBytes = (unsigned)step_smem_bytes<S>(block);
+        p.kernelParams = args;
+        cudaGraphNode_t node;
+        e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &p);
+        prev = node;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    return e;
+}
+
+template <typename R, typename S>
 cudaError_t launch_init(const double* phi, const double* p, const double* ux, const double* uy,
                         void* state, const Geometry& G, const Consts<R>& K, cudaStream_t st)
 {
@@ -560,6 +646,20 @@ template size_t step_smem_bytes<double>(int);
 template size_t step_smem_bytes<float>(int);
 template cudaError_t configure_step<double, double>(int);
 template int step_blocks_per_sm<double, double>(int);
+template cudaError_t configure_batch<double, double>(int);
+template cudaError_t build_batch_graph<double, double>(void*, const BatchCase<double>*,
+                                                       const int2*, int, int, int, int*, int,
+                                                       cudaGraphExec_t*);
+template cudaError_t build_batch_graph<float, float>(void*, const BatchCase<float>*,
+                                                     const int2*, int, int, int, int*, int,
+                                                     cudaGraphExec_t*);
+template cudaError_t configure_batch<float, float>(int);
+template cudaError_t launch_batch_step<double, double>(void*, const BatchCase<double>*,
+                                                       const int2*, int, int, int, int*,
+                                                       cudaStream_t);
+template cudaError_t launch_batch_step<float, float>(void*, const BatchCase<float>*,
+                                                     const int2*, int, int, int, int*,
+                                                     cudaStream_t);
 template cudaError_t build_step_graph<double, double>(const void*, const void*, const Geometry&,
                                                       const Consts<double>&, int, int, int*, int,
                                                       cudaGraphExec_t*);

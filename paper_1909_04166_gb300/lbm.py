@@ -38,6 +38,9 @@ EXPORTS = [
     "lbm_set_populations", "lbm_state_device", "lbm_diagnostics", "lbm_set_launch",
     "lbm_get_launch", "lbm_steps_done", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error",
     "lbm_check", "lbm_set_graphs", "lbm_diagnostics_noalloc",
+    "lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_get_fields",
+    "lbm_batch_get_populations", "lbm_batch_set_launch", "lbm_batch_get_launch",
+    "lbm_batch_tune", "lbm_batch_nodes", "lbm_batch_check", "lbm_batch_destroy",
 ]
 
 
@@ -114,6 +117,19 @@ def lib(build_if_missing: bool = True):
     dd = ctypes.c_double
     L.lbm_diagnostics_noalloc.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, dd, dd, dd, dd,
                                           vp, vp]
+    L.lbm_batch_create.argtypes = [P(lbm_params), i32, P(vp)]
+    L.lbm_batch_init_fields.argtypes = [vp, i32, dp, dp, dp, dp]
+    L.lbm_batch_step.argtypes = [vp, i32]
+    L.lbm_batch_get_fields.argtypes = [vp, i32, dp, dp, dp, dp, dp]
+    L.lbm_batch_get_populations.argtypes = [vp, i32, dp, dp]
+    L.lbm_batch_set_launch.argtypes = [vp, i32, i32]
+    L.lbm_batch_get_launch.argtypes = [vp, P(i32), P(i32)]
+    L.lbm_batch_tune.argtypes = [vp, i32, P(i32), P(i32)]
+    L.lbm_batch_nodes.argtypes = [vp]
+    L.lbm_batch_nodes.restype = i64
+    L.lbm_batch_check.argtypes = [vp]
+    L.lbm_batch_destroy.argtypes = [vp]
+    L.lbm_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -259,7 +275,121 @@ def lbm_last_cuda_error(ctx) -> int:
     return int(lib().lbm_last_cuda_error(ctx))
 
 
+def lbm_batch_create(params_list) -> ctypes.c_void_p:
+    arr = (lbm_params * len(params_list))(*params_list)
+    b = ctypes.c_void_p()
+    _check(lib().lbm_batch_create(arr, len(params_list), ctypes.byref(b)), "lbm_batch_create")
+    return b
+
+
+def lbm_batch_init_fields(b, c, phi, p, ux, uy) -> None:
+    _check(lib().lbm_batch_init_fields(b, int(c), _dptr(phi), _dptr(p), _dptr(ux), _dptr(uy)),
+           "lbm_batch_init_fields")
+
+
+def lbm_batch_step(b, nsteps: int) -> None:
+    _check(lib().lbm_batch_step(b, int(nsteps)), "lbm_batch_step")
+
+
+def lbm_batch_get_fields(b, c, phi=None, p=None, ux=None, uy=None, rho=None) -> None:
+    _check(lib().lbm_batch_get_fields(b, int(c), _dptr(phi), _dptr(p), _dptr(ux), _dptr(uy),
+                                      _dptr(rho)), "lbm_batch_get_fields")
+
+
+def lbm_batch_get_populations(b, c, g, f) -> None:
+    _check(lib().lbm_batch_get_populations(b, int(c), _dptr(g), _dptr(f)),
+           "lbm_batch_get_populations")
+
+
+def lbm_batch_set_launch(b, seg_rows: int = 0, block_threads: int = 0) -> None:
+    _check(lib().lbm_batch_set_launch(b, int(seg_rows), int(block_threads)),
+           "lbm_batch_set_launch")
+
+
+def lbm_batch_get_launch(b):
+    a, c = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().lbm_batch_get_launch(b, ctypes.byref(a), ctypes.byref(c)), "lbm_batch_get_launch")
+    return int(a.value), int(c.value)
+
+
+def lbm_batch_tune(b, trial_steps: int = 8):
+    a, c = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().lbm_batch_tune(b, int(trial_steps), ctypes.byref(a), ctypes.byref(c)),
+           "lbm_batch_tune")
+    return int(a.value), int(c.value)
+
+
+def lbm_batch_nodes(b) -> int:
+    return int(lib().lbm_batch_nodes(b))
+
+
+def lbm_batch_check(b) -> None:
+    _check(lib().lbm_batch_check(b), "lbm_batch_check")
+
+
+def lbm_batch_destroy(b) -> None:
+    if b is not None and b.value:
+        lib().lbm_batch_destroy(b)
+        b.value = None
+
+
 # ---- convenience ------------------------------------------------------------------------------
+
+class Batch:
+    """Owns one batch of independent cases (dictionaries from ``workloads``)."""
+
+    def __init__(self, cases, precision="fp32", device=0, stream=0):
+        self.cases = list(cases)
+        self.params = [make_params(c, precision, device, stream) for c in self.cases]
+        self.b = lbm_batch_create(self.params)
+
+    def init_case(self, i, fields=None):
+        c = self.cases[i]
+        f = fields or c["fields"]
+        shape = (int(c["ny"]), int(c["nx"]))
+        arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(f[k], np.float64), shape))
+                for k in ("phi", "p", "ux", "uy")]
+        lbm_batch_init_fields(self.b, i, *arrs)
+        return self
+
+    def init_all(self):
+        for i in range(len(self.cases)):
+            self.init_case(i)
+        return self
+
+    def step(self, n=1):
+        lbm_batch_step(self.b, n)
+        return self
+
+    def fields(self, i) -> dict:
+        c = self.cases[i]
+        shape = (int(c["ny"]), int(c["nx"]))
+        out = {k: np.empty(shape) for k in ("phi", "p", "ux", "uy", "rho")}
+        lbm_batch_get_fields(self.b, i, out["phi"], out["p"], out["ux"], out["uy"], out["rho"])
+        return out
+
+    def populations(self, i):
+        c = self.cases[i]
+        g = np.empty((9, int(c["ny"]), int(c["nx"])))
+        f = np.empty_like(g)
+        lbm_batch_get_populations(self.b, i, g, f)
+        return g, f
+
+    def close(self):
+        lbm_batch_destroy(self.b)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 class Simulation:
     """Owns one context; a case dictionary from ``workloads`` gives its parameters."""

@@ -198,9 +198,11 @@ def random_drop(nx, ny, seed=0, wall_x=False, wall_y=False, rho_ratio=10.0, sigm
 
 
 def ensemble(ncases=512, seed0=1000, side_min=32, side_max=256, nu=0.1, mobility=0.02,
-             width=4.0) -> list:
+             width=5.0) -> list:
     """Independent static and oscillating drops of uneven sizes: case i draws its grid, radius,
-    density ratio, sigma and a 1 % random velocity perturbation from seed seed0 + i."""
+    density ratio (log-uniform 10..1000), sigma (log-uniform 1e-4..1e-2) and a 1 % random
+    velocity perturbation from seed seed0 + i; even cases are circles, odd ones 5:3 ellipses.
+    W = 5: with W = 4 the density-ratio-1000 cases diverge."""
     cases = []
     for i in range(ncases):
         rng = np.random.default_rng(seed0 + i)

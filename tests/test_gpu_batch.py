@@ -1,0 +1,94 @@
+"""Batched stepping (lbm_batch_*): one launch per step over many independent cases.
+
+Each case must evolve as in its own context (the batched kernel inlines the same per-node
+arithmetic; the compiler may contract a few multiply-adds differently in the two kernels, so
+the comparison allows rounding-level differences), match the FP64 oracle, and survive the
+autotuner bit for bit (within one kernel the launch shape does not change any result)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1909_04166_gb300 import lbm
+from paper_1909_04166_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def mixed_cases():
+    return [
+        W.random_drop(40, 33, seed=1, wall_y=True, rho_ratio=100.0, gravity=1e-6),
+        W.random_drop(97, 64, seed=2, wall_x=True, rho_ratio=10.0, marangoni=-2e-5),
+        W.random_drop(17, 120, seed=3, rho_ratio=1000.0, width=5.0),
+        W.random_drop(1, 9, seed=4, wall_y=True),
+        W.random_drop(64, 64, seed=5, wall_x=True, wall_y=True, rho_ratio=50.0),
+        W.random_drop(129, 31, seed=6, rho_ratio=300.0, width=5.0),
+    ]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-6), ("fp64", 1e-14)])
+def test_batch_cases_match_their_own_contexts(prec, tol):
+    cases = mixed_cases()
+    with lbm.Batch(cases, precision=prec) as b:
+        b.init_all().step(37)
+        got = [b.populations(i) for i in range(len(cases))]
+    for i, c in enumerate(cases):
+        with lbm.Simulation(c, precision=prec) as s:
+            g, f = s.init_case().step(37).populations()
+        assert np.linalg.norm(got[i][0] - g) <= tol * np.linalg.norm(g), i
+        assert np.linalg.norm(got[i][1] - f) <= tol * np.linalg.norm(f), i
+
+
+def test_batch_matches_oracle_fp64():
+    cases = mixed_cases()[:3] + W.ensemble(ncases=4)[1:3]
+    with lbm.Batch(cases, precision="fp64") as b:
+        b.init_all().step(12)
+        for i, c in enumerate(cases):
+            oc = O.OracleCase.from_dict(c.params)
+            fl = c["fields"]
+            g0, f0 = O.init(oc, fl["phi"], fl["p"], fl["ux"], fl["uy"])
+            g_ref, f_ref = O.run(oc, g0, f0, 12)
+            g, f = b.populations(i)
+            assert np.linalg.norm(g - g_ref) <= 1e-12 * np.linalg.norm(g_ref), i
+            assert np.linalg.norm(f - f_ref) <= 1e-12 * np.linalg.norm(f_ref), i
+
+
+def test_autotuner_restores_state_and_keeps_results():
+    cases = mixed_cases()
+    with lbm.Batch(cases, precision="fp32") as b:
+        b.init_all().step(5)
+        before = [b.populations(i) for i in range(len(cases))]
+        seg, block = lbm.lbm_batch_tune(b.b, 3)
+        assert seg >= 1 and block in (64, 128)
+        assert lbm.lbm_batch_get_launch(b.b) == (seg, block)
+        after = [b.populations(i) for i in range(len(cases))]
+        for (g0, f0), (g1, f1) in zip(before, after):
+            assert np.array_equal(g0, g1) and np.array_equal(f0, f1)
+        b.step(11)
+        tuned = [b.populations(i) for i in range(len(cases))]
+    with lbm.Batch(cases, precision="fp32") as b:
+        b.init_all().step(16)
+        ref = [b.populations(i) for i in range(len(cases))]
+    for (g0, f0), (g1, f1) in zip(tuned, ref):
+        assert np.array_equal(g0, g1) and np.array_equal(f0, f1)
+
+
+def test_ensemble_of_512_cases_stays_finite_and_conserves_phi():
+    cases = W.ensemble()
+    with lbm.Batch(cases, precision="fp32") as b:
+        b.init_all()
+        m0 = np.array([b.fields(i)["phi"].sum() for i in range(len(cases))])
+        b.step(500)
+        m1 = []
+        for i in range(len(cases)):
+            fl = b.fields(i)
+            assert np.isfinite(fl["p"]).all() and np.isfinite(fl["ux"]).all(), i
+            m1.append(fl["phi"].sum())
+    assert np.all(np.abs(np.array(m1) - m0) <= 1e-5 * m0)
+
+
+def test_batch_rejects_mixed_precision():
+    cases = mixed_cases()[:2]
+    p = [lbm.make_params(cases[0], "fp32"), lbm.make_params(cases[1], "fp64")]
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_batch_create(p)
+    assert e.value.status == lbm.LBM_ERR_ARG
