@@ -270,6 +270,8 @@ def run_ours(args):
     if args.variants:
         line["variants"] = {"ensemble_512_cases": measure_ensemble(
             args.ensemble_steps, 16, args.precision, local, stream.cuda_stream)}
+        line["variants"].update(measure_storage(case, args.storage_steps, local,
+                                                stream.cuda_stream))
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(case, args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -327,6 +329,42 @@ def measure_ensemble(steps, per_case_steps, precision="fp32", device=0, stream=0
                     "per_case_steps": per_case_steps,
                     "per_case_launches_per_step": len(cases)})
         out["batched_over_per_case"] = round(out["batched_mlups"] / out["per_case_mlups"], 2)
+    return out
+
+
+def measure_storage(case, steps, device=0, stream=0):
+    """FP32 and 16-bit storage forms of the same workload: MLUPS, and relative L2 of the fields
+    against the GPU FP64 mode after 1000 steps (FP64 mode pinned to the oracle in the tests)."""
+    import torch
+
+    from paper_1909_04166_gb300 import lbm
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    with lbm.Simulation(case, "fp64", device, stream) as a:
+        ref = a.init_case().step(1000).fields()
+    out = {}
+    for prec in ("fp32", "fp16", "bf16"):
+        with lbm.Simulation(case, prec, device, stream) as s:
+            got = s.init_case().step(1000).fields()
+            s.step(64)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.step(steps)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+        bpl = {"fp32": 144, "fp16": 72, "bf16": 72}[prec]
+        out[f"storage_{prec}"] = {
+            "mlups": round(case.nodes / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms, 5),
+            "algorithmic_gbs": round(bpl * case.nodes / (ms * 1e-3) / 1e9, 1),
+            "bytes_per_lu": bpl,
+            "rel_l2_vs_fp64_after_1000": {k: (rel(got[k], ref[k]) if np.isfinite(got[k]).all()
+                                              else "non-finite")
+                                          for k in ("phi", "p", "ux", "uy")}}
     return out
 
 
@@ -444,6 +482,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--ensemble-steps", type=int, default=256)
+    ap.add_argument("--storage-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -66,9 +66,16 @@ extern "C" {
 
 /* Storage / compute precision of a context. */
 typedef enum {
-    LBM_FP64 = 0,  /* populations stored and collided in double (correctness mode) */
-    LBM_FP32 = 1   /* populations stored and collided in float */
+    LBM_FP64 = 0,       /* populations stored and collided in double (correctness mode) */
+    LBM_FP32 = 1,       /* populations stored and collided in float */
+    LBM_FP32_FP16 = 2,  /* collided in float; stored as IEEE half deviations (see below) */
+    LBM_FP32_BF16 = 3   /* collided in float; stored as bfloat16 deviations (see below) */
 } lbm_precision;
+/* 16-bit storage: population a of lattice L is stored as (q_a - w_a ref_L) * scale_L, w the
+ * D2Q9 weights (4/9, 1/9, 1/36), ref_g = params.store_ref_g (a reference pressure, default 0),
+ * ref_f = 1/2 (the mid phase), scale_L = params.store_scale_g / store_scale_f, or when those are
+ * 0 the defaults 2^14 / 2^8 for FP16 (|g-bar| up to ~4 without overflow, deviations above
+ * ~4e-9 kept normal) and 1 / 1 for BF16.  Collisions, forces and stencils stay in float. */
 
 /* Boundary pair along one axis. */
 typedef enum {
@@ -90,6 +97,8 @@ typedef struct {
     int32_t precision;              /* lbm_precision */
     int32_t device;                 /* CUDA device ordinal */
     void* stream;                   /* cudaStream_t for all work of the context */
+    double store_scale_g, store_scale_f;  /* 16-bit storage scales; 0 = default */
+    double store_ref_g;             /* 16-bit storage reference pressure of the fluid lattice */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -146,7 +155,7 @@ int lbm_get_populations(lbm_ctx* ctx, double* g, double* f);
 int lbm_set_populations(lbm_ctx* ctx, const double* g, const double* f);
 
 /* Device pointer of the current state, valid until the next lbm_step.  Element type double for
- * LBM_FP64, float for LBM_FP32.  Layout: tiles of 32 columns; population a (0..8 fluid g-bar,
+ * LBM_FP64, float for LBM_FP32, half / bfloat16 (encoded as above) for the 16-bit modes.  Layout: tiles of 32 columns; population a (0..8 fluid g-bar,
  * 9..17 interface f) of node (x, y) is element ((y * nstrips + x / 32) * 18 + a) * 32 + x % 32,
  * nstrips = ceil(nx / 32).  *elements receives the element count of one state buffer. */
 int lbm_state_device(lbm_ctx* ctx, void** state, int32_t* nstrips, int64_t* elements);

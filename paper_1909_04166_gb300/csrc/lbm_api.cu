@@ -11,29 +11,7 @@
 
 #include "../../include/cmlbm.h"
 #include "lbm_device.cuh"
-
-namespace cmlbm {
-template <typename R, typename S>
-cudaError_t launch_step(const void*, void*, const Geometry&, const Consts<R>&, int, int, int*,
-                        cudaStream_t);
-template <typename R, typename S>
-cudaError_t configure_step(int block);
-template <typename R, typename S>
-int step_blocks_per_sm(int block);
-template <typename R, typename S>
-cudaError_t build_step_graph(const void*, const void*, const Geometry&, const Consts<R>&, int,
-                             int, int*, int, cudaGraphExec_t*);
-template <typename R, typename S>
-cudaError_t launch_init(const double*, const double*, const double*, const double*, void*,
-                        const Geometry&, const Consts<R>&, cudaStream_t);
-template <typename R, typename S>
-cudaError_t launch_fields(const void*, const Geometry&, const Consts<R>&, double*, double*,
-                          double*, double*, double*, cudaStream_t);
-template <typename S>
-cudaError_t launch_pack(const void*, double*, const Geometry&, cudaStream_t);
-template <typename S>
-cudaError_t launch_unpack(const double*, void*, const Geometry&, cudaStream_t);
-}  // namespace cmlbm
+#include "lbm_host.h"
 
 using namespace cmlbm;
 
@@ -65,54 +43,11 @@ namespace {
 constexpr int kReduceSlots = 8;
 constexpr int kGraphChunk = 32;   // steps per replayed graph (even: the buffer parity returns)
 
-bool finite(double v) { return std::isfinite(v); }
+template <typename R> const Consts<R>& kref(const lbm_ctx* c);
+template <> const Consts<double>& kref<double>(const lbm_ctx* c) { return c->Kd; }
+template <> const Consts<float>& kref<float>(const lbm_ctx* c) { return c->Kf; }
 
-int validate(const lbm_params* P)
-{
-    if (!P) return LBM_ERR_ARG;
-    if (P->nx < 1 || P->ny < 1 || P->nx > 65536 || P->ny > 65536) return LBM_ERR_ARG;
-    if ((P->bc_x != LBM_PERIODIC && P->bc_x != LBM_WALL) ||
-        (P->bc_y != LBM_PERIODIC && P->bc_y != LBM_WALL))
-        return LBM_ERR_ARG;
-    if (P->precision != LBM_FP64 && P->precision != LBM_FP32) return LBM_ERR_UNSUPPORTED;
-    const double v[] = {P->rho_a, P->rho_b, P->mu_a, P->mu_b, P->sigma0, P->dsigma_dT, P->T0,
-                        P->gradT_x, P->gradT_y, P->mobility, P->width, P->gx, P->gy,
-                        P->rho_ref};
-    for (double d : v)
-        if (!finite(d)) return LBM_ERR_PARAM;
-    if (P->rho_a <= 0 || P->rho_b <= 0 || P->mu_a <= 0 || P->mu_b <= 0) return LBM_ERR_PARAM;
-    if (P->width <= 0 || P->mobility <= 0) return LBM_ERR_PARAM;
-    return LBM_OK;
-}
-
-int strips_of(int nx) { return (nx + 31) / 32; }
-
-size_t buffer_elems(int nx, int ny) { return (size_t)ny * strips_of(nx) * 18 * 32; }
-
-size_t elem_of(int precision) { return precision == LBM_FP64 ? sizeof(double) : sizeof(float); }
-
-template <typename R>
-Consts<R> make_consts(const lbm_params& P)
-{
-    Consts<R> K;
-    K.rho_b = R(P.rho_b);
-    K.drho = R(P.rho_a - P.rho_b);
-    K.mu_b = R(P.mu_b);
-    K.dmu = R(P.mu_a - P.mu_b);
-    // kappa-tilde = 3/2 sigma W with sigma = sigma0 + dsigma_dT (gradT . x)
-    K.kt0 = R(1.5 * P.width * P.sigma0);
-    K.dktx = R(1.5 * P.width * P.dsigma_dT * P.gradT_x);
-    K.dkty = R(1.5 * P.width * P.dsigma_dT * P.gradT_y);
-    K.mob = R(P.mobility);
-    K.four_over_w = R(4.0 / P.width);
-    // M_phi = c^2 (1/omega - 1/2) -> omega = 1 / (3 M_phi + 1/2)
-    K.omega_phi = R(1.0 / (3.0 * P.mobility + 0.5));
-    K.gx = R(P.gx);
-    K.gy = R(P.gy);
-    K.rho_ref = R(P.rho_ref);
-    K.cs2_drho = R((P.rho_a - P.rho_b) / 3.0);
-    return K;
-}
+int validate(const lbm_params* P) { return validate_params(P); }
 
 int cuda_fail(lbm_ctx* c, cudaError_t e)
 {
@@ -127,8 +62,9 @@ void* cur_state(lbm_ctx* c) { return c->buf + (size_t)c->cur * c->state_bytes; }
 // about once (one wave): warps = strips * ceil(ny / rows).
 int default_seg_rows(const lbm_ctx* c)
 {
-    const int bps = c->P.precision == LBM_FP64 ? step_blocks_per_sm<double, double>(c->block)
-                                               : step_blocks_per_sm<float, float>(c->block);
+    const int bps = with_types(c->P.precision, [&](auto r, auto s) {
+        return step_blocks_per_sm<decltype(r), decltype(s)>(c->block);
+    });
     const long long resident = (long long)c->nsm * bps * (c->block / 32);
     const long long strips = c->G.nstrips;
     long long nseg = resident / strips;
@@ -141,8 +77,9 @@ int default_seg_rows(const lbm_ctx* c)
 
 cudaError_t configure(lbm_ctx* c)
 {
-    return c->P.precision == LBM_FP64 ? configure_step<double, double>(c->block)
-                                      : configure_step<float, float>(c->block);
+    return with_types(c->P.precision, [&](auto r, auto s) {
+        return configure_step<decltype(r), decltype(s)>(c->block);
+    });
 }
 
 void drop_graphs(lbm_ctx* c)
@@ -156,10 +93,11 @@ void drop_graphs(lbm_ctx* c)
 
 cudaError_t launch_one(lbm_ctx* c, const void* src, void* dst)
 {
-    if (c->P.precision == LBM_FP64)
-        return launch_step<double, double>(src, dst, c->G, c->Kd, c->seg_h, c->block, c->err,
-                                           c->st);
-    return launch_step<float, float>(src, dst, c->G, c->Kf, c->seg_h, c->block, c->err, c->st);
+    return with_types(c->P.precision, [&](auto r, auto s) {
+        using R = decltype(r);
+        return launch_step<R, decltype(s)>(src, dst, c->G, kref<R>(c), c->seg_h, c->block,
+                                           c->err, c->st);
+    });
 }
 
 cudaError_t ensure_graph(lbm_ctx* c, int start)
@@ -167,11 +105,11 @@ cudaError_t ensure_graph(lbm_ctx* c, int start)
     if (c->graph[start]) return cudaSuccess;
     const void* a = c->buf + (size_t)start * c->state_bytes;
     const void* b = c->buf + (size_t)(1 - start) * c->state_bytes;
-    if (c->P.precision == LBM_FP64)
-        return build_step_graph<double, double>(a, b, c->G, c->Kd, c->seg_h, c->block, c->err,
-                                                kGraphChunk, &c->graph[start]);
-    return build_step_graph<float, float>(a, b, c->G, c->Kf, c->seg_h, c->block, c->err,
-                                          kGraphChunk, &c->graph[start]);
+    return with_types(c->P.precision, [&](auto r, auto s) {
+        using R = decltype(r);
+        return build_step_graph<R, decltype(s)>(a, b, c->G, kref<R>(c), c->seg_h, c->block,
+                                                c->err, kGraphChunk, &c->graph[start]);
+    });
 }
 
 // Read the step kernel's error word (synchronises the stream).
@@ -202,7 +140,7 @@ int make_ctx(const lbm_params* params, void* ext, size_t ext_bytes, lbm_ctx** ou
     c->G.wall_y = params->bc_y == LBM_WALL;
     c->Kd = make_consts<double>(*params);
     c->Kf = make_consts<float>(*params);
-    c->elem = elem_of(params->precision);
+    c->elem = elem_bytes(params->precision);
     c->state_bytes = buffer_elems(params->nx, params->ny) * c->elem;
     c->st = static_cast<cudaStream_t>(params->stream);
     int dev = params->device, nsm = 0;
@@ -260,11 +198,11 @@ int ensure_scratch(lbm_ctx* c)
 
 int run_fields(lbm_ctx* c, double* phi, double* p, double* ux, double* uy, double* rho)
 {
-    cudaError_t e;
-    if (c->P.precision == LBM_FP64)
-        e = launch_fields<double, double>(cur_state(c), c->G, c->Kd, phi, p, ux, uy, rho, c->st);
-    else
-        e = launch_fields<float, float>(cur_state(c), c->G, c->Kf, phi, p, ux, uy, rho, c->st);
+    cudaError_t e = with_types(c->P.precision, [&](auto r, auto s) {
+        using R = decltype(r);
+        return launch_fields<R, decltype(s)>(cur_state(c), c->G, kref<R>(c), phi, p, ux, uy, rho,
+                                             c->st);
+    });
     return e == cudaSuccess ? LBM_OK : cuda_fail(c, e);
 }
 
@@ -387,7 +325,7 @@ int lbm_state_bytes(const lbm_params* params, size_t* bytes)
     if (!bytes) return LBM_ERR_ARG;
     int s = validate(params);
     if (s) return s;
-    *bytes = 2 * buffer_elems(params->nx, params->ny) * elem_of(params->precision);
+    *bytes = 2 * buffer_elems(params->nx, params->ny) * elem_bytes(params->precision);
     return LBM_OK;
 }
 
@@ -412,11 +350,11 @@ int lbm_init_fields_device(lbm_ctx* c, const double* phi, const double* p, const
     if (!c || !phi || !p || !ux || !uy) return LBM_ERR_ARG;
     cudaSetDevice(c->P.device);
     c->cur = 0;
-    cudaError_t e;
-    if (c->P.precision == LBM_FP64)
-        e = launch_init<double, double>(phi, p, ux, uy, cur_state(c), c->G, c->Kd, c->st);
-    else
-        e = launch_init<float, float>(phi, p, ux, uy, cur_state(c), c->G, c->Kf, c->st);
+    cudaError_t e = with_types(c->P.precision, [&](auto r, auto s) {
+        using R = decltype(r);
+        return launch_init<R, decltype(s)>(phi, p, ux, uy, cur_state(c), c->G, kref<R>(c),
+                                           c->st);
+    });
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->initialised = true;
     c->steps = 0;
@@ -507,8 +445,9 @@ int lbm_get_populations(lbm_ctx* c, double* g, double* f)
     double* tmp = nullptr;
     cudaError_t e = cudaMalloc(&tmp, 18 * N * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(c, e);
-    e = (c->P.precision == LBM_FP64) ? launch_pack<double>(cur_state(c), tmp, c->G, c->st)
-                                     : launch_pack<float>(cur_state(c), tmp, c->G, c->st);
+    e = with_types(c->P.precision, [&](auto r, auto s) {
+        return launch_pack<double, decltype(s)>(cur_state(c), tmp, c->G, c->Kd, c->st);
+    });
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g, tmp, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess)
@@ -534,8 +473,9 @@ int lbm_set_populations(lbm_ctx* c, const double* g, const double* f)
                             c->st);
     c->cur = 0;
     if (e == cudaSuccess)
-        e = (c->P.precision == LBM_FP64) ? launch_unpack<double>(tmp, cur_state(c), c->G, c->st)
-                                         : launch_unpack<float>(tmp, cur_state(c), c->G, c->st);
+        e = with_types(c->P.precision, [&](auto r, auto s) {
+            return launch_unpack<double, decltype(s)>(tmp, cur_state(c), c->G, c->Kd, c->st);
+        });
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(c, e);

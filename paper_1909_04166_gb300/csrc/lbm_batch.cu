@@ -10,27 +10,7 @@
 
 #include "../../include/cmlbm.h"
 #include "lbm_device.cuh"
-
-namespace cmlbm {
-template <typename R, typename S>
-cudaError_t configure_batch(int block);
-template <typename R, typename S>
-cudaError_t launch_batch_step(void*, const BatchCase<R>*, const int2*, int, int, int, int*,
-                              cudaStream_t);
-template <typename R, typename S>
-cudaError_t build_batch_graph(void*, const BatchCase<R>*, const int2*, int, int, int, int*, int,
-                              cudaGraphExec_t*);
-template <typename R, typename S>
-cudaError_t launch_init(const double*, const double*, const double*, const double*, void*,
-                        const Geometry&, const Consts<R>&, cudaStream_t);
-template <typename R, typename S>
-cudaError_t launch_fields(const void*, const Geometry&, const Consts<R>&, double*, double*,
-                          double*, double*, double*, cudaStream_t);
-template <typename S>
-cudaError_t launch_pack(const void*, double*, const Geometry&, cudaStream_t);
-template <typename S>
-size_t step_smem_bytes(int block);
-}  // namespace cmlbm
+#include "lbm_host.h"
 
 using namespace cmlbm;
 
@@ -46,45 +26,6 @@ struct HostCase {
     long long off0, off1;   // element offsets of the two buffers
     long long nodes;
 };
-
-// Same validation and constants as a single context (kept here so each TU stands alone).
-int validate_case(const lbm_params* P)
-{
-    if (P->nx < 1 || P->ny < 1 || P->nx > 65536 || P->ny > 65536) return LBM_ERR_ARG;
-    if ((P->bc_x != LBM_PERIODIC && P->bc_x != LBM_WALL) ||
-        (P->bc_y != LBM_PERIODIC && P->bc_y != LBM_WALL))
-        return LBM_ERR_ARG;
-    if (P->precision != LBM_FP64 && P->precision != LBM_FP32) return LBM_ERR_UNSUPPORTED;
-    const double v[] = {P->rho_a, P->rho_b, P->mu_a, P->mu_b, P->sigma0, P->dsigma_dT, P->T0,
-                        P->gradT_x, P->gradT_y, P->mobility, P->width, P->gx, P->gy,
-                        P->rho_ref};
-    for (double d : v)
-        if (!std::isfinite(d)) return LBM_ERR_PARAM;
-    if (P->rho_a <= 0 || P->rho_b <= 0 || P->mu_a <= 0 || P->mu_b <= 0) return LBM_ERR_PARAM;
-    if (P->width <= 0 || P->mobility <= 0) return LBM_ERR_PARAM;
-    return LBM_OK;
-}
-
-template <typename R>
-Consts<R> consts_of(const lbm_params& P)
-{
-    Consts<R> K;
-    K.rho_b = R(P.rho_b);
-    K.drho = R(P.rho_a - P.rho_b);
-    K.mu_b = R(P.mu_b);
-    K.dmu = R(P.mu_a - P.mu_b);
-    K.kt0 = R(1.5 * P.width * P.sigma0);
-    K.dktx = R(1.5 * P.width * P.dsigma_dT * P.gradT_x);
-    K.dkty = R(1.5 * P.width * P.dsigma_dT * P.gradT_y);
-    K.mob = R(P.mobility);
-    K.four_over_w = R(4.0 / P.width);
-    K.omega_phi = R(1.0 / (3.0 * P.mobility + 0.5));
-    K.gx = R(P.gx);
-    K.gy = R(P.gy);
-    K.rho_ref = R(P.rho_ref);
-    K.cs2_drho = R((P.rho_a - P.rho_b) / 3.0);
-    return K;
-}
 
 }  // namespace
 
@@ -130,7 +71,7 @@ int build_tasks(lbm_batch* b, int h)
     const int n = (int)b->cases.size();
     std::vector<int2> tasks;
     std::vector<BatchCase<double>> cd(b->precision == LBM_FP64 ? n : 0);
-    std::vector<BatchCase<float>> cf(b->precision == LBM_FP32 ? n : 0);
+    std::vector<BatchCase<float>> cf(b->precision != LBM_FP64 ? n : 0);
     for (int c = 0; c < n; ++c) {
         const HostCase& hc = b->cases[c];
         const int nseg = (hc.G.ny + h - 1) / h;
@@ -166,34 +107,37 @@ int build_tasks(lbm_batch* b, int h)
 
 cudaError_t configure(lbm_batch* b)
 {
-    return b->precision == LBM_FP64 ? configure_batch<double, double>(b->block)
-                                    : configure_batch<float, float>(b->block);
+    return with_types(b->precision, [&](auto r, auto s) {
+        return configure_batch<decltype(r), decltype(s)>(b->block);
+    });
 }
 
 cudaError_t launch_one(lbm_batch* b)
 {
-    if (b->precision == LBM_FP64)
-        return launch_batch_step<double, double>(b->base,
-                                                 static_cast<BatchCase<double>*>(b->dcases),
+    return with_types(b->precision, [&](auto r, auto s) {
+        using R = decltype(r);
+        return launch_batch_step<R, decltype(s)>(b->base,
+                                                 static_cast<BatchCase<R>*>(b->dcases),
                                                  b->dtasks, b->ntasks, b->cur, b->block, b->err,
                                                  b->st);
-    return launch_batch_step<float, float>(b->base, static_cast<BatchCase<float>*>(b->dcases),
-                                           b->dtasks, b->ntasks, b->cur, b->block, b->err,
-                                           b->st);
+    });
 }
 
 cudaError_t ensure_graph(lbm_batch* b)
 {
     if (b->graph[b->cur]) return cudaSuccess;
-    if (b->precision == LBM_FP64)
-        return build_batch_graph<double, double>(b->base,
-                                                 static_cast<BatchCase<double>*>(b->dcases),
+    return with_types(b->precision, [&](auto r, auto s) {
+        using R = decltype(r);
+        return build_batch_graph<R, decltype(s)>(b->base,
+                                                 static_cast<BatchCase<R>*>(b->dcases),
                                                  b->dtasks, b->ntasks, b->cur, b->block, b->err,
                                                  kBatchGraphChunk, &b->graph[b->cur]);
-    return build_batch_graph<float, float>(b->base, static_cast<BatchCase<float>*>(b->dcases),
-                                           b->dtasks, b->ntasks, b->cur, b->block, b->err,
-                                           kBatchGraphChunk, &b->graph[b->cur]);
+    });
 }
+
+template <typename R> const Consts<R>& kref(const HostCase& hc);
+template <> const Consts<double>& kref<double>(const HostCase& hc) { return hc.Kd; }
+template <> const Consts<float>& kref<float>(const HostCase& hc) { return hc.Kf; }
 
 void* case_state(lbm_batch* b, int c)
 {
@@ -220,7 +164,7 @@ int lbm_batch_create(const lbm_params* params, int32_t ncases, lbm_batch** out)
     *out = nullptr;
     if (!params || ncases < 1) return LBM_ERR_ARG;
     for (int c = 0; c < ncases; ++c) {
-        int s = validate_case(&params[c]);
+        int s = validate_params(&params[c]);
         if (s) return s;
         if (params[c].precision != params[0].precision || params[c].device != params[0].device ||
             params[c].stream != params[0].stream)
@@ -231,7 +175,7 @@ int lbm_batch_create(const lbm_params* params, int32_t ncases, lbm_batch** out)
     if (!b) return LBM_ERR_NOMEM;
     b->precision = params[0].precision;
     b->device = params[0].device;
-    b->elem = b->precision == LBM_FP64 ? sizeof(double) : sizeof(float);
+    b->elem = elem_bytes(b->precision);
     b->st = static_cast<cudaStream_t>(params[0].stream);
     b->block = 128;
     long long off = 0;
@@ -243,12 +187,12 @@ int lbm_batch_create(const lbm_params* params, int32_t ncases, lbm_batch** out)
         hc.G.nstrips = (params[c].nx + 31) / 32;
         hc.G.wall_x = params[c].bc_x == LBM_WALL;
         hc.G.wall_y = params[c].bc_y == LBM_WALL;
-        hc.Kd = consts_of<double>(params[c]);
-        hc.Kf = consts_of<float>(params[c]);
+        hc.Kd = make_consts<double>(params[c]);
+        hc.Kf = make_consts<float>(params[c]);
         const long long elems = (long long)hc.G.ny * hc.G.nstrips * 18 * 32;
         hc.off0 = off;
         hc.off1 = off + elems;
-        off += 2 * elems;                  // multiples of 576 elements keep 16-byte alignment
+        off += 2 * elems;      // multiples of 576 elements keep every buffer 16-byte aligned
         hc.nodes = (long long)hc.G.nx * hc.G.ny;
         b->max_nodes = std::max(b->max_nodes, hc.nodes);
         b->total_nodes += hc.nodes;
@@ -259,7 +203,7 @@ int lbm_batch_create(const lbm_params* params, int32_t ncases, lbm_batch** out)
     if (e == cudaSuccess) e = cudaMemsetAsync(b->base, 0, b->base_bytes, b->st);
     if (e == cudaSuccess)
         e = cudaMalloc(&b->dcases, ncases * (b->precision == LBM_FP64 ? sizeof(BatchCase<double>)
-                                                                     : sizeof(BatchCase<float>)));
+                                                                      : sizeof(BatchCase<float>)));
     if (e == cudaSuccess) e = cudaMalloc(&b->err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->err, 0, sizeof(int), b->st);
     if (e == cudaSuccess) e = cudaMalloc(&b->scratch, 5 * (size_t)b->max_nodes * sizeof(double));
@@ -287,11 +231,11 @@ int lbm_batch_init_fields(lbm_batch* b, int32_t c, const double* phi, const doub
         e = cudaMemcpyAsync(b->scratch + k * N, src[k], B, cudaMemcpyHostToDevice, b->st);
     double* d = b->scratch;
     if (e == cudaSuccess)
-        e = b->precision == LBM_FP64
-                ? launch_init<double, double>(d, d + N, d + 2 * N, d + 3 * N, case_state(b, c),
-                                              hc.G, hc.Kd, b->st)
-                : launch_init<float, float>(d, d + N, d + 2 * N, d + 3 * N, case_state(b, c),
-                                            hc.G, hc.Kf, b->st);
+        e = with_types(b->precision, [&](auto r, auto s) {
+            using R = decltype(r);
+            return launch_init<R, decltype(s)>(d, d + N, d + 2 * N, d + 3 * N, case_state(b, c),
+                                               hc.G, kref<R>(hc), b->st);
+        });
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     return e == cudaSuccess ? LBM_OK : fail_cuda(b, e);
 }
@@ -323,11 +267,11 @@ int lbm_batch_get_fields(lbm_batch* b, int32_t c, double* phi, double* p, double
     const HostCase& hc = b->cases[c];
     const size_t N = (size_t)hc.nodes, B = N * sizeof(double);
     double* d = b->scratch;
-    cudaError_t e = b->precision == LBM_FP64
-                        ? launch_fields<double, double>(case_state(b, c), hc.G, hc.Kd, d, d + N,
-                                                        d + 2 * N, d + 3 * N, d + 4 * N, b->st)
-                        : launch_fields<float, float>(case_state(b, c), hc.G, hc.Kf, d, d + N,
-                                                      d + 2 * N, d + 3 * N, d + 4 * N, b->st);
+    cudaError_t e = with_types(b->precision, [&](auto r, auto s) {
+        using R = decltype(r);
+        return launch_fields<R, decltype(s)>(case_state(b, c), hc.G, kref<R>(hc), d, d + N,
+                                             d + 2 * N, d + 3 * N, d + 4 * N, b->st);
+    });
     double* h[5] = {phi, p, ux, uy, rho};
     for (int k = 0; k < 5 && e == cudaSuccess; ++k)
         if (h[k]) e = cudaMemcpyAsync(h[k], d + k * N, B, cudaMemcpyDeviceToHost, b->st);
@@ -345,8 +289,9 @@ int lbm_batch_get_populations(lbm_batch* b, int32_t c, double* g, double* f)
     double* tmp = nullptr;
     cudaError_t e = cudaMalloc(&tmp, 18 * N * sizeof(double));
     if (e == cudaSuccess)
-        e = b->precision == LBM_FP64 ? launch_pack<double>(case_state(b, c), tmp, hc.G, b->st)
-                                     : launch_pack<float>(case_state(b, c), tmp, hc.G, b->st);
+        e = with_types(b->precision, [&](auto r, auto s) {
+            return launch_pack<double, decltype(s)>(case_state(b, c), tmp, hc.G, hc.Kd, b->st);
+        });
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g, tmp, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, b->st);
     if (e == cudaSuccess)

@@ -29,7 +29,76 @@ struct Consts {
     R omega_phi;         // omega^phi_{1,2}, from M_phi = c^2 (1/omega - 1/2)   (Sec. 5)
     R gx, gy, rho_ref;   // F_ext = (rho - rho_ref) g
     R cs2_drho;          // c_s^2 (rho_A - rho_B), the factor of grad rho in F_p
+    // 16-bit storage codec, lattice 0 = fluid g-bar, 1 = interface f: the stored number is
+    // (q_a - w_a ref) * scale; unused for FP32 / FP64 storage
+    R st_scale[2], st_inv[2], st_ref[2];
 };
+
+// D2Q9 weights (the populations of the rest state are w_a times the zeroth moment).
+__host__ __device__ constexpr double d2q9_w(int a)
+{
+    return a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Storage codec.  FP32 and FP64 states hold the populations themselves; FP16 / BF16 states
+// hold scaled deviations from the rest-state weights times a per-lattice reference.
+// ---------------------------------------------------------------------------------------------
+template <typename S> struct Narrow { static constexpr bool value = sizeof(S) < 4; };
+
+__device__ __forceinline__ float narrow_to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float narrow_to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename S> __device__ __forceinline__ S f_to_narrow(float v);
+template <> __device__ __forceinline__ __half f_to_narrow<__half>(float v)
+{
+    return __float2half_rn(v);
+}
+template <> __device__ __forceinline__ __nv_bfloat16 f_to_narrow<__nv_bfloat16>(float v)
+{
+    return __float2bfloat16_rn(v);
+}
+
+template <typename S, typename R>
+__device__ __forceinline__ R decode(S v, int lat, int a, const Consts<R>& K)
+{
+    if constexpr (!Narrow<S>::value) {
+        return static_cast<R>(v);
+    } else {
+        const R inv = lat ? K.st_inv[1] : K.st_inv[0];
+        const R ref = lat ? K.st_ref[1] : K.st_ref[0];
+        return narrow_to_f(v) * inv + R(d2q9_w(a)) * ref;
+    }
+}
+
+template <typename S, typename R>
+__device__ __forceinline__ S encode(R v, int lat, int a, const Consts<R>& K)
+{
+    if constexpr (!Narrow<S>::value) {
+        return static_cast<S>(v);
+    } else {
+        const R scale = lat ? K.st_scale[1] : K.st_scale[0];
+        const R ref = lat ? K.st_ref[1] : K.st_ref[0];
+        return f_to_narrow<S>((v - R(d2q9_w(a)) * ref) * scale);
+    }
+}
+
+// Sum of the nine decoded populations of one lattice from their stored values (the weights
+// sum to one, so the reference enters once).
+template <typename S, typename R>
+__device__ __forceinline__ R decode_sum(const S* q, int stride, int lat, const Consts<R>& K)
+{
+    if constexpr (!Narrow<S>::value) {
+        R s = R(0);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) s += static_cast<R>(q[a * stride]);
+        return s;
+    } else {
+        float s = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) s += narrow_to_f(q[a * stride]);
+        return s * (lat ? K.st_inv[1] : K.st_inv[0]) + (lat ? K.st_ref[1] : K.st_ref[0]);
+    }
+}
 
 struct Geometry {
     int nx, ny;

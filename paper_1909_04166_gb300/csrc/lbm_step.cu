@@ -133,13 +133,10 @@ struct Row3 {
 // halo loads (one plane of the left / right halo column, or 0).
 template <typename R, typename S>
 __device__ __forceinline__ void window_row(const S* tile, int lane, int wlast, R hl, R hr,
-                                           Row3<R>& row)
+                                           const Consts<R>& K, Row3<R>& row)
 {
-    R ps = R(0), ph = R(0);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) ps += static_cast<R>(tile[a * 32 + lane]);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) ph += static_cast<R>(tile[(9 + a) * 32 + lane]);
+    const R ps = decode_sum<S, R>(tile + lane, 32, 0, K);
+    const R ph = decode_sum<S, R>(tile + 9 * 32 + lane, 32, 1, K);
 #pragma unroll
     for (int off = 8; off >= 1; off >>= 1) {
         hl += __shfl_xor_sync(FULL, hl, off);
@@ -170,12 +167,13 @@ __device__ __forceinline__ void make_window(const Row3<R>& s, const Row3<R>& c,
 }
 
 template <typename S, typename R>
-__device__ __forceinline__ void ld_pops_t(const S* tile, int lane, R g[9], R f[9])
+__device__ __forceinline__ void ld_pops_t(const S* tile, int lane, const Consts<R>& K, R g[9],
+                                          R f[9])
 {
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-        g[a] = static_cast<R>(tile[a * 32 + lane]);
-        f[a] = static_cast<R>(tile[(9 + a) * 32 + lane]);
+        g[a] = decode<S, R>(tile[a * 32 + lane], 0, a, K);
+        f[a] = decode<S, R>(tile[(9 + a) * 32 + lane], 1, a, K);
     }
 }
 
@@ -225,8 +223,8 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
         hr = R(0);
         if (hlane) {
             const S* rb = row_ptr(src, row_of(k));
-            hl = static_cast<R>(__ldg(rb + hoffl));
-            hr = static_cast<R>(__ldg(rb + hoffr));
+            hl = decode<S, R>(__ldg(rb + hoffl), lane >> 4, hq, K);
+            hr = decode<S, R>(__ldg(rb + hoffr), lane >> 4, hq, K);
         }
     };
 
@@ -260,11 +258,11 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     R hl, hr, hl2, hr2;
     halo_load(-1, hl, hr);
     if (!wait_k(-1, 0)) { fail(-1); return; }
-    window_row<R, S>(tiles, lane, wlast, hl, hr, rb);
+    window_row<R, S>(tiles, lane, wlast, hl, hr, K, rb);
     issue(NS - 1, 0);
     halo_load(0, hl, hr);
     if (!wait_k(0, 1)) { fail(0); return; }
-    window_row<R, S>(tiles + TILE, lane, wlast, hl, hr, rc);
+    window_row<R, S>(tiles + TILE, lane, wlast, hl, hr, K, rc);
     halo_load(1, hl2, hr2);
 
     // neighbour columns of this lane (periodic wrap; walls handled by bounce flags)
@@ -281,7 +279,7 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     auto body = [&](int i, int st) {
         const int st1 = st + 1 == NS ? 0 : st + 1;       // stage of row i + 1
         if (!wait_k(i + 1, st1)) { fail(i + 1); ok = false; return; }
-        window_row<R, S>(tiles + st1 * TILE, lane, wlast, hl2, hr2, rn);
+        window_row<R, S>(tiles + st1 * TILE, lane, wlast, hl2, hr2, K, rn);
         if (i + 2 <= nrows) halo_load(i + 2, hl2, hr2);
 
         const int y = up ? ys + i : ye - 1 - i;
@@ -289,7 +287,7 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
         if (up) make_window(rb, rc, rn, ph, ps);
         else make_window(rn, rc, rb, ph, ps);
         R g[9], f[9];
-        ld_pops_t<S, R>(tiles + st * TILE, lane, g, f);
+        ld_pops_t<S, R>(tiles + st * TILE, lane, K, g, f);
         const R jgx = (g[1] - g[3]) + (g[5] - g[6]) - (g[7] - g[8]);
         const R jgy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
         Macro<R> m;
@@ -314,16 +312,16 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
             if (active) {
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
-                    p[a][a * 32] = static_cast<S>(g[a]);
-                    p[a][(9 + a) * 32] = static_cast<S>(f[a]);
+                    p[a][a * 32] = encode<S, R>(g[a], 0, a, K);
+                    p[a][(9 + a) * 32] = encode<S, R>(f[a], 1, a, K);
                 }
             }
         } else if (active) {
 #pragma unroll
             for (int a = 0; a < 9; ++a) {
                 S* q = bnc[a] ? pc + (OPP[a] - a) * 32 : p[a];
-                q[a * 32] = static_cast<S>(g[a]);
-                q[(9 + a) * 32] = static_cast<S>(f[a]);
+                q[a * 32] = encode<S, R>(g[a], 0, a, K);
+                q[(9 + a) * 32] = encode<S, R>(f[a], 1, a, K);
             }
         }
         issue(i + NS, st);      // the tile of row i is consumed: refill its stage
@@ -393,8 +391,8 @@ __global__ void init_kernel(const double* __restrict__ phi, const double* __rest
     equilibria<R>(ph, R(p[n]), R(ux[n]), R(uy[n]), rho, g, f);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-        state[elem_index(G, a, x, y)] = static_cast<S>(g[a]);
-        state[elem_index(G, 9 + a, x, y)] = static_cast<S>(f[a]);
+        state[elem_index(G, a, x, y)] = encode<S, R>(g[a], 0, a, K);
+        state[elem_index(G, 9 + a, x, y)] = encode<S, R>(f[a], 1, a, K);
     }
 }
 
@@ -416,8 +414,8 @@ __global__ void fields_kernel(const S* __restrict__ state, Geometry G, Consts<R>
             const int xx = map_col(x + i, G);
             R gq[9], fq[9];
             for (int a = 0; a < 9; ++a) {
-                gq[a] = static_cast<R>(state[elem_index(G, a, xx, yy)]);
-                fq[a] = static_cast<R>(state[elem_index(G, 9 + a, xx, yy)]);
+                gq[a] = decode<S, R>(state[elem_index(G, a, xx, yy)], 0, a, K);
+                fq[a] = decode<S, R>(state[elem_index(G, 9 + a, xx, yy)], 1, a, K);
             }
             vph[j + 1][i + 1] =
                 ((fq[0] + fq[1]) + (fq[2] + fq[3])) + ((fq[4] + fq[5]) + (fq[6] + fq[7])) + fq[8];
@@ -430,7 +428,7 @@ __global__ void fields_kernel(const S* __restrict__ state, Geometry G, Consts<R>
     Win<R> ps = {vps[0][0], vps[0][1], vps[0][2], vps[1][0], vps[1][1], vps[1][2],
                  vps[2][0], vps[2][1], vps[2][2]};
     R gq[9];
-    for (int a = 0; a < 9; ++a) gq[a] = static_cast<R>(state[elem_index(G, a, x, y)]);
+    for (int a = 0; a < 9; ++a) gq[a] = decode<S, R>(state[elem_index(G, a, x, y)], 0, a, K);
     const R jgx = (gq[1] - gq[3]) + (gq[5] - gq[6]) - (gq[7] - gq[8]);
     const R jgy = (gq[2] - gq[4]) + (gq[5] + gq[6]) - (gq[7] + gq[8]);
     Macro<R> m;
@@ -442,27 +440,31 @@ __global__ void fields_kernel(const S* __restrict__ state, Geometry G, Consts<R>
     if (rho_o) rho_o[n] = double(m.rho);
 }
 
-// Copy between the tiled device state and a dense [18][ny][nx] double array.
-template <typename S>
-__global__ void pack_kernel(const S* __restrict__ state, double* __restrict__ out, Geometry G)
+// Copy between the tiled device state and a dense [18][ny][nx] double array (decoded values).
+template <typename R, typename S>
+__global__ void pack_kernel(const S* __restrict__ state, double* __restrict__ out, Geometry G,
+                            Consts<R> K)
 {
     const long long N = (long long)G.nx * G.ny;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 18 * N) return;
     const int a = (int)(t / N);
     const long long n = t % N;
-    out[t] = double(state[elem_index(G, a, (int)(n % G.nx), (int)(n / G.nx))]);
+    out[t] = double(decode<S, R>(state[elem_index(G, a, (int)(n % G.nx), (int)(n / G.nx))],
+                                 a >= 9, a % 9, K));
 }
 
-template <typename S>
-__global__ void unpack_kernel(const double* __restrict__ in, S* __restrict__ state, Geometry G)
+template <typename R, typename S>
+__global__ void unpack_kernel(const double* __restrict__ in, S* __restrict__ state, Geometry G,
+                              Consts<R> K)
 {
     const long long N = (long long)G.nx * G.ny;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 18 * N) return;
     const int a = (int)(t / N);
     const long long n = t % N;
-    state[elem_index(G, a, (int)(n % G.nx), (int)(n / G.nx))] = static_cast<S>(in[t]);
+    state[elem_index(G, a, (int)(n % G.nx), (int)(n / G.nx))] =
+        encode<S, R>(R(in[t]), a >= 9, a % 9, K);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -625,70 +627,64 @@ cudaError_t launch_fields(const void* state, const Geometry& G, const Consts<R>&
     return cudaGetLastError();
 }
 
-template <typename S>
-cudaError_t launch_pack(const void* state, double* out, const Geometry& G, cudaStream_t st)
+template <typename R, typename S>
+cudaError_t launch_pack(const void* state, double* out, const Geometry& G, const Consts<R>& K,
+                        cudaStream_t st)
 {
     const long long T = 18LL * G.nx * G.ny;
-    pack_kernel<S><<<(unsigned)((T + 255) / 256), 256, 0, st>>>(static_cast<const S*>(state),
-                                                               out, G);
+    pack_kernel<R, S><<<(unsigned)((T + 255) / 256), 256, 0, st>>>(
+        static_cast<const S*>(state), out, G, K);
     return cudaGetLastError();
 }
 
-template <typename S>
-cudaError_t launch_unpack(const double* in, void* state, const Geometry& G, cudaStream_t st)
+template <typename R, typename S>
+cudaError_t launch_unpack(const double* in, void* state, const Geometry& G, const Consts<R>& K,
+                          cudaStream_t st)
 {
     const long long T = 18LL * G.nx * G.ny;
-    unpack_kernel<S><<<(unsigned)((T + 255) / 256), 256, 0, st>>>(in, static_cast<S*>(state), G);
+    unpack_kernel<R, S><<<(unsigned)((T + 255) / 256), 256, 0, st>>>(in, static_cast<S*>(state),
+                                                                     G, K);
     return cudaGetLastError();
 }
 
-template size_t step_smem_bytes<double>(int);
-template size_t step_smem_bytes<float>(int);
-template cudaError_t configure_step<double, double>(int);
-template int step_blocks_per_sm<double, double>(int);
-template cudaError_t configure_batch<double, double>(int);
-template cudaError_t build_batch_graph<double, double>(void*, const BatchCase<double>*,
-                                                       const int2*, int, int, int, int*, int,
-                                                       cudaGraphExec_t*);
-template cudaError_t build_batch_graph<float, float>(void*, const BatchCase<float>*,
-                                                     const int2*, int, int, int, int*, int,
-                                                     cudaGraphExec_t*);
-template cudaError_t configure_batch<float, float>(int);
-template cudaError_t launch_batch_step<double, double>(void*, const BatchCase<double>*,
-                                                       const int2*, int, int, int, int*,
-                                                       cudaStream_t);
-template cudaError_t launch_batch_step<float, float>(void*, const BatchCase<float>*,
-                                                     const int2*, int, int, int, int*,
-                                                     cudaStream_t);
-template cudaError_t build_step_graph<double, double>(const void*, const void*, const Geometry&,
-                                                      const Consts<double>&, int, int, int*, int,
-                                                      cudaGraphExec_t*);
-template cudaError_t build_step_graph<float, float>(const void*, const void*, const Geometry&,
-                                                    const Consts<float>&, int, int, int*, int,
-                                                    cudaGraphExec_t*);
-template int step_blocks_per_sm<float, float>(int);
-template cudaError_t configure_step<float, float>(int);
-template cudaError_t launch_step<double, double>(const void*, void*, const Geometry&,
-                                                 const Consts<double>&, int, int, int*,
-                                                 cudaStream_t);
-template cudaError_t launch_step<float, float>(const void*, void*, const Geometry&,
-                                               const Consts<float>&, int, int, int*,
-                                               cudaStream_t);
-template cudaError_t launch_init<double, double>(const double*, const double*, const double*,
-                                                 const double*, void*, const Geometry&,
-                                                 const Consts<double>&, cudaStream_t);
-template cudaError_t launch_init<float, float>(const double*, const double*, const double*,
-                                               const double*, void*, const Geometry&,
-                                               const Consts<float>&, cudaStream_t);
-template cudaError_t launch_fields<double, double>(const void*, const Geometry&,
-                                                   const Consts<double>&, double*, double*,
-                                                   double*, double*, double*, cudaStream_t);
-template cudaError_t launch_fields<float, float>(const void*, const Geometry&,
-                                                 const Consts<float>&, double*, double*,
-                                                 double*, double*, double*, cudaStream_t);
-template cudaError_t launch_pack<double>(const void*, double*, const Geometry&, cudaStream_t);
-template cudaError_t launch_pack<float>(const void*, double*, const Geometry&, cudaStream_t);
-template cudaError_t launch_unpack<double>(const double*, void*, const Geometry&, cudaStream_t);
-template cudaError_t launch_unpack<float>(const double*, void*, const Geometry&, cudaStream_t);
+#define CMLBM_INSTANTIATE(R, S)                                                                   \
+    template size_t step_smem_bytes<S>(int);                                                    \
+    template cudaError_t configure_step<R, S>(int);                                             \
+    template int step_blocks_per_sm<R, S>(int);                                                 \
+    template cudaError_t configure_batch<R, S>(int);                                            \
+    template cudaError_t build_batch_graph<R, S>(void*, const BatchCase<R>*, const int2*, int,  \
+                                                 int, int, int*, int, cudaGraphExec_t*);        \
+    template cudaError_t launch_batch_step<R, S>(void*, const BatchCase<R>*, const int2*, int,  \
+                                                 int, int, int*, cudaStream_t);                 \
+    template cudaError_t build_step_graph<R, S>(const void*, const void*, const Geometry&,      \
+                                                const Consts<R>&, int, int, int*, int,          \
+                                                cudaGraphExec_t*);                              \
+    template cudaError_t launch_step<R, S>(const void*, void*, const Geometry&,                 \
+                                           const Consts<R>&, int, int, int*, cudaStream_t);     \
+    template cudaError_t launch_init<R, S>(const double*, const double*, const double*,         \
+                                           const double*, void*, const Geometry&,               \
+                                           const Consts<R>&, cudaStream_t);                     \
+    template cudaError_t launch_fields<R, S>(const void*, const Geometry&, const Consts<R>&,    \
+                                             double*, double*, double*, double*, double*,       \
+                                             cudaStream_t);
+
+// Populations are copied in and out in double; the codec of the 16-bit formats is applied in
+// double there so that a value read out and written back is stored exactly as before.
+#define CMLBM_INSTANTIATE_PACK(S)                                                                 \
+    template cudaError_t launch_pack<double, S>(const void*, double*, const Geometry&,          \
+                                                const Consts<double>&, cudaStream_t);           \
+    template cudaError_t launch_unpack<double, S>(const double*, void*, const Geometry&,        \
+                                                  const Consts<double>&, cudaStream_t);
+
+CMLBM_INSTANTIATE(double, double)
+CMLBM_INSTANTIATE(float, float)
+CMLBM_INSTANTIATE(float, __half)
+CMLBM_INSTANTIATE(float, __nv_bfloat16)
+CMLBM_INSTANTIATE_PACK(double)
+CMLBM_INSTANTIATE_PACK(float)
+CMLBM_INSTANTIATE_PACK(__half)
+CMLBM_INSTANTIATE_PACK(__nv_bfloat16)
+#undef CMLBM_INSTANTIATE
+#undef CMLBM_INSTANTIATE_PACK
 
 }  // namespace cmlbm

@@ -27,7 +27,9 @@ LBM_ERR_TIMEOUT = -8
 
 LBM_FP64 = 0
 LBM_FP32 = 1
-PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32}
+LBM_FP32_FP16 = 2
+LBM_FP32_BF16 = 3
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP32_FP16, "bf16": LBM_FP32_BF16}
 
 LBM_PERIODIC = 0
 LBM_WALL = 1
@@ -62,6 +64,8 @@ class lbm_params(ctypes.Structure):
         ("gx", ctypes.c_double), ("gy", ctypes.c_double), ("rho_ref", ctypes.c_double),
         ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
+        ("store_scale_g", ctypes.c_double), ("store_scale_f", ctypes.c_double),
+        ("store_ref_g", ctypes.c_double),
     ]
 
 
@@ -158,7 +162,9 @@ def make_params(case: dict, precision="fp32", device=0, stream=0) -> lbm_params:
         float(case.get("T0", 0.0)), float(case.get("gradT_x", 0.0)),
         float(case.get("gradT_y", 0.0)), float(case["mobility"]), float(case["width"]),
         float(case.get("gx", 0.0)), float(case.get("gy", 0.0)), float(case.get("rho_ref", 0.0)),
-        prec, int(device), ctypes.c_void_p(int(stream)))
+        prec, int(device), ctypes.c_void_p(int(stream)),
+        float(case.get("store_scale_g", 0.0)), float(case.get("store_scale_f", 0.0)),
+        float(case.get("store_ref_g", 0.0)))
 
 
 # ---- ABI wrappers (same names as the C entry points) ------------------------------------------

