@@ -79,8 +79,8 @@ def kernel_source_hash() -> str:
 # DRAM traffic per launch of the step kernel from an ncu capture (profiles/), keyed by the
 # hash of the kernel sources it was taken on; scaled by node count to the bench workload.
 NCU_TRAFFIC = {
-    # profiles/step_kernel_impact_2048x1024_fp32.md (read 152.64 MB + write 98.29 MB)
-    ("f9ec9254c6c8c845", "impact", "fp32"): 250_936_832,
+    # profiles/step_kernel_impact_2048x1024_fp32.md (read 152.59 MB + write 98.80 MB)
+    ("111f7b57711cb659", "impact", "fp32"): 251_388_416,
 }
 
 
