@@ -40,6 +40,18 @@
  *   R10 initial populations are the equilibria (no -S/2 shift); the interface equilibrium at
  *       initialisation has its M_phi theta n term set to zero.
  *   R11 F_ext = (rho - rho_ref) g.
+ *   R14 free-slip walls (Secs. 6.4-6.6): specular reflection half a node outside the last node;
+ *       a population crossing such a wall keeps its tangential velocity, reverses the normal
+ *       one and lands on the tangential neighbour inside; a population crossing a free-slip
+ *       and a no-slip wall at a corner bounces back.  Stencils use mirror ghosts as in R8.
+ *   R15 single relaxation time (Sec. 7): the cascaded operators of Secs. 4 and 5 with every
+ *       relaxation rate equal to the shear rate (fluid) or to omega^phi_{1,2} (interface); with
+ *       equal rates both reduce to relaxing all central moments at one rate.
+ *   R16 Langmuir isotherm (Sec. 6.7): kappa-tilde(psi) = (3/2) W sigma0 [1 + beta ln(1 - psi)]
+ *       for an imposed psi = psi0 + gradpsi . x, with the analytic gradient of kappa-tilde.
+ *   R17 imposed shear flow (Sec. 6.1): the interface lattice alone, advected by the single-vortex
+ *       field at node positions (x, y) = (i, j) with L0 = nx along x and ny along y, reversed for
+ *       time levels t >= reverse_step; the fluid populations are carried unchanged.
  *
  * Layout: a population field is 9 planes [alpha][y][x], plane size nx*ny, row-major in x.
  * Node coordinates are (x, y) = (i, j), i in [0, nx), j in [0, ny).
@@ -59,15 +71,29 @@ static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 /* Regularisation of the interface normal (reading R6). */
 #define NORMAL_EPS 1e-6
 
+/* Boundary kind of one side of the grid. */
+#define BC_PERIODIC 0
+#define BC_NOSLIP 1
+#define BC_FREESLIP 2
+
 typedef struct {
     int nx, ny;
-    int wall_x, wall_y;        /* 0 periodic, 1 no-slip walls on both ends */
+    int bc_x0, bc_x1;          /* left (x = 0) and right (x = nx - 1) sides: BC_* */
+    int bc_y0, bc_y1;          /* bottom (y = 0) and top (y = ny - 1) sides */
     double rho_a, rho_b;       /* phase A is phi = 1 */
     double mu_a, mu_b;         /* dynamic viscosities */
     double sigma0, dsigma_dT;  /* sigma(T) = sigma0 + dsigma_dT (T - T0) */
     double T0, gradT_x, gradT_y;   /* T(x, y) = T0 + gradT_x x + gradT_y y */
     double mobility, width;    /* M_phi, W */
     double gx, gy, rho_ref;    /* F_ext = (rho - rho_ref) (gx, gy) */
+    int collision;             /* 0 cascaded (Secs. 4, 5); 1 single relaxation time (R15) */
+    int sigma_model;           /* 0 sigma linear in T; 1 Langmuir isotherm in psi (R16) */
+    double beta;               /* Gibbs elasticity number of the Langmuir isotherm */
+    double psi0, gradpsi_x, gradpsi_y;   /* imposed psi = psi0 + gradpsi_x x + gradpsi_y y */
+    int flow;                  /* 0 coupled lattices; 1 interface lattice in the imposed shear (R17) */
+    int reverse_step;          /* imposed flow reversed for t >= reverse_step (<= 0: never) */
+    double u0;                 /* imposed flow amplitude U_0 */
+    int t;                     /* time level of the state (used by the imposed flow only) */
 } orc_case;
 
 /* Per-node macroscopic quantities of a step, exposed for the tests. */
@@ -334,13 +360,40 @@ void orc_ace_collide(const double f[9], double ux, double uy, double jx, double 
 
 static inline int wrap(int v, int n) { v %= n; return v < 0 ? v + n : v; }
 
-/* Nodal field value at (x+dx, y+dy): periodic wrap, or at a wall the mirror ghost of R8. */
+/* Index of a column / row just outside the grid: periodic wrap, or at a wall (either kind) the
+ * mirror ghost of R8 / R14, i.e. the first or last node. */
+static int ghost_col(const orc_case* c, int xx)
+{
+    if (xx >= 0 && xx < c->nx) return xx;
+    if (xx < 0) return c->bc_x0 == BC_PERIODIC ? wrap(xx, c->nx) : 0;
+    return c->bc_x1 == BC_PERIODIC ? wrap(xx, c->nx) : c->nx - 1;
+}
+
+static int ghost_row(const orc_case* c, int yy)
+{
+    if (yy >= 0 && yy < c->ny) return yy;
+    if (yy < 0) return c->bc_y0 == BC_PERIODIC ? wrap(yy, c->ny) : 0;
+    return c->bc_y1 == BC_PERIODIC ? wrap(yy, c->ny) : c->ny - 1;
+}
+
+/* R17: the imposed single-vortex shear flow of Sec. 6.1 at node (x, y) and time level t,
+ *   u_x = -U_0 pi cos(pi (x/L0 - 1/2)) sin(pi (y/L0 - 1/2)),
+ *   u_y =  U_0 pi sin(pi (x/L0 - 1/2)) cos(pi (y/L0 - 1/2)),
+ * with L0 = nx along x and ny along y, and the sign reversed for t >= reverse_step. */
+#define ORC_PI 3.14159265358979323846
+static void imposed_velocity(const orc_case* c, int x, int y, int t, double* ux, double* uy)
+{
+    const double s = (c->reverse_step > 0 && t >= c->reverse_step) ? -1.0 : 1.0;
+    const double ax = ORC_PI * ((double)x / c->nx - 0.5);
+    const double ay = ORC_PI * ((double)y / c->ny - 0.5);
+    *ux = -s * c->u0 * ORC_PI * cos(ax) * sin(ay);
+    *uy = s * c->u0 * ORC_PI * sin(ax) * cos(ay);
+}
+
+/* Nodal field value at (x+dx, y+dy). */
 static double field_at(const orc_case* c, const double* a, int x, int y, int dx, int dy)
 {
-    int xx = x + dx, yy = y + dy;
-    if (xx < 0 || xx >= c->nx) xx = c->wall_x ? (xx < 0 ? 0 : c->nx - 1) : wrap(xx, c->nx);
-    if (yy < 0 || yy >= c->ny) yy = c->wall_y ? (yy < 0 ? 0 : c->ny - 1) : wrap(yy, c->ny);
-    return a[(size_t)yy * c->nx + xx];
+    return a[(size_t)ghost_row(c, y + dy) * c->nx + ghost_col(c, x + dx)];
 }
 
 /* Second-order isotropic finite differences on the D2Q9 stencil (Sec. 4, closing remark):
@@ -431,11 +484,22 @@ static void node_macros(const orc_case* c, const double* phi, const double* pst,
         o->ny = o->dphiy / (gm + NORMAL_EPS);
         const double nHn = o->nx * o->nx * o->hxx + 2.0 * o->nx * o->ny * o->hxy
                            + o->ny * o->ny * o->hyy;
-        const double T = c->T0 + c->gradT_x * x + c->gradT_y * y;
-        const double sigma = c->sigma0 + c->dsigma_dT * (T - c->T0);
-        const double kt = 1.5 * sigma * c->width;                      /* R4 */
-        const double dktx = 1.5 * c->width * c->dsigma_dT * c->gradT_x;
-        const double dkty = 1.5 * c->width * c->dsigma_dT * c->gradT_y;
+        double kt, dktx, dkty;   /* kappa-tilde = (3/2) sigma W (R4) and its gradient */
+        if (c->sigma_model == 1) {
+            /* R16: Langmuir isotherm sigma = sigma0 [1 + beta ln(1 - psi)], psi imposed */
+            const double psi = c->psi0 + c->gradpsi_x * x + c->gradpsi_y * y;
+            const double sigma = c->sigma0 * (1.0 + c->beta * log(1.0 - psi));
+            const double dsigma_dpsi = -c->sigma0 * c->beta / (1.0 - psi);
+            kt = 1.5 * sigma * c->width;
+            dktx = 1.5 * c->width * dsigma_dpsi * c->gradpsi_x;
+            dkty = 1.5 * c->width * dsigma_dpsi * c->gradpsi_y;
+        } else {
+            const double T = c->T0 + c->gradT_x * x + c->gradT_y * y;
+            const double sigma = c->sigma0 + c->dsigma_dT * (T - c->T0);
+            kt = 1.5 * sigma * c->width;
+            dktx = 1.5 * c->width * c->dsigma_dT * c->gradT_x;
+            dkty = 1.5 * c->width * c->dsigma_dT * c->gradT_y;
+        }
         const double curv = gm * (o->lap - nHn);                       /* |grad phi|^2 div n */
         o->Fsx = -kt * curv * o->nx
                  + g2 * ((1.0 - o->nx * o->nx) * dktx - o->nx * o->ny * dkty);
@@ -464,8 +528,7 @@ static void zeroth_moments_rows(const orc_case* c, const double* g, const double
     int lo = y0 - 1, hi = y1;
     if (hi - lo + 1 >= c->ny) { lo = 0; hi = c->ny - 1; }
     for (int yr = lo; yr <= hi; ++yr) {
-        int y = yr;
-        if (y < 0 || y >= c->ny) y = c->wall_y ? (y < 0 ? 0 : c->ny - 1) : wrap(y, c->ny);
+        const int y = ghost_row(c, yr);
         for (int x = 0; x < c->nx; ++x) {
             const size_t n = (size_t)y * c->nx + x;
             double sp = 0.0, sg = 0.0;
@@ -515,6 +578,10 @@ void orc_fields(const orc_case* c, const double* g, const double* f, double* phi
             for (int q = 0; q < 9; ++q) gb[q] = g[q * N + n];
             orc_node o;
             node_macros(c, phi, pst, gb, x, y, &o);
+            if (c->flow == 1) {   /* R17: u imposed, no pressure field */
+                imposed_velocity(c, x, y, c->t, &o.ux, &o.uy);
+                o.p = 0.0;
+            }
             if (phi_out) phi_out[n] = o.phi;
             if (p_out) p_out[n] = o.p;
             if (ux_out) ux_out[n] = o.ux;
@@ -542,23 +609,45 @@ void orc_node_info(const orc_case* c, const double* g, const double* f, int x, i
 }
 
 /* Destination of the population leaving (x, y) along alpha: the neighbour x + e_alpha (periodic
- * wrap), or, when that crosses a wall, the same node in the opposite direction (half-way
- * bounce-back, R8).  Returns the flat index into the 9-plane field. */
+ * wrap).  Where that crosses a no-slip wall, the same node in the opposite direction (half-way
+ * bounce-back, R8); where it crosses only free-slip walls, the normal components crossing them
+ * are reversed and the population stays on that side of the wall (specular reflection, R14).
+ * Returns the flat index into the 9-plane field. */
+static int direction_of(int ex, int ey)
+{
+    for (int q = 0; q < 9; ++q)
+        if (EX[q] == ex && EY[q] == ey) return q;
+    return -1;
+}
+
 static size_t stream_target(const orc_case* c, int q, int x, int y)
 {
     static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
     const size_t N = (size_t)c->nx * c->ny;
-    int xx = x + EX[q], yy = y + EY[q];
-    int bounce = 0;
-    if (xx < 0 || xx >= c->nx) { if (c->wall_x) bounce = 1; else xx = wrap(xx, c->nx); }
-    if (yy < 0 || yy >= c->ny) { if (c->wall_y) bounce = 1; else yy = wrap(yy, c->ny); }
-    if (bounce) return (size_t)OPP[q] * N + (size_t)y * c->nx + x;
-    return (size_t)q * N + (size_t)yy * c->nx + xx;
+    int ex = EX[q], ey = EY[q];
+    int xx = x + ex, yy = y + ey;
+    int cross_x = 0, cross_y = 0, noslip = 0;
+    if (xx < 0 || xx >= c->nx) {
+        const int kind = xx < 0 ? c->bc_x0 : c->bc_x1;
+        if (kind == BC_PERIODIC) xx = wrap(xx, c->nx);
+        else { cross_x = 1; noslip |= kind == BC_NOSLIP; }
+    }
+    if (yy < 0 || yy >= c->ny) {
+        const int kind = yy < 0 ? c->bc_y0 : c->bc_y1;
+        if (kind == BC_PERIODIC) yy = wrap(yy, c->ny);
+        else { cross_y = 1; noslip |= kind == BC_NOSLIP; }
+    }
+    if (noslip) return (size_t)OPP[q] * N + (size_t)y * c->nx + x;
+    if (cross_x) { ex = -ex; xx = x; }
+    if (cross_y) { ey = -ey; yy = y; }
+    return (size_t)direction_of(ex, ey) * N + (size_t)yy * c->nx + xx;
 }
 
 /* Rows [y0, y1) of one time step: collide both lattices at every node of those rows (Secs. 4
  * and 5) and stream the post-collision populations, g-bar(x + e, t + 1) = g-bar-tilde(x, t) and
- * f likewise.  Restricting the rows serves only to time a bounded sample of a large grid. */
+ * f likewise.  Restricting the rows serves only to time a bounded sample of a large grid.
+ * Relaxation rates: R9 (cascaded) or all equal (R15).  With the imposed flow (R17) only the
+ * interface lattice collides and streams; the fluid populations are copied unchanged. */
 void orc_step_rows(const orc_case* c, const double* g, const double* f, double* g_new,
                    double* f_new, int y0, int y1)
 {
@@ -567,8 +656,10 @@ void orc_step_rows(const orc_case* c, const double* g, const double* f, double* 
     double* pst = (double*)malloc(N * sizeof(double));
     zeroth_moments_rows(c, g, f, phi, pst, y0, y1);
 
+    const int srt = c->collision == 1;
     const double omega_phi = 1.0 / (c->mobility / CS2 + 0.5);   /* Sec. 5: M_phi relation */
-    const double om_f[9] = {1.0, omega_phi, omega_phi, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0};
+    const double o3 = srt ? omega_phi : 1.0;
+    const double om_f[9] = {o3, omega_phi, omega_phi, o3, o3, o3, o3, o3, o3};
 
 #pragma omp parallel for schedule(static)
     for (int y = y0; y < y1; ++y) {
@@ -576,9 +667,25 @@ void orc_step_rows(const orc_case* c, const double* g, const double* f, double* 
             const size_t n = (size_t)y * c->nx + x;
             double gb[9], fq[9], go[9], fo[9];
             for (int q = 0; q < 9; ++q) { gb[q] = g[q * N + n]; fq[q] = f[q * N + n]; }
+            if (c->flow == 1) {
+                double dphx, dphy, ux, uy;
+                stencil(c, phi, x, y, &dphx, &dphy, NULL, NULL, NULL, NULL);
+                const double gm = sqrt(dphx * dphx + dphy * dphy);
+                const double theta = 4.0 * phi[n] * (1.0 - phi[n]) / c->width;
+                imposed_velocity(c, x, y, c->t, &ux, &uy);
+                const double nx = dphx / (gm + NORMAL_EPS), ny = dphy / (gm + NORMAL_EPS);
+                orc_ace_collide(fq, ux, uy, c->mobility * theta * nx, c->mobility * theta * ny,
+                                om_f, fo, NULL);
+                for (int q = 0; q < 9; ++q) {
+                    f_new[stream_target(c, q, x, y)] = fo[q];
+                    g_new[q * N + n] = gb[q];
+                }
+                continue;
+            }
             orc_node o;
             node_macros(c, phi, pst, gb, x, y, &o);
-            const double om_g[9] = {1.0, 1.0, 1.0, 1.0, o.omega_nu, o.omega_nu, 1.0, 1.0, 1.0};
+            const double w = o.omega_nu, r = srt ? w : 1.0;
+            const double om_g[9] = {r, r, r, r, w, w, r, r, r};
             orc_fluid_collide(gb, o.p, o.ux, o.uy, o.rho, o.Ftx, o.Fty, o.Fpx, o.Fpy, om_g, go,
                               NULL);
             const double jx = c->mobility * o.theta * o.nx;
@@ -606,8 +713,10 @@ void orc_step(const orc_case* c, const double* g, const double* f, double* g_new
 void orc_run(const orc_case* c, double* g, double* f, double* g_tmp, double* f_tmp, int nsteps)
 {
     const size_t bytes = (size_t)9 * c->nx * c->ny * sizeof(double);
+    orc_case cs = *c;
     for (int s = 0; s < nsteps; ++s) {
-        orc_step(c, g, f, g_tmp, f_tmp);
+        cs.t = c->t + s;
+        orc_step(&cs, g, f, g_tmp, f_tmp);
         memcpy(g, g_tmp, bytes);
         memcpy(f, f_tmp, bytes);
     }

@@ -11,6 +11,7 @@ import ctypes
 import os
 import subprocess
 from dataclasses import dataclass
+from typing import Optional
 
 import numpy as np
 
@@ -42,14 +43,34 @@ def build(force: bool = False) -> str:
 class _Case(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int), ("ny", ctypes.c_int),
-        ("wall_x", ctypes.c_int), ("wall_y", ctypes.c_int),
+        ("bc_x0", ctypes.c_int), ("bc_x1", ctypes.c_int),
+        ("bc_y0", ctypes.c_int), ("bc_y1", ctypes.c_int),
         ("rho_a", ctypes.c_double), ("rho_b", ctypes.c_double),
         ("mu_a", ctypes.c_double), ("mu_b", ctypes.c_double),
         ("sigma0", ctypes.c_double), ("dsigma_dT", ctypes.c_double),
         ("T0", ctypes.c_double), ("gradT_x", ctypes.c_double), ("gradT_y", ctypes.c_double),
         ("mobility", ctypes.c_double), ("width", ctypes.c_double),
         ("gx", ctypes.c_double), ("gy", ctypes.c_double), ("rho_ref", ctypes.c_double),
+        ("collision", ctypes.c_int), ("sigma_model", ctypes.c_int),
+        ("beta", ctypes.c_double), ("psi0", ctypes.c_double),
+        ("gradpsi_x", ctypes.c_double), ("gradpsi_y", ctypes.c_double),
+        ("flow", ctypes.c_int), ("reverse_step", ctypes.c_int),
+        ("u0", ctypes.c_double), ("t", ctypes.c_int),
     ]
+
+
+# boundary kinds of one side (wall_x / wall_y and their *_hi overrides)
+PERIODIC, NOSLIP, FREESLIP = 0, 1, 2
+
+
+def side_kinds(lo, hi):
+    """(low side, high side) kinds of one axis: ``lo`` is 0 / False (periodic), 1 / True
+    (no-slip) or 2 (free-slip) and applies to both sides unless ``hi`` (None = same) is given."""
+    lo = int(lo)
+    hi = lo if hi is None or int(hi) == 0 else int(hi)
+    if lo not in (0, 1, 2) or hi not in (0, 1, 2) or (lo == 0) != (hi == 0):
+        raise ValueError(f"invalid boundary pair ({lo}, {hi})")
+    return lo, hi
 
 
 class _Node(ctypes.Structure):
@@ -61,11 +82,18 @@ class _Node(ctypes.Structure):
 
 @dataclass
 class OracleCase:
-    """Physical parameters of one case (the paper's statement of the problem)."""
+    """Physical parameters of one case (the paper's statement of the problem).
+
+    wall_x / wall_y: boundary kind of the left+right / bottom+top sides (0 or False periodic,
+    1 or True no-slip, 2 free-slip); wall_x_hi / wall_y_hi override the right / top side.
+    collision: 0 cascaded, 1 single relaxation time.  sigma_model: 0 sigma linear in T, 1
+    Langmuir isotherm in the imposed psi.  flow: 0 coupled lattices, 1 interface lattice alone in
+    the imposed reversing shear flow (amplitude u0, reversed for time levels >= reverse_step);
+    t: time level of the state that step / run start from."""
     nx: int
     ny: int
-    wall_x: bool = False
-    wall_y: bool = False
+    wall_x: int = 0
+    wall_y: int = 0
     rho_a: float = 1.0
     rho_b: float = 1.0
     mu_a: float = 0.1
@@ -80,12 +108,28 @@ class OracleCase:
     gx: float = 0.0
     gy: float = 0.0
     rho_ref: float = 0.0
+    wall_x_hi: Optional[int] = None
+    wall_y_hi: Optional[int] = None
+    collision: int = 0
+    sigma_model: int = 0
+    beta: float = 0.0
+    psi0: float = 0.0
+    gradpsi_x: float = 0.0
+    gradpsi_y: float = 0.0
+    flow: int = 0
+    reverse_step: int = 0
+    u0: float = 0.0
+    t: int = 0
 
     def c(self) -> _Case:
-        return _Case(int(self.nx), int(self.ny), int(bool(self.wall_x)), int(bool(self.wall_y)),
+        bx0, bx1 = side_kinds(self.wall_x, self.wall_x_hi)
+        by0, by1 = side_kinds(self.wall_y, self.wall_y_hi)
+        return _Case(int(self.nx), int(self.ny), bx0, bx1, by0, by1,
                      self.rho_a, self.rho_b, self.mu_a, self.mu_b, self.sigma0, self.dsigma_dT,
                      self.T0, self.gradT_x, self.gradT_y, self.mobility, self.width,
-                     self.gx, self.gy, self.rho_ref)
+                     self.gx, self.gy, self.rho_ref, int(self.collision), int(self.sigma_model),
+                     self.beta, self.psi0, self.gradpsi_x, self.gradpsi_y, int(self.flow),
+                     int(self.reverse_step), self.u0, int(self.t))
 
     @classmethod
     def from_dict(cls, d: dict) -> "OracleCase":
