@@ -22,7 +22,11 @@
  *     shear rates from mu (Eq. fluidviscosity), all other rates 1;
  *   - the interface (conservative Allen-Cahn) cascaded collision with M_phi theta n in its
  *     first-order equilibria (Sec. 5), omega^phi_{1,2} from M_phi, all other rates 1;
- *   - streaming of both lattices, with half-way bounce-back at no-slip walls.
+ *   - streaming of both lattices, with half-way bounce-back at no-slip walls and specular
+ *     reflection at free-slip walls.
+ * lbm_params also selects the paper's other forms: the single-relaxation-time operators of its
+ * stability comparison (Sec. 7), the Langmuir isotherm of its surfactant Marangoni case (Sec.
+ * 6.7) and the interface lattice alone in its imposed reversing shear flow (Sec. 6.1).
  *
  * Conventions: c_s^2 = 1/3, lattice units (dx = dt = 1).  Node (i, j) is at x = i, y = j.
  * Host nodal arrays are row-major [ny][nx] doubles.  Population arrays are [9][ny][nx] doubles
@@ -59,7 +63,9 @@ extern "C" {
 #define LBM_ERR_NOMEM (-4)      /* device allocation failed */
 #define LBM_ERR_STATE (-5)      /* the state was never initialised */
 #define LBM_ERR_NONFINITE (-6)  /* a diagnostic found NaN or Inf in the fields */
-#define LBM_ERR_UNSUPPORTED (-7)/* precision mode not built into this library */
+#define LBM_ERR_UNSUPPORTED (-7)/* precision mode not built into this library, or a collision
+                                   model / flow mode not offered with the precision or in a
+                                   batch */
 #define LBM_ERR_TIMEOUT (-8)    /* a bounded wait inside the step kernel gave up; the state of
                                    that step is invalid (reported by the next synchronising
                                    call or lbm_check) */
@@ -77,12 +83,47 @@ typedef enum {
  * 0 the defaults 2^14 / 2^8 for FP16 (|g-bar| up to ~4 without overflow, deviations above
  * ~4e-9 kept normal) and 1 / 1 for BF16.  Collisions, forces and stencils stay in float. */
 
-/* Boundary pair along one axis. */
+/* Boundary kind of the sides of one axis. */
 typedef enum {
     LBM_PERIODIC = 0,
-    LBM_WALL = 1   /* no-slip walls half a node outside the first and last node (half-way
-                      bounce-back on both lattices; mirror ghosts for the stencils) */
+    LBM_WALL = 1,      /* no-slip wall half a node outside the first / last node (half-way
+                          bounce-back on both lattices; mirror ghosts for the stencils) */
+    LBM_FREESLIP = 2   /* free-slip wall (Secs. 6.4-6.6) half a node outside the first / last
+                          node: a population crossing it reverses its normal velocity and lands on
+                          the tangential neighbour inside (specular reflection); at a corner with
+                          a no-slip side it bounces back; mirror ghosts for the stencils */
 } lbm_bc;
+
+/* Collision model of both lattices. */
+typedef enum {
+    LBM_CASCADED = 0,  /* the cascaded operators of Secs. 4 and 5 (rates as above) */
+    LBM_SRT = 1        /* single relaxation time, the comparison model of Sec. 7: the same
+                          operators with every rate equal to the shear rate (fluid) and to
+                          omega^phi_{1,2} (interface), i.e. BGK towards the same equilibria with
+                          the same sources.  LBM_FP64 / LBM_FP32 only. */
+} lbm_collision;
+
+/* Surface tension law. */
+typedef enum {
+    LBM_SIGMA_LINEAR_T = 0,  /* sigma = sigma0 + dsigma_dT (T - T0), T = T0 + gradT . x */
+    LBM_SIGMA_LANGMUIR = 1   /* Langmuir isotherm (Sec. 6.7 Eq. Langmuirisotherm):
+                                sigma = sigma0 [1 + beta ln(1 - psi)] in the imposed surfactant
+                                concentration psi = psi0 + gradpsi_x x + gradpsi_y y (psi < 1 on
+                                the whole grid); kappa-tilde = (3/2) sigma W with its analytic
+                                gradient in the Marangoni force */
+} lbm_sigma_model;
+
+/* What is advanced. */
+typedef enum {
+    LBM_FLOW_COUPLED = 0,  /* both lattices, coupled (the method) */
+    LBM_FLOW_SHEAR = 1     /* the interface lattice alone in the imposed shear flow of Sec. 6.1,
+                              u_x = -U_0 pi cos(pi (x/nx - 1/2)) sin(pi (y/ny - 1/2)),
+                              u_y =  U_0 pi sin(pi (x/nx - 1/2)) cos(pi (y/ny - 1/2)),
+                              reversed (both signs) for time levels t >= reverse_step when
+                              reverse_step > 0.  The fluid populations are not advanced and their
+                              content is unspecified; lbm_get_fields reports this u and p = 0.
+                              LBM_FP64 / LBM_FP32 only. */
+} lbm_flow;
 
 /* Problem statement of one case (Secs. 2, 4-6 of the paper). */
 typedef struct {
@@ -99,6 +140,19 @@ typedef struct {
     void* stream;                   /* cudaStream_t for all work of the context */
     double store_scale_g, store_scale_f;  /* 16-bit storage scales; 0 = default */
     double store_ref_g;             /* 16-bit storage reference pressure of the fluid lattice */
+    /* Further forms of the paper's cases; all zero gives the coupled cascaded step above. */
+    int32_t bc_x_hi, bc_y_hi;       /* lbm_bc of the right (x = nx - 1) / top (y = ny - 1) side
+                                       when it differs from bc_x / bc_y (which then name the
+                                       left / bottom side); 0 = same as bc_x / bc_y.  A periodic
+                                       axis is periodic on both sides. */
+    int32_t collision;              /* lbm_collision */
+    int32_t sigma_model;            /* lbm_sigma_model */
+    double beta;                    /* Langmuir: Gibbs elasticity number */
+    double psi0, gradpsi_x, gradpsi_y;   /* Langmuir: imposed psi = psi0 + gradpsi . x */
+    int32_t flow;                   /* lbm_flow */
+    int32_t reverse_step;           /* LBM_FLOW_SHEAR: time level from which the field reverses
+                                       (<= 0: never) */
+    double u0;                      /* LBM_FLOW_SHEAR: amplitude U_0 */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -221,7 +275,9 @@ int lbm_diagnostics_noalloc(const double* phi, const double* p, const double* ux
 typedef struct lbm_batch lbm_batch;
 
 /* params: array of ncases (>= 1) cases; precision, device and stream must be equal in all of
- * them.  One device allocation holds every case's two state buffers (zeroed). */
+ * them.  One device allocation holds every case's two state buffers (zeroed).  Cases may mix
+ * boundary kinds; every case must take the cascaded coupled step with the linear sigma(T)
+ * (LBM_CASCADED, LBM_FLOW_COUPLED, LBM_SIGMA_LINEAR_T), else LBM_ERR_UNSUPPORTED. */
 int lbm_batch_create(const lbm_params* params, int32_t ncases, lbm_batch** out);
 
 /* Equilibrium initialisation of case c from host fields ([ny][nx] doubles of that case), as

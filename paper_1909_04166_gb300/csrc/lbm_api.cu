@@ -3,6 +3,7 @@
 // lbm_step.cu and the reductions below; nothing here computes physics on the host.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -32,7 +33,8 @@ struct lbm_ctx {
     double* scratch;       // nodal fields for diagnostics / field extraction (5 N doubles)
     double* partials;      // reduction partials
     int* err;              // device error word of the step kernel (bounded waits)
-    cudaGraphExec_t graph[2];   // kGraphChunk steps starting from buffer 0 / buffer 1
+    int variant;           // step variant (lbm_host.h step_variant)
+    cudaGraphExec_t graph[2][2];   // kGraphChunk steps from buffer 0 / 1, flow sign + / -
     int use_graph;
     int nsm;
     int last_cuda;
@@ -62,8 +64,8 @@ void* cur_state(lbm_ctx* c) { return c->buf + (size_t)c->cur * c->state_bytes; }
 // about once (one wave): warps = strips * ceil(ny / rows).
 int default_seg_rows(const lbm_ctx* c)
 {
-    const int bps = with_types(c->P.precision, [&](auto r, auto s) {
-        return step_blocks_per_sm<decltype(r), decltype(s)>(c->block);
+    const int bps = with_variant(c->P.precision, c->variant, [&](auto r, auto s, auto v) {
+        return step_blocks_per_sm<decltype(r), decltype(s), decltype(v)::value>(c->block);
     });
     const long long resident = (long long)c->nsm * bps * (c->block / 32);
     const long long strips = c->G.nstrips;
@@ -77,38 +79,49 @@ int default_seg_rows(const lbm_ctx* c)
 
 cudaError_t configure(lbm_ctx* c)
 {
-    return with_types(c->P.precision, [&](auto r, auto s) {
-        return configure_step<decltype(r), decltype(s)>(c->block);
+    return with_variant(c->P.precision, c->variant, [&](auto r, auto s, auto v) {
+        return configure_step<decltype(r), decltype(s), decltype(v)::value>(c->block);
     });
 }
 
 void drop_graphs(lbm_ctx* c)
 {
     for (int k = 0; k < 2; ++k)
-        if (c->graph[k]) {
-            cudaGraphExecDestroy(c->graph[k]);
-            c->graph[k] = nullptr;
-        }
+        for (int d = 0; d < 2; ++d)
+            if (c->graph[k][d]) {
+                cudaGraphExecDestroy(c->graph[k][d]);
+                c->graph[k][d] = nullptr;
+            }
 }
 
-cudaError_t launch_one(lbm_ctx* c, const void* src, void* dst)
+// Sign of the imposed flow for the step from time level t (+1 before the reversal, -1 from it
+// on); 0 when the case advances the coupled lattices.
+int flow_sign_at(const lbm_ctx* c, long long t)
 {
-    return with_types(c->P.precision, [&](auto r, auto s) {
+    if (c->P.flow != LBM_FLOW_SHEAR) return 0;
+    return (c->P.reverse_step > 0 && t >= c->P.reverse_step) ? -1 : 1;
+}
+
+cudaError_t launch_one(lbm_ctx* c, const void* src, void* dst, int sign)
+{
+    return with_variant(c->P.precision, c->variant, [&](auto r, auto s, auto v) {
         using R = decltype(r);
-        return launch_step<R, decltype(s)>(src, dst, c->G, kref<R>(c), c->seg_h, c->block,
-                                           c->err, c->st);
+        return launch_step<R, decltype(s), decltype(v)::value>(
+            src, dst, c->G, kref<R>(c), c->seg_h, c->block, c->err, sign ? sign : 1, c->st);
     });
 }
 
-cudaError_t ensure_graph(lbm_ctx* c, int start)
+cudaError_t ensure_graph(lbm_ctx* c, int start, int sign)
 {
-    if (c->graph[start]) return cudaSuccess;
+    cudaGraphExec_t* slot = &c->graph[start][sign < 0 ? 1 : 0];
+    if (*slot) return cudaSuccess;
     const void* a = c->buf + (size_t)start * c->state_bytes;
     const void* b = c->buf + (size_t)(1 - start) * c->state_bytes;
-    return with_types(c->P.precision, [&](auto r, auto s) {
+    return with_variant(c->P.precision, c->variant, [&](auto r, auto s, auto v) {
         using R = decltype(r);
-        return build_step_graph<R, decltype(s)>(a, b, c->G, kref<R>(c), c->seg_h, c->block,
-                                                c->err, kGraphChunk, &c->graph[start]);
+        return build_step_graph<R, decltype(s), decltype(v)::value>(
+            a, b, c->G, kref<R>(c), c->seg_h, c->block, c->err, sign ? sign : 1, kGraphChunk,
+            slot);
     });
 }
 
@@ -133,11 +146,8 @@ int make_ctx(const lbm_params* params, void* ext, size_t ext_bytes, lbm_ctx** ou
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return LBM_ERR_NOMEM;
     c->P = *params;
-    c->G.nx = params->nx;
-    c->G.ny = params->ny;
-    c->G.nstrips = strips_of(params->nx);
-    c->G.wall_x = params->bc_x == LBM_WALL;
-    c->G.wall_y = params->bc_y == LBM_WALL;
+    c->G = make_geometry(*params);
+    c->variant = step_variant(*params);
     c->Kd = make_consts<double>(*params);
     c->Kf = make_consts<float>(*params);
     c->elem = elem_bytes(params->precision);
@@ -200,7 +210,8 @@ int run_fields(lbm_ctx* c, double* phi, double* p, double* ux, double* uy, doubl
 {
     cudaError_t e = with_types(c->P.precision, [&](auto r, auto s) {
         using R = decltype(r);
-        return launch_fields<R, decltype(s)>(cur_state(c), c->G, kref<R>(c), phi, p, ux, uy, rho,
+        return launch_fields<R, decltype(s)>(cur_state(c), c->G, kref<R>(c),
+                                             flow_sign_at(c, c->steps), phi, p, ux, uy, rho,
                                              c->st);
     });
     return e == cudaSuccess ? LBM_OK : cuda_fail(c, e);
@@ -387,21 +398,29 @@ int lbm_step(lbm_ctx* c, int32_t nsteps)
     if (!c || nsteps < 0) return LBM_ERR_ARG;
     if (!c->initialised) return LBM_ERR_STATE;
     int32_t k = 0;
-    // whole chunks as replays of a prebuilt graph of kGraphChunk launches
-    while (c->use_graph && nsteps - k >= kGraphChunk) {
-        cudaError_t e = ensure_graph(c, c->cur);
-        if (e == cudaSuccess) e = cudaGraphLaunch(c->graph[c->cur], c->st);
-        if (e != cudaSuccess) return cuda_fail(c, e);
-        k += kGraphChunk;
-        c->steps += kGraphChunk;   // even chunk: the current buffer is unchanged
-    }
-    for (; k < nsteps; ++k) {
-        void* src = cur_state(c);
-        void* dst = c->buf + (size_t)(1 - c->cur) * c->state_bytes;
-        cudaError_t e = launch_one(c, src, dst);
-        if (e != cudaSuccess) return cuda_fail(c, e);
-        c->cur = 1 - c->cur;
-        ++c->steps;
+    while (k < nsteps) {
+        // steps until the imposed flow reverses (the sign is constant within a run)
+        const int sign = flow_sign_at(c, c->steps);
+        long long run = nsteps - k;
+        if (sign > 0 && c->P.reverse_step > 0)
+            run = std::min<long long>(run, c->P.reverse_step - c->steps);
+        // whole chunks as replays of a prebuilt graph of kGraphChunk launches
+        while (c->use_graph && run >= kGraphChunk) {
+            cudaError_t e = ensure_graph(c, c->cur, sign);
+            if (e == cudaSuccess) e = cudaGraphLaunch(c->graph[c->cur][sign < 0 ? 1 : 0], c->st);
+            if (e != cudaSuccess) return cuda_fail(c, e);
+            k += kGraphChunk;
+            run -= kGraphChunk;
+            c->steps += kGraphChunk;   // even chunk: the current buffer is unchanged
+        }
+        for (; run > 0; --run, ++k) {
+            void* src = cur_state(c);
+            void* dst = c->buf + (size_t)(1 - c->cur) * c->state_bytes;
+            cudaError_t e = launch_one(c, src, dst, sign);
+            if (e != cudaSuccess) return cuda_fail(c, e);
+            c->cur = 1 - c->cur;
+            ++c->steps;
+        }
     }
     return LBM_OK;
 }
@@ -595,8 +614,7 @@ int lbm_diagnostics_noalloc(const double* phi, const double* p, const double* ux
                             void* stream)
 {
     if (!phi || !p || !ux || !uy || !out || nx < 1 || ny < 1) return LBM_ERR_ARG;
-    if ((bc_x != LBM_PERIODIC && bc_x != LBM_WALL) || (bc_y != LBM_PERIODIC && bc_y != LBM_WALL))
-        return LBM_ERR_ARG;
+    if (!valid_bc(bc_x) || !valid_bc(bc_y)) return LBM_ERR_ARG;
     const long long N = (long long)nx * ny;
     if (N > (long long)kNoAllocMaxBlocks * kNoAllocNodesPerBlock) return LBM_ERR_ARG;
     int dev = 0;
@@ -614,7 +632,7 @@ int lbm_diagnostics_noalloc(const double* phi, const double* p, const double* ux
     }
     const int nb = (int)((N + kNoAllocNodesPerBlock - 1) / kNoAllocNodesPerBlock);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    DiagArgs A{nx, ny, bc_x == LBM_WALL, bc_y == LBM_WALL, xc, yc, r_in, r_out};
+    DiagArgs A{nx, ny, bc_x != LBM_PERIODIC, bc_y != LBM_PERIODIC, xc, yc, r_in, r_out};
     diag_partial_kernel<<<nb, kNoAllocThreads, 0, st>>>(phi, p, ux, uy, A, part);
     diag_store_kernel<<<1, 32, 0, st>>>(part, nb, out);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;

@@ -169,6 +169,7 @@ int lbm_batch_create(const lbm_params* params, int32_t ncases, lbm_batch** out)
         if (params[c].precision != params[0].precision || params[c].device != params[0].device ||
             params[c].stream != params[0].stream)
             return LBM_ERR_ARG;
+        if (step_variant(params[c]) != 0) return LBM_ERR_UNSUPPORTED;
     }
     if (cudaSetDevice(params[0].device) != cudaSuccess) return LBM_ERR_CUDA;
     lbm_batch* b = new (std::nothrow) lbm_batch();
@@ -182,11 +183,7 @@ int lbm_batch_create(const lbm_params* params, int32_t ncases, lbm_batch** out)
     for (int c = 0; c < ncases; ++c) {
         HostCase hc;
         hc.P = params[c];
-        hc.G.nx = params[c].nx;
-        hc.G.ny = params[c].ny;
-        hc.G.nstrips = (params[c].nx + 31) / 32;
-        hc.G.wall_x = params[c].bc_x == LBM_WALL;
-        hc.G.wall_y = params[c].bc_y == LBM_WALL;
+        hc.G = make_geometry(params[c]);
         hc.Kd = make_consts<double>(params[c]);
         hc.Kf = make_consts<float>(params[c]);
         const long long elems = (long long)hc.G.ny * hc.G.nstrips * 18 * 32;
@@ -269,7 +266,7 @@ int lbm_batch_get_fields(lbm_batch* b, int32_t c, double* phi, double* p, double
     double* d = b->scratch;
     cudaError_t e = with_types(b->precision, [&](auto r, auto s) {
         using R = decltype(r);
-        return launch_fields<R, decltype(s)>(case_state(b, c), hc.G, kref<R>(hc), d, d + N,
+        return launch_fields<R, decltype(s)>(case_state(b, c), hc.G, kref<R>(hc), 0, d, d + N,
                                              d + 2 * N, d + 3 * N, d + 4 * N, b->st);
     });
     double* h[5] = {phi, p, ux, uy, rho};

@@ -29,6 +29,13 @@ struct Consts {
     R omega_phi;         // omega^phi_{1,2}, from M_phi = c^2 (1/omega - 1/2)   (Sec. 5)
     R gx, gy, rho_ref;   // F_ext = (rho - rho_ref) g
     R cs2_drho;          // c_s^2 (rho_A - rho_B), the factor of grad rho in F_p
+    // Langmuir isotherm (Sec. 6.7): kappa-tilde = kt0 [1 + beta ln(1 - psi)], psi = psi0 +
+    // gpsx x + gpsy y; replaces the linear kappa-tilde above when langmuir != 0 (the step
+    // kernel's variant selects it at compile time)
+    int langmuir;
+    R beta, psi0, gpsx, gpsy;
+    R u0pi;              // imposed shear flow (Sec. 6.1): U_0 pi
+    R inv_nx, inv_ny;    // 1 / L0 along x and y for the imposed flow
     // 16-bit storage codec, lattice 0 = fluid g-bar, 1 = interface f: the stored number is
     // (q_a - w_a ref) * scale; unused for FP32 / FP64 storage
     R st_scale[2], st_inv[2], st_ref[2];
@@ -103,7 +110,8 @@ __device__ __forceinline__ R decode_sum(const S* q, int stride, int lat, const C
 struct Geometry {
     int nx, ny;
     int nstrips;         // ceil(nx / 32): tiles of 32 columns per row
-    int wall_x, wall_y;
+    int wall_x, wall_y;  // the axis has walls (either kind) instead of a period
+    int slip;            // free-slip sides: bit 0 left, 1 right, 2 bottom, 3 top
 };
 
 // One case of a batch: its geometry and constants, the element offsets of its two state
@@ -152,6 +160,16 @@ __device__ __forceinline__ void lap_hess(const Win<R>& a, R& lap, R& hxx, R& hyy
     hxy = ((a.ne - a.nw) - (a.se - a.sw)) * R(0.25);
 }
 
+template <typename R> __device__ __forceinline__ R log_(R v) { return log(v); }
+template <> __device__ __forceinline__ float log_<float>(float v) { return logf(v); }
+template <typename R> __device__ __forceinline__ void sincospi_(R v, R* s, R* c)
+{
+    sincospi(v, s, c);
+}
+template <> __device__ __forceinline__ void sincospi_<float>(float v, float* s, float* c)
+{
+    sincospif(v, s, c);
+}
 template <typename R> __device__ __forceinline__ R rcp_(R v) { return R(1) / v; }
 template <> __device__ __forceinline__ float rcp_<float>(float v) { return __fdividef(1.0f, v); }
 template <typename R> __device__ __forceinline__ R rsqrt_(R v) { return R(1) / sqrt(v); }
@@ -175,7 +193,7 @@ struct Macro {
 // Forces and corrected fields of one node, from the phi and p* windows and the streamed g-bar
 // first moments (Sec. 2 properties and surface tension, Sec. 6.7 Marangoni components, Sec. 3
 // net gradient pressure force, Sec. 4 Eqs. hydrodynamicfields and fluidviscosity).
-template <typename R>
+template <typename R, bool LANGMUIR = false>
 __device__ __forceinline__ void node_macro(const Win<R>& ph, const Win<R>& ps, R jgx, R jgy,
                                            R xf, R yf, const Consts<R>& K, Macro<R>& m)
 {
@@ -198,11 +216,22 @@ __device__ __forceinline__ void node_macro(const Win<R>& ph, const Win<R>& ps, R
     const R ig = rcp_(gm + R(1e-6));
     const R nx = dphx * ig, ny = dphy * ig;
     const R nHn = nx * nx * hxx + R(2) * nx * ny * hxy + ny * ny * hyy;
-    const R kt = K.kt0 + K.dktx * xf + K.dkty * yf;
+    R kt, dktx, dkty;   // kappa-tilde and its gradient at the node
+    if constexpr (LANGMUIR) {
+        const R om = R(1) - (K.psi0 + K.gpsx * xf + K.gpsy * yf);   // 1 - psi
+        kt = K.kt0 * (R(1) + K.beta * log_(om));
+        const R s = -K.kt0 * K.beta * rcp_(om);                      // d kappa-tilde / d psi
+        dktx = s * K.gpsx;
+        dkty = s * K.gpsy;
+    } else {
+        kt = K.kt0 + K.dktx * xf + K.dkty * yf;
+        dktx = K.dktx;
+        dkty = K.dkty;
+    }
     const R cap = -kt * gm * (lap - nHn);          // -kappa-tilde |grad phi|^2 div n
-    const R nd = nx * K.dktx + ny * K.dkty;         // n . grad kappa-tilde
-    const R Fsx = cap * nx + g2 * (K.dktx - nx * nd);   // + |grad phi|^2 (I - n n) grad kappa-tilde
-    const R Fsy = cap * ny + g2 * (K.dkty - ny * nd);
+    const R nd = nx * dktx + ny * dkty;             // n . grad kappa-tilde
+    const R Fsx = cap * nx + g2 * (dktx - nx * nd);   // + |grad phi|^2 (I - n n) grad kappa-tilde
+    const R Fsy = cap * ny + g2 * (dkty - ny * nd);
     const R dr = m.rho - K.rho_ref;
     m.Ftx = Fsx + dr * K.gx;
     m.Fty = Fsy + dr * K.gy;
@@ -215,6 +244,31 @@ __device__ __forceinline__ void node_macro(const Win<R>& ph, const Win<R>& ps, R
     const R theta_m = K.mob * K.four_over_w * phi * (R(1) - phi);
     m.jx = theta_m * nx;
     m.jy = theta_m * ny;
+}
+
+// Interface quantities of one node for the interface lattice alone (imposed flow): the
+// sharpening flux M_phi theta n from the phi window, as in node_macro.
+template <typename R>
+__device__ __forceinline__ void interface_flux(const Win<R>& ph, const Consts<R>& K, R& jx, R& jy)
+{
+    R dphx, dphy;
+    grad_iso(ph, dphx, dphy);
+    const R gm = norm_(dphx * dphx + dphy * dphy);
+    const R ig = rcp_(gm + R(1e-6));
+    const R theta_m = K.mob * K.four_over_w * ph.c * (R(1) - ph.c);
+    jx = theta_m * (dphx * ig);
+    jy = theta_m * (dphy * ig);
+}
+
+// The imposed single-vortex shear of Sec. 6.1 from the precomputed sin / cos of
+// pi (x / L0 - 1/2) (sx, cx) and pi (y / L0 - 1/2) (sy, cy); sign +1, or -1 once reversed.
+template <typename R>
+__device__ __forceinline__ void imposed_velocity(R sx, R cx, R sy, R cy, R sign,
+                                                 const Consts<R>& K, R& ux, R& uy)
+{
+    const R a = sign * K.u0pi;
+    ux = -a * cx * sy;
+    uy = a * sx * cy;
 }
 
 // Populations from the nine raw moments (00,10,01,20,02,11,21,12,22) of D2Q9: the closed-form
@@ -299,6 +353,114 @@ __device__ __forceinline__ void collide_fluid(R g[9], R pstar, const Macro<R>& m
     const R r10 = rc2 * ux + R(0.5) * third * Ftx;
     const R r01 = rc2 * uy + R(0.5) * third * Fty;
     raw_to_pop_fast(r00, r10, r01, r20, r02, r11, r21, r12, r22, g);
+}
+
+// Fluid-lattice operator of Sec. 4 with every relaxation rate equal to the shear rate omega
+// (single relaxation time, Sec. 7), in raw-moment space.  As in collide_fluid, K (h-hat_3 ..
+// h-hat_8) relaxes the central moments about u of the state V (raw moments of g-bar with the
+// zeroth and first replaced by p and rho c^2 u), here all of orders >= 2 at omega; K (h-hat_0,
+// h-hat_1, h-hat_2) adds omega G00 / 18 K_0 and omega c^2 F_t / 12 (K_1, K_2); with equal rates
+// the cumulative source is (1 - omega/2) times the source itself, whose raw moments are sigma'.
+template <typename R>
+__device__ __forceinline__ void collide_fluid_srt(R g[9], R pstar, const Macro<R>& m)
+{
+    const R third = R(1) / R(3), ninth = R(1) / R(9);
+    const R ux = m.ux, uy = m.uy, p = m.p, rho = m.rho, om = m.omega;
+    const R ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const R rc2 = rho * third;
+    const R psi = p - rc2;
+    // raw moments of g-bar of orders >= 2
+    const R s56 = g[5] + g[6], s78 = g[7] + g[8], d56 = g[5] - g[6], d78 = g[7] - g[8];
+    const R e20 = (g[1] + g[3]) + (s56 + s78);
+    const R e02 = (g[2] + g[4]) + (s56 + s78);
+    const R e11 = d56 + d78, e21 = s56 - s78, e12 = d56 - d78, e22 = s56 + s78;
+    // central moments of V about u
+    const R a2 = p - R(2) * rc2, a3 = R(3) * rc2 - p, a4 = p - R(4) * rc2;
+    const R v20 = e20 + ux2 * a2, v02 = e02 + uy2 * a2, v11 = e11 + uxy * a2;
+    const R v21 = e21 - R(2) * ux * e11 - uy * e20 + ux2 * uy * a3;
+    const R v12 = e12 - R(2) * uy * e11 - ux * e02 + ux * uy2 * a3;
+    const R v22 = e22 - R(2) * (ux * e12 + uy * e21) + ux2 * e02 + uy2 * e20
+                  + R(4) * uxy * e11 + ux2 * uy2 * a4;
+    // relaxed towards the transformed Maxwellian's central moments
+    const R c20 = v20 + om * (p * third + psi * ux2 - v20);
+    const R c02 = v02 + om * (p * third + psi * uy2 - v02);
+    const R c11 = v11 + om * (psi * uxy - v11);
+    const R c21 = v21 + om * (-psi * (third + ux2) * uy - v21);
+    const R c12 = v12 + om * (-psi * (third + uy2) * ux - v12);
+    const R c22 = v22 + om * (ninth * p + third * psi * (ux2 + uy2) + psi * ux2 * uy2 - v22);
+    // back to raw moments about 0 (lower central moments: p, -psi u)
+    const R b2 = p - R(2) * psi, b3 = p - R(3) * psi, b4 = p - R(4) * psi;
+    R r20 = c20 + ux2 * b2;
+    R r02 = c02 + uy2 * b2;
+    R r11 = c11 + uxy * b2;
+    R r21 = c21 + uy * c20 + R(2) * ux * c11 + ux2 * uy * b3;
+    R r12 = c12 + ux * c02 + R(2) * uy * c11 + ux * uy2 * b3;
+    R r22 = c22 + R(2) * (uy * c21 + ux * c12) + uy2 * c20 + ux2 * c02 + R(4) * uxy * c11
+            + ux2 * uy2 * b4;
+    // h-hat_0..2 and (1 - omega/2) sigma'
+    const R G00 = m.Fpx * ux + m.Fpy * uy;
+    const R Ftx = m.Ftx, Fty = m.Fty;
+    const R hs = R(1) - R(0.5) * om;
+    const R s20 = R(2) * third * (Ftx + m.Fpx) * ux + third * G00;
+    const R s02 = R(2) * third * (Fty + m.Fpy) * uy + third * G00;
+    const R s11 = third * ((Ftx + m.Fpx) * uy + (Fty + m.Fpy) * ux);
+    r20 += om * third * G00 + hs * s20;
+    r02 += om * third * G00 + hs * s02;
+    r11 += hs * s11;
+    r21 += om * ninth * Fty;
+    r12 += om * ninth * Ftx;
+    r22 += R(2) * ninth * om * G00;
+    const R r00 = pstar + G00;
+    const R r10 = rc2 * ux + R(0.5) * third * Ftx;
+    const R r01 = rc2 * uy + R(0.5) * third * Fty;
+    raw_to_pop_fast(r00, r10, r01, r20, r02, r11, r21, r12, r22, g);
+}
+
+// Interface-lattice operator of Sec. 5 with every rate equal to omega^phi (Sec. 7): all central
+// moments about u relax at omega^phi towards the equilibria (first order M_phi theta n,
+// c20 = c02 = c^2 phi, c22 = c^4 phi, the others 0), in raw-moment space.
+template <typename R>
+__device__ __forceinline__ void collide_ace_srt(R f[9], R phi, const Macro<R>& m, R omega_phi)
+{
+    const R third = R(1) / R(3), ninth = R(1) / R(9);
+    const R ux = m.ux, uy = m.uy, om = omega_phi;
+    const R ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const R s56 = f[5] + f[6], s78 = f[7] + f[8], d56 = f[5] - f[6], d78 = f[7] - f[8];
+    const R k10 = (f[1] - f[3]) + (d56 - d78);
+    const R k01 = (f[2] - f[4]) + (s56 - s78);
+    const R k20 = (f[1] + f[3]) + (s56 + s78);
+    const R k02 = (f[2] + f[4]) + (s56 + s78);
+    const R k11 = d56 + d78, k21 = s56 - s78, k12 = d56 - d78, k22 = s56 + s78;
+    // central moments about u
+    const R c10 = k10 - ux * phi, c01 = k01 - uy * phi;
+    const R c20 = k20 - R(2) * ux * k10 + ux2 * phi;
+    const R c02 = k02 - R(2) * uy * k01 + uy2 * phi;
+    const R c11 = k11 - ux * k01 - uy * k10 + uxy * phi;
+    const R c21 = k21 - R(2) * ux * k11 - uy * k20 + R(2) * uxy * k10 + ux2 * k01
+                  - ux2 * uy * phi;
+    const R c12 = k12 - R(2) * uy * k11 - ux * k02 + R(2) * uxy * k01 + uy2 * k10
+                  - ux * uy2 * phi;
+    const R c22 = k22 - R(2) * (ux * k12 + uy * k21) + ux2 * k02 + uy2 * k20 + R(4) * uxy * k11
+                  - R(2) * uxy * (uy * k10 + ux * k01) + ux2 * uy2 * phi;
+    // relaxation at one rate
+    const R a = c10 + om * (m.jx - c10);
+    const R b = c01 + om * (m.jy - c01);
+    const R keep = R(1) - om;
+    const R d20 = c20 + om * (third * phi - c20);
+    const R d02 = c02 + om * (third * phi - c02);
+    const R d11 = keep * c11, d21 = keep * c21, d12 = keep * c12;
+    const R d22 = c22 + om * (ninth * phi - c22);
+    // back to raw moments about 0
+    const R r10 = a + ux * phi;
+    const R r01 = b + uy * phi;
+    const R r20 = d20 + R(2) * ux * a + ux2 * phi;
+    const R r02 = d02 + R(2) * uy * b + uy2 * phi;
+    const R r11 = d11 + ux * b + uy * a + uxy * phi;
+    const R r21 = d21 + uy * d20 + R(2) * ux * d11 + R(2) * uxy * a + ux2 * b + ux2 * uy * phi;
+    const R r12 = d12 + ux * d02 + R(2) * uy * d11 + R(2) * uxy * b + uy2 * a + ux * uy2 * phi;
+    const R r22 = d22 + R(2) * (uy * d21 + ux * d12) + uy2 * d20 + ux2 * d02 + R(4) * uxy * d11
+                  + R(2) * uxy * (uy * a + ux * b) + ux2 * uy2 * phi;
+    raw_to_pop_fast(phi, r10, r01, r20, r02, r11, r21, r12, r22, f);
 }
 
 // Interface-lattice collision (Sec. 5), evaluated in raw-moment space: the cascaded operator

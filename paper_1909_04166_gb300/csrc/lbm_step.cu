@@ -35,7 +35,13 @@ struct StepLaunch {
     int seg_h;     // rows per segment
     int nseg;      // ceil(ny / seg_h)
     int* err;      // device error word (0 = ok)
+    int flow_sign; // imposed flow: +1, or -1 once reversed
 };
+
+// Step variants: bit 0 single relaxation time (Sec. 7) instead of the cascaded rates; bit 1 the
+// interface lattice alone in the imposed shear flow (Sec. 6.1); bit 2 the Langmuir isotherm
+// (Sec. 6.7) instead of the linear sigma(T).
+enum : int { kVarSRT = 1, kVarShear = 2, kVarLangmuir = 4 };
 
 template <typename S> struct Stages { static constexpr int value = 4; };
 template <> struct Stages<double> { static constexpr int value = 3; };
@@ -130,12 +136,12 @@ struct Row3 {
 };
 
 // Sum the lane's column of a staged tile and assemble its window row; hl/hr are this lane's
-// halo loads (one plane of the left / right halo column, or 0).
-template <typename R, typename S>
+// halo loads (one plane of the left / right halo column, or 0).  PHI_ONLY: p* is not formed.
+template <typename R, typename S, bool PHI_ONLY = false>
 __device__ __forceinline__ void window_row(const S* tile, int lane, int wlast, R hl, R hr,
                                            const Consts<R>& K, Row3<R>& row)
 {
-    const R ps = decode_sum<S, R>(tile + lane, 32, 0, K);
+    const R ps = PHI_ONLY ? R(0) : decode_sum<S, R>(tile + lane, 32, 0, K);
     const R ph = decode_sum<S, R>(tile + 9 * 32 + lane, 32, 1, K);
 #pragma unroll
     for (int off = 8; off >= 1; off >>= 1) {
@@ -166,25 +172,31 @@ __device__ __forceinline__ void make_window(const Row3<R>& s, const Row3<R>& c,
     ps.nw = n.psw; ps.n = n.psc; ps.ne = n.pse;
 }
 
-template <typename S, typename R>
+template <typename S, typename R, bool F_ONLY = false>
 __device__ __forceinline__ void ld_pops_t(const S* tile, int lane, const Consts<R>& K, R g[9],
                                           R f[9])
 {
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-        g[a] = decode<S, R>(tile[a * 32 + lane], 0, a, K);
+        if (!F_ONLY) g[a] = decode<S, R>(tile[a * 32 + lane], 0, a, K);
         f[a] = decode<S, R>(tile[(9 + a) * 32 + lane], 1, a, K);
     }
 }
 
 // The march of one warp over one strip x segment of one grid: everything the step does for
 // those nodes.  Used by the single-grid kernel and by the batched kernel.
-template <typename R, typename S>
+template <typename R, typename S, int V>
 __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__ dst,
                                       const Geometry& G, const Consts<R>& K, int strip, int seg,
-                                      int seg_h, int* err)
+                                      int seg_h, int* err, int flow_sign)
 {
     constexpr int NS = Stages<S>::value;
+    constexpr bool SRT = (V & kVarSRT) != 0;
+    constexpr bool SHEAR = (V & kVarShear) != 0;
+    constexpr bool LANGMUIR = (V & kVarLangmuir) != 0;
+    // the interface lattice alone copies only the f half of every tile (planes 9..17)
+    constexpr int COPY_OFF = SHEAR ? 9 * 32 : 0;
+    constexpr uint32_t COPY_BYTES = (SHEAR ? 9 * 32 : TILE) * sizeof(S);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -214,7 +226,7 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
 
     // halo: lanes 0..8 load g-bar plane q, lanes 16..24 f plane q, at columns xl and xr
     const int hq = lane & 15;
-    const bool hlane = hq < 9;
+    const bool hlane = hq < 9 && (!SHEAR || lane >= 16);
     const int hplane = (lane >> 4) * 9 + hq;
     const int hoffl = col_off(xl) + hplane * 32;
     const int hoffr = col_off(xr) + hplane * 32;
@@ -237,9 +249,9 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
         if (lane == 0) {
             fence_proxy_async();
             const uint32_t bar = bar0 + 8 * st;
-            mbar_expect_tx(bar, TILE * sizeof(S));
-            bulk_g2s(smem_u32(tiles + st * TILE), row_ptr(src, row_of(k)) + strip * TILE,
-                     TILE * sizeof(S), bar);
+            mbar_expect_tx(bar, COPY_BYTES);
+            bulk_g2s(smem_u32(tiles + st * TILE + COPY_OFF),
+                     row_ptr(src, row_of(k)) + strip * TILE + COPY_OFF, COPY_BYTES, bar);
         }
         issued = k;
     };
@@ -258,11 +270,11 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     R hl, hr, hl2, hr2;
     halo_load(-1, hl, hr);
     if (!wait_k(-1, 0)) { fail(-1); return; }
-    window_row<R, S>(tiles, lane, wlast, hl, hr, K, rb);
+    window_row<R, S, SHEAR>(tiles, lane, wlast, hl, hr, K, rb);
     issue(NS - 1, 0);
     halo_load(0, hl, hr);
     if (!wait_k(0, 1)) { fail(0); return; }
-    window_row<R, S>(tiles + TILE, lane, wlast, hl, hr, K, rc);
+    window_row<R, S, SHEAR>(tiles + TILE, lane, wlast, hl, hr, K, rc);
     halo_load(1, hl2, hr2);
 
     // neighbour columns of this lane (periodic wrap; walls handled by bounce flags)
@@ -274,12 +286,16 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     const bool xwall_warp = __any_sync(FULL, bxw || bxe);
     const R xf = R(x);
     bool ok = true;
+    // imposed flow: sin / cos of pi (x / L0 - 1/2) for this lane's column
+    R sxl = R(0), cxl = R(0);
+    if (SHEAR) sincospi_(xf * K.inv_nx - R(0.5), &sxl, &cxl);
+    const R fsign = R(flow_sign);
 
     // one row of the march; st = stage of row i
     auto body = [&](int i, int st) {
         const int st1 = st + 1 == NS ? 0 : st + 1;       // stage of row i + 1
         if (!wait_k(i + 1, st1)) { fail(i + 1); ok = false; return; }
-        window_row<R, S>(tiles + st1 * TILE, lane, wlast, hl2, hr2, K, rn);
+        window_row<R, S, SHEAR>(tiles + st1 * TILE, lane, wlast, hl2, hr2, K, rn);
         if (i + 2 <= nrows) halo_load(i + 2, hl2, hr2);
 
         const int y = up ? ys + i : ye - 1 - i;
@@ -287,13 +303,22 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
         if (up) make_window(rb, rc, rn, ph, ps);
         else make_window(rn, rc, rb, ph, ps);
         R g[9], f[9];
-        ld_pops_t<S, R>(tiles + st * TILE, lane, K, g, f);
-        const R jgx = (g[1] - g[3]) + (g[5] - g[6]) - (g[7] - g[8]);
-        const R jgy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+        ld_pops_t<S, R, SHEAR>(tiles + st * TILE, lane, K, g, f);
         Macro<R> m;
-        node_macro<R>(ph, ps, jgx, jgy, xf, R(y), K, m);
-        collide_fluid<R>(g, ps.c, m);
-        collide_ace<R>(f, ph.c, m, K.omega_phi);
+        if constexpr (SHEAR) {
+            R syr, cyr;
+            sincospi_(R(y) * K.inv_ny - R(0.5), &syr, &cyr);
+            imposed_velocity<R>(sxl, cxl, syr, cyr, fsign, K, m.ux, m.uy);
+            interface_flux<R>(ph, K, m.jx, m.jy);
+        } else {
+            const R jgx = (g[1] - g[3]) + (g[5] - g[6]) - (g[7] - g[8]);
+            const R jgy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+            node_macro<R, LANGMUIR>(ph, ps, jgx, jgy, xf, R(y), K, m);
+            if constexpr (SRT) collide_fluid_srt<R>(g, ps.c, m);
+            else collide_fluid<R>(g, ps.c, m);
+        }
+        if constexpr (SRT) collide_ace_srt<R>(f, ph.c, m, K.omega_phi);
+        else collide_ace<R>(f, ph.c, m, K.omega_phi);
 
         // push to x + e_a: rows y-1, y, y+1 and columns x-1, x, x+1 of the other buffer
         int ym = y - 1, yp = y + 1;
@@ -305,23 +330,42 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
         S* rN = const_cast<S*>(row_ptr(dst, yp));
         S* pc = rC + cc;
         S* p[9] = {pc, rC + ce, rN + cc, rC + cw, rS + cc, rN + ce, rN + cw, rS + cw, rS + ce};
-        const bool bnc[9] = {false, bxe, byn, bxw, bys, bxe || byn, bxw || byn, bxw || bys,
-                             bxe || bys};
-        constexpr int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
         if (!(bys || byn) && !xwall_warp) {      // warp-uniform: no wall crossed by this row
             if (active) {
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
-                    p[a][a * 32] = encode<S, R>(g[a], 0, a, K);
+                    if (!SHEAR) p[a][a * 32] = encode<S, R>(g[a], 0, a, K);
                     p[a][(9 + a) * 32] = encode<S, R>(f[a], 1, a, K);
                 }
             }
         } else if (active) {
+            // a population crossing a no-slip wall returns to this node reversed (half-way
+            // bounce-back); one crossing only free-slip walls has its normal components
+            // reversed and stays on this side of them (specular reflection)
+            constexpr int EXc[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+            constexpr int EYc[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+            constexpr int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+            constexpr int MX[9] = {0, 3, 2, 1, 4, 6, 5, 8, 7};    // e_x reversed
+            constexpr int MY[9] = {0, 1, 4, 3, 2, 8, 7, 6, 5};    // e_y reversed
 #pragma unroll
             for (int a = 0; a < 9; ++a) {
-                S* q = bnc[a] ? pc + (OPP[a] - a) * 32 : p[a];
-                q[a * 32] = encode<S, R>(g[a], 0, a, K);
-                q[(9 + a) * 32] = encode<S, R>(f[a], 1, a, K);
+                const int ex = EXc[a], ey = EYc[a];
+                const bool cx = (ex < 0 && bxw) || (ex > 0 && bxe);
+                const bool cy = (ey < 0 && bys) || (ey > 0 && byn);
+                const bool sx = ((G.slip >> (ex < 0 ? 0 : 1)) & 1) != 0;
+                const bool sy = ((G.slip >> (ey < 0 ? 2 : 3)) & 1) != 0;
+                int plane = a;
+                S* q = p[a];
+                if ((cx && !sx) || (cy && !sy)) {
+                    plane = OPP[a];
+                    q = pc;
+                } else if (cx || cy) {
+                    plane = cx ? (cy ? OPP[a] : MX[a]) : MY[a];
+                    S* row = cy ? rC : (ey > 0 ? rN : (ey < 0 ? rS : rC));
+                    q = row + (cx ? cc : (ex > 0 ? ce : (ex < 0 ? cw : cc)));
+                }
+                if (!SHEAR) q[plane * 32] = encode<S, R>(g[a], 0, a, K);
+                q[(9 + plane) * 32] = encode<S, R>(f[a], 1, a, K);
             }
         }
         issue(i + NS, st);      // the tile of row i is consumed: refill its stage
@@ -337,7 +381,7 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     }
 }
 
-template <typename R, typename S>
+template <typename R, typename S, int V>
 __global__ void __launch_bounds__(256)
 step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R> K,
             StepLaunch L)
@@ -346,7 +390,7 @@ step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R
     const int strip = warp % G.nstrips;
     const int seg = warp / G.nstrips;
     if (seg >= L.nseg) return;                       // warp-uniform
-    march<R, S>(src, dst, G, K, strip, seg, L.seg_h, L.err);
+    march<R, S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign);
 }
 
 // One time step of many independent grids in one launch: warp w takes task w = (case, local
@@ -366,7 +410,7 @@ batch_step_kernel(S* __restrict__ base, const BatchCase<R>* __restrict__ cases,
     const int seg = t.y / G.nstrips;
     const S* src = base + (parity ? c.off1 : c.off0);
     S* dst = base + (parity ? c.off0 : c.off1);
-    march<R, S>(src, dst, G, c.K, strip, seg, c.seg_h, err);
+    march<R, S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -400,7 +444,7 @@ __global__ void init_kernel(const double* __restrict__ phi, const double* __rest
 // thread per node; the 3x3 neighbourhood sums are recomputed per node (diagnostic path).
 template <typename R, typename S>
 __global__ void fields_kernel(const S* __restrict__ state, Geometry G, Consts<R> K,
-                              double* __restrict__ phi_o, double* __restrict__ p_o,
+                              int flow_sign, double* __restrict__ phi_o, double* __restrict__ p_o,
                               double* __restrict__ ux_o, double* __restrict__ uy_o,
                               double* __restrict__ rho_o)
 {
@@ -432,7 +476,15 @@ __global__ void fields_kernel(const S* __restrict__ state, Geometry G, Consts<R>
     const R jgx = (gq[1] - gq[3]) + (gq[5] - gq[6]) - (gq[7] - gq[8]);
     const R jgy = (gq[2] - gq[4]) + (gq[5] + gq[6]) - (gq[7] + gq[8]);
     Macro<R> m;
-    node_macro<R>(ph, ps, jgx, jgy, R(x), R(y), K, m);
+    if (K.langmuir) node_macro<R, true>(ph, ps, jgx, jgy, R(x), R(y), K, m);
+    else node_macro<R, false>(ph, ps, jgx, jgy, R(x), R(y), K, m);
+    if (flow_sign) {   // imposed flow: u from the field, no pressure
+        R sx, cx, sy, cy;
+        sincospi_(R(x) * K.inv_nx - R(0.5), &sx, &cx);
+        sincospi_(R(y) * K.inv_ny - R(0.5), &sy, &cy);
+        imposed_velocity<R>(sx, cx, sy, cy, R(flow_sign), K, m.ux, m.uy);
+        m.p = R(0);
+    }
     if (phi_o) phi_o[n] = double(ph.c);
     if (p_o) p_o[n] = double(m.p);
     if (ux_o) ux_o[n] = double(m.ux);
@@ -474,54 +526,58 @@ template <typename S>
 size_t step_smem_bytes(int block) { return (size_t)(block / 32) * warp_smem_bytes<S>(); }
 
 // Allow the dynamic shared memory of a block of `block` threads (call once per device).
-template <typename R, typename S>
+template <typename R, typename S, int V>
 cudaError_t configure_step(int block)
 {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<R, S>,
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<R, S, V>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)step_smem_bytes<S>(block));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(step_kernel<R, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    return cudaFuncSetAttribute(step_kernel<R, S, V>,
+                                cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
 }
 
 // Resident blocks of `block` threads per SM for the step kernel.
-template <typename R, typename S>
+template <typename R, typename S, int V>
 int step_blocks_per_sm(int block)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<R, S>, block,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<R, S, V>, block,
                                                       step_smem_bytes<S>(block)) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
 
-template <typename R, typename S>
+template <typename R, typename S, int V>
 cudaError_t launch_step(const void* src, void* dst, const Geometry& G, const Consts<R>& K,
-                        int seg_h, int block, int* err, cudaStream_t st)
+                        int seg_h, int block, int* err, int flow_sign, cudaStream_t st)
 {
     StepLaunch L;
     L.seg_h = seg_h;
     L.nseg = (G.ny + seg_h - 1) / seg_h;
     L.err = err;
+    L.flow_sign = flow_sign;
     const long long warps = (long long)G.nstrips * L.nseg;
     const int wpb = block / 32;
     const long long grid = (warps + wpb - 1) / wpb;
-    step_kernel<R, S><<<(unsigned)grid, block, step_smem_bytes<S>(block), st>>>(
+    step_kernel<R, S, V><<<(unsigned)grid, block, step_smem_bytes<S>(block), st>>>(
         static_cast<const S*>(src), static_cast<S*>(dst), G, K, L);
     return cudaGetLastError();
 }
 
 // A graph of `chunk` (even) consecutive steps starting from buffer `a` (a -> b -> a -> ...),
 // replayed by lbm_step to cut the per-launch gaps between steps.
-template <typename R, typename S>
+template <typename R, typename S, int V>
 cudaError_t build_step_graph(const void* a, const void* b, const Geometry& G, const Consts<R>& K,
-                             int seg_h, int block, int* err, int chunk, cudaGraphExec_t* out)
+                             int seg_h, int block, int* err, int flow_sign, int chunk,
+                             cudaGraphExec_t* out)
 {
     StepLaunch L;
     L.seg_h = seg_h;
     L.nseg = (G.ny + seg_h - 1) / seg_h;
     L.err = err;
+    L.flow_sign = flow_sign;
     const long long warps = (long long)G.nstrips * L.nseg;
     const int wpb = block / 32;
     const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
@@ -536,7 +592,7 @@ cudaError_t build_step_graph(const void* a, const void* b, const Geometry& G, co
         S* dst = const_cast<S*>(static_cast<const S*>((s & 1) ? a : b));
         void* args[] = {(void*)&src, (void*)&dst, (void*)&g, (void*)&k, (void*)&L};
         cudaKernelNodeParams p = {};
-        p.func = (void*)step_kernel<R, S>;
+        p.func = (void*)step_kernel<R, S, V>;
         p.gridDim = dim3(grid);
         p.blockDim = dim3(block);
         p.sharedMemBytes = (unsigned)step_smem_bytes<S>(block);
@@ -618,12 +674,12 @@ cudaError_t launch_init(const double* phi, const double* p, const double* ux, co
 
 template <typename R, typename S>
 cudaError_t launch_fields(const void* state, const Geometry& G, const Consts<R>& K,
-                          double* phi, double* p, double* ux, double* uy, double* rho,
-                          cudaStream_t st)
+                          int flow_sign, double* phi, double* p, double* ux, double* uy,
+                          double* rho, cudaStream_t st)
 {
     const long long N = (long long)G.nx * G.ny;
     fields_kernel<R, S><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(
-        static_cast<const S*>(state), G, K, phi, p, ux, uy, rho);
+        static_cast<const S*>(state), G, K, flow_sign, phi, p, ux, uy, rho);
     return cudaGetLastError();
 }
 
@@ -647,25 +703,28 @@ cudaError_t launch_unpack(const double* in, void* state, const Geometry& G, cons
     return cudaGetLastError();
 }
 
+#define CMLBM_INSTANTIATE_STEP(R, S, V)                                                           \
+    template cudaError_t configure_step<R, S, V>(int);                                          \
+    template int step_blocks_per_sm<R, S, V>(int);                                              \
+    template cudaError_t build_step_graph<R, S, V>(const void*, const void*, const Geometry&,   \
+                                                   const Consts<R>&, int, int, int*, int, int,  \
+                                                   cudaGraphExec_t*);                           \
+    template cudaError_t launch_step<R, S, V>(const void*, void*, const Geometry&,              \
+                                              const Consts<R>&, int, int, int*, int,            \
+                                              cudaStream_t);
+
 #define CMLBM_INSTANTIATE(R, S)                                                                   \
     template size_t step_smem_bytes<S>(int);                                                    \
-    template cudaError_t configure_step<R, S>(int);                                             \
-    template int step_blocks_per_sm<R, S>(int);                                                 \
     template cudaError_t configure_batch<R, S>(int);                                            \
     template cudaError_t build_batch_graph<R, S>(void*, const BatchCase<R>*, const int2*, int,  \
                                                  int, int, int*, int, cudaGraphExec_t*);        \
     template cudaError_t launch_batch_step<R, S>(void*, const BatchCase<R>*, const int2*, int,  \
                                                  int, int, int*, cudaStream_t);                 \
-    template cudaError_t build_step_graph<R, S>(const void*, const void*, const Geometry&,      \
-                                                const Consts<R>&, int, int, int*, int,          \
-                                                cudaGraphExec_t*);                              \
-    template cudaError_t launch_step<R, S>(const void*, void*, const Geometry&,                 \
-                                           const Consts<R>&, int, int, int*, cudaStream_t);     \
     template cudaError_t launch_init<R, S>(const double*, const double*, const double*,         \
                                            const double*, void*, const Geometry&,               \
                                            const Consts<R>&, cudaStream_t);                     \
     template cudaError_t launch_fields<R, S>(const void*, const Geometry&, const Consts<R>&,    \
-                                             double*, double*, double*, double*, double*,       \
+                                             int, double*, double*, double*, double*, double*,  \
                                              cudaStream_t);
 
 // Populations are copied in and out in double; the codec of the 16-bit formats is applied in
@@ -680,11 +739,27 @@ CMLBM_INSTANTIATE(double, double)
 CMLBM_INSTANTIATE(float, float)
 CMLBM_INSTANTIATE(float, __half)
 CMLBM_INSTANTIATE(float, __nv_bfloat16)
+// every variant in FP64 and FP32; the 16-bit storage modes take the cascaded coupled step only
+CMLBM_INSTANTIATE_STEP(double, double, 0)
+CMLBM_INSTANTIATE_STEP(double, double, 1)
+CMLBM_INSTANTIATE_STEP(double, double, 2)
+CMLBM_INSTANTIATE_STEP(double, double, 3)
+CMLBM_INSTANTIATE_STEP(double, double, 4)
+CMLBM_INSTANTIATE_STEP(double, double, 5)
+CMLBM_INSTANTIATE_STEP(float, float, 0)
+CMLBM_INSTANTIATE_STEP(float, float, 1)
+CMLBM_INSTANTIATE_STEP(float, float, 2)
+CMLBM_INSTANTIATE_STEP(float, float, 3)
+CMLBM_INSTANTIATE_STEP(float, float, 4)
+CMLBM_INSTANTIATE_STEP(float, float, 5)
+CMLBM_INSTANTIATE_STEP(float, __half, 0)
+CMLBM_INSTANTIATE_STEP(float, __nv_bfloat16, 0)
 CMLBM_INSTANTIATE_PACK(double)
 CMLBM_INSTANTIATE_PACK(float)
 CMLBM_INSTANTIATE_PACK(__half)
 CMLBM_INSTANTIATE_PACK(__nv_bfloat16)
 #undef CMLBM_INSTANTIATE
+#undef CMLBM_INSTANTIATE_STEP
 #undef CMLBM_INSTANTIATE_PACK
 
 }  // namespace cmlbm

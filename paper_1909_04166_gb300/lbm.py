@@ -33,6 +33,13 @@ PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP32_FP16, "bf16":
 
 LBM_PERIODIC = 0
 LBM_WALL = 1
+LBM_FREESLIP = 2
+LBM_CASCADED = 0
+LBM_SRT = 1
+LBM_SIGMA_LINEAR_T = 0
+LBM_SIGMA_LANGMUIR = 1
+LBM_FLOW_COUPLED = 0
+LBM_FLOW_SHEAR = 1
 
 EXPORTS = [
     "lbm_state_bytes", "lbm_create", "lbm_create_with_buffer", "lbm_init_fields",
@@ -66,6 +73,12 @@ class lbm_params(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("store_scale_g", ctypes.c_double), ("store_scale_f", ctypes.c_double),
         ("store_ref_g", ctypes.c_double),
+        ("bc_x_hi", ctypes.c_int32), ("bc_y_hi", ctypes.c_int32),
+        ("collision", ctypes.c_int32), ("sigma_model", ctypes.c_int32),
+        ("beta", ctypes.c_double), ("psi0", ctypes.c_double),
+        ("gradpsi_x", ctypes.c_double), ("gradpsi_y", ctypes.c_double),
+        ("flow", ctypes.c_int32), ("reverse_step", ctypes.c_int32),
+        ("u0", ctypes.c_double),
     ]
 
 
@@ -151,12 +164,14 @@ def _dptr(a):
 
 
 def make_params(case: dict, precision="fp32", device=0, stream=0) -> lbm_params:
-    """lbm_params from a case dictionary (keys of ``workloads.Case``)."""
+    """lbm_params from a case dictionary (keys of ``workloads.Case``; boundary kinds 0 / False
+    periodic, 1 / True no-slip, 2 free-slip; wall_x_hi / wall_y_hi for a differing right / top
+    side)."""
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    hi_x, hi_y = case.get("wall_x_hi"), case.get("wall_y_hi")
     return lbm_params(
         int(case["nx"]), int(case["ny"]),
-        LBM_WALL if case.get("wall_x") else LBM_PERIODIC,
-        LBM_WALL if case.get("wall_y") else LBM_PERIODIC,
+        int(case.get("wall_x", 0)), int(case.get("wall_y", 0)),
         float(case["rho_a"]), float(case["rho_b"]), float(case["mu_a"]), float(case["mu_b"]),
         float(case.get("sigma0", 0.0)), float(case.get("dsigma_dT", 0.0)),
         float(case.get("T0", 0.0)), float(case.get("gradT_x", 0.0)),
@@ -164,7 +179,12 @@ def make_params(case: dict, precision="fp32", device=0, stream=0) -> lbm_params:
         float(case.get("gx", 0.0)), float(case.get("gy", 0.0)), float(case.get("rho_ref", 0.0)),
         prec, int(device), ctypes.c_void_p(int(stream)),
         float(case.get("store_scale_g", 0.0)), float(case.get("store_scale_f", 0.0)),
-        float(case.get("store_ref_g", 0.0)))
+        float(case.get("store_ref_g", 0.0)),
+        0 if hi_x is None else int(hi_x), 0 if hi_y is None else int(hi_y),
+        int(case.get("collision", 0)), int(case.get("sigma_model", 0)),
+        float(case.get("beta", 0.0)), float(case.get("psi0", 0.0)),
+        float(case.get("gradpsi_x", 0.0)), float(case.get("gradpsi_y", 0.0)),
+        int(case.get("flow", 0)), int(case.get("reverse_step", 0)), float(case.get("u0", 0.0)))
 
 
 # ---- ABI wrappers (same names as the C entry points) ------------------------------------------

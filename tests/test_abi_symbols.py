@@ -58,3 +58,73 @@ def test_create_reports_cuda_error_without_a_device():
         lbm.lbm_create(lbm.make_params(W.laplace(n=16), "fp32"))
     assert e.value.status == lbm.LBM_ERR_CUDA
     lbm.lbm_destroy(None)
+
+
+def test_binding_struct_matches_header_layout(tmp_path):
+    """sizeof and every field offset of lbm_params / lbm_diag as the C compiler lays them out
+    from include/cmlbm.h equal the ctypes structures of the binding."""
+    structs = {"lbm_params": lbm.lbm_params, "lbm_diag": lbm.lbm_diag}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"',
+             "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in filter(None, out):
+        name, field, value = line.split()
+        cls = structs[name]
+        expect = ctypes.sizeof(cls) if field == "sizeof" else getattr(cls, field).offset
+        assert int(value) == expect, (name, field)
+        seen += 1
+    assert seen == sum(len(c._fields_) + 1 for c in structs.values())
+
+
+def test_new_forms_are_validated_without_a_device():
+    """Boundary pairs, collision / sigma / flow enums, the Langmuir domain psi < 1 and the
+    16-bit storage limits are checked before any device work (lbm_state_bytes validates)."""
+    from paper_1909_04166_gb300 import workloads as W
+
+    def status(precision="fp32", **kw):
+        case = W.random_drop(40, 30, seed=0)
+        case.update(kw)
+        try:
+            lbm.lbm_state_bytes(lbm.make_params(case, precision))
+            return lbm.LBM_OK
+        except lbm.LbmError as e:
+            return e.status
+
+    assert status(wall_y=1, wall_y_hi=2) == lbm.LBM_OK
+    assert status(wall_x=2) == lbm.LBM_OK
+    assert status(wall_y=0, wall_y_hi=2) == lbm.LBM_ERR_ARG      # periodic must pair
+    assert status(wall_x=3) == lbm.LBM_ERR_ARG
+    assert status(collision=1) == lbm.LBM_OK
+    assert status(collision=2) == lbm.LBM_ERR_ARG
+    assert status(sigma_model=1, beta=0.5, psi0=0.2, gradpsi_x=0.01) == lbm.LBM_OK
+    # psi reaches 0.2 + 0.03 * 39 > 1 at the right edge: ln(1 - psi) undefined
+    assert status(sigma_model=1, beta=0.5, psi0=0.2, gradpsi_x=0.03) == lbm.LBM_ERR_PARAM
+    assert status(flow=1, u0=0.02, reverse_step=100) == lbm.LBM_OK
+    assert status(flow=5) == lbm.LBM_ERR_ARG
+    assert status("fp16", collision=1) == lbm.LBM_ERR_UNSUPPORTED
+    assert status("bf16", flow=1, u0=0.01) == lbm.LBM_ERR_UNSUPPORTED
+    assert status("fp16", wall_y=2) == lbm.LBM_OK
+
+
+def test_batch_rejects_other_step_forms_without_a_device():
+    """A batch takes the cascaded coupled step with the linear sigma(T) only; the check comes
+    before any device work."""
+    from paper_1909_04166_gb300 import workloads as W
+    base = lbm.make_params(W.random_drop(40, 30, seed=1), "fp32")
+    for bad in (dict(collision=1), dict(flow=1, u0=0.01), dict(sigma_model=1, beta=0.5)):
+        c = W.random_drop(40, 30, seed=2)
+        c.update(bad)
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_batch_create([base, lbm.make_params(c, "fp32")])
+        assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
