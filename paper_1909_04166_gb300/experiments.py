@@ -1,0 +1,141 @@
+"""The paper's experiments for the step's further forms, run on the GPU through the C ABI.
+
+* ``e1``  circular interface in the imposed reversing shear flow (Sec. 6.1): shape error when it
+  returns at 2 T_f, and the phase-mass drift.
+* ``e7``  Young's problem recast for a surfactant (Sec. 6.7): migration velocity of a neutrally
+  buoyant drop in the imposed psi = psi0 + G y with the Langmuir isotherm, against the creeping-
+  flow terminal velocity V = -sigma_Gamma G D / (6 mu_B + 9 mu_A), sigma_Gamma = -sigma0 beta,
+  for the paper's three sensitivities sigma0 beta.
+* ``e8``  numerical stability of the two collision models (Sec. 7): the smallest kinematic
+  viscosity nu_A = nu_B at which the oscillating elliptic cylinder (kappa-tilde = 0.01) still runs
+  stably, for the cascaded and the single-relaxation-time operators at density ratios 500, 600,
+  800 and 900, on a grid of quarter decades in nu.
+
+``python -m paper_1909_04166_gb300.experiments [e1|e7|e8|all]`` prints one JSON line each.
+"""
+from __future__ import annotations
+
+import json
+import math
+import sys
+import time
+
+import numpy as np
+
+from . import lbm
+from . import workloads as W
+
+
+def _area_mismatch(a, b):
+    return float(np.sum((a > 0.5) != (b > 0.5)) / np.sum(b > 0.5))
+
+
+def e1(L0=200, u0=0.02, precision="fp32") -> dict:
+    case = W.shear_circle(L0=L0, u0=u0)
+    tf = case["meta"]["t_f"]
+    phi0 = case["fields"]["phi"]
+    t0 = time.perf_counter()
+    with lbm.Simulation(case, precision=precision) as sim:
+        sim.init_case()
+        m0 = sim.diagnostics()["sum_phi"]
+        sim.step(tf)
+        mid = sim.fields()["phi"]
+        sim.step(tf)
+        end = sim.fields()["phi"]
+        m1 = sim.diagnostics()["sum_phi"]
+    return {"experiment": "e1 reversing shear (Sec. 6.1)", "L0": L0, "u0": u0, "T_f": tf,
+            "precision": precision, "area_mismatch_at_Tf": round(_area_mismatch(mid, phi0), 4),
+            "area_mismatch_at_2Tf": round(_area_mismatch(end, phi0), 5),
+            "rel_l2_phi_at_2Tf": round(float(np.linalg.norm(end - phi0) /
+                                             np.linalg.norm(phi0)), 5),
+            "phase_mass_drift": float(abs(m1 - m0) / m0),
+            "wall_s": round(time.perf_counter() - t0, 2)}
+
+
+def e7(sens=(0.0048, 0.0146, 0.0244), steps=100000, sample=1000, precision="fp32") -> dict:
+    out = {"experiment": "e7 Young's problem, Langmuir isotherm (Sec. 6.7)", "steps": steps,
+           "precision": precision, "cases": []}
+    for sb in sens:
+        case = W.young_drop(sigma0_beta=sb)
+        meta = case["meta"]
+        mu_a, mu_b = case["mu_a"], case["mu_b"]
+        v_theory = -meta["sigma_gamma"] * meta["grad_psi"] * meta["diameter"] / (6 * mu_b
+                                                                                 + 9 * mu_a)
+        vs, ys = [], []
+        with lbm.Simulation(case, precision=precision) as sim:
+            sim.init_case()
+            for k in range(steps // sample):
+                sim.step(sample)
+                fl = sim.fields()
+                ph = np.clip(fl["phi"], 0.0, 1.0)
+                vs.append(float((ph * fl["uy"]).sum() / ph.sum()))
+                y = np.arange(case["ny"], dtype=float)[:, None]
+                ys.append(float((ph * y).sum() / ph.sum()))
+        tail = vs[len(vs) // 2:]
+        out["cases"].append({
+            "sigma0_beta": sb, "v_theory": v_theory,
+            "v_mean_second_half": float(np.mean(tail)),
+            "ratio": float(np.mean(tail) / v_theory),
+            "centroid_start_end": [round(ys[0], 3), round(ys[-1], 3)],
+            "v_centroid_second_half": float((ys[-1] - ys[len(ys) // 2]) /
+                                            (sample * (len(ys) - 1 - len(ys) // 2))),
+        })
+    return out
+
+
+def _stable(case, precision, steps, check, umax):
+    """Run `steps` steps; unstable at the first checkpoint with a non-finite node or a speed
+    above umax (the flow has left the low-Mach range the scheme is built for)."""
+    with lbm.Simulation(case, precision=precision) as sim:
+        sim.init_case()
+        done, peak = 0, 0.0
+        while done < steps:
+            n = min(check, steps - done)
+            sim.step(n)
+            done += n
+            d = sim.diagnostics()
+            if d["nonfinite"] or not math.isfinite(d["max_speed"]) or d["max_speed"] > umax:
+                return False, done, peak
+            peak = max(peak, d["max_speed"])
+    return True, done, peak
+
+
+def e8(ratios=(500.0, 600.0, 800.0, 900.0), steps=50000, check=2000, umax=0.1, nu_max=0.1,
+       nu_min=1e-8, per_decade=4, precision="fp32") -> dict:
+    """A run counts as stable when every checkpoint (each `check` steps, `steps` in all: about
+    eight capillary oscillation periods) has finite fields and a largest speed <= umax."""
+    nus = [nu_max * 10 ** (-k / per_decade)
+           for k in range(int(round(per_decade * math.log10(nu_max / nu_min))) + 1)]
+    out = {"experiment": "e8 minimum stable viscosity, oscillating cylinder (Sec. 7)",
+           "steps": steps, "check_every": check, "max_speed_bound": umax, "kappa_tilde": 0.01,
+           "precision": precision, "nu_grid": [float(f"{v:.4g}") for v in nus], "rows": []}
+    t0 = time.perf_counter()
+    for ratio in ratios:
+        row = {"density_ratio": ratio}
+        for model, col in (("cascaded", 0), ("srt", 1)):
+            smallest, failed_at = None, None
+            for nu in nus:            # decreasing; stop at the first unstable viscosity
+                case = W.oscillating_cylinder(rho_ratio=ratio, nu=nu, collision=col)
+                ok, done, peak = _stable(case, precision, steps, check, umax)
+                if not ok:
+                    failed_at = {"nu": float(f"{nu:.4g}"), "step": done}
+                    break
+                smallest = nu
+            row[f"nu_min_{model}"] = None if smallest is None else float(f"{smallest:.4g}")
+            row[f"first_unstable_{model}"] = failed_at
+        if row["nu_min_cascaded"] and row["nu_min_srt"]:
+            row["srt_over_cascaded"] = row["nu_min_srt"] / row["nu_min_cascaded"]
+        out["rows"].append(row)
+    out["wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
+
+
+def main(argv=None):
+    which = (argv or sys.argv[1:] or ["all"])[0]
+    for name, fn in (("e1", e1), ("e7", e7), ("e8", e8)):
+        if which in (name, "all"):
+            print(json.dumps(fn()), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -273,11 +273,13 @@ def rising_bubble(nx=161, ny=481, diameter=64.0, centre=(80.0, 120.0), rho_ratio
 
 
 def young_drop(nx=51, ny=201, diameter=30.0, yc=45.0, nu=0.05, grad_psi=9.95e-5,
-               sigma0_beta=0.0244, beta=0.5, psi0=0.0, width=4.0, mobility=0.02) -> Case:
+               sigma0_beta=0.0244, beta=5.0, psi0=0.0, width=4.0, mobility=0.02) -> Case:
     """Sec. 6.7, Young's problem recast for a surfactant: a neutrally buoyant drop (density and
     viscosity ratio 1) near the bottom of a channel (periodic x, no-slip y) in the imposed
     psi = psi0 + G y with the Langmuir isotherm sigma = sigma0 [1 + beta ln(1 - psi)].  The
-    paper gives sigma0 beta and G; beta (hence sigma0) and psi0 are not given."""
+    paper gives sigma0 beta and G; beta (hence sigma0) and psi0 are not given.  beta = 5 keeps
+    sigma0 small (1e-3 .. 5e-3): with beta = 1/2 (sigma0 up to 0.05) the capillary part's
+    discretisation noise swamps the slow migration."""
     sigma0 = sigma0_beta / beta
     c = _base(nx, ny, wall_y=1, rho_a=1.0, rho_b=1.0, mu_a=nu, mu_b=nu, sigma0=sigma0,
               mobility=mobility, width=width, sigma_model=1, beta=beta, psi0=psi0,
