@@ -64,11 +64,15 @@ void* cur_state(lbm_ctx* c) { return c->buf + (size_t)c->cur * c->state_bytes; }
 // about once (one wave): warps = strips * ceil(ny / rows).
 int default_seg_rows(const lbm_ctx* c)
 {
+    int strips_per_row = 1;
     const int bps = with_variant(c->P.precision, c->variant, [&](auto r, auto s, auto v) {
-        return step_blocks_per_sm<decltype(r), decltype(s), decltype(v)::value>(c->block);
+        using R = decltype(r);
+        using S = decltype(s);
+        strips_per_row = step_warp_strips<R, S, decltype(v)::value>(c->G.nstrips);
+        return step_blocks_per_sm<R, S, decltype(v)::value>(c->block);
     });
     const long long resident = (long long)c->nsm * bps * (c->block / 32);
-    const long long strips = c->G.nstrips;
+    const long long strips = strips_per_row;
     long long nseg = resident / strips;
     if (nseg < 1) nseg = 1;
     long long h = (c->G.ny + nseg - 1) / nseg;

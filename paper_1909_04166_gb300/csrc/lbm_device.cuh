@@ -125,43 +125,39 @@ struct BatchCase {
 };
 
 // ---------------------------------------------------------------------------------------------
-// Nine-point stencil window of a nodal field: value at (x + i, y + j), i, j in {-1, 0, 1}.
+// Arithmetic types of the per-node update: float or double for one node, or F2 for two nodes at
+// once (the two columns a lane owns in the paired FP32 step) on the packed FP32x2 instructions
+// of sm_100+ (__ffma2_rn, __fadd2_rn, __fmul2_rn).  The formulas below are written once for all
+// three; fmad(a, b, c) = a b + c marks the products that fuse (the packed instructions are not
+// contracted by the compiler).  Transcendentals and reciprocals act on each half.
 // ---------------------------------------------------------------------------------------------
-template <typename R>
-struct Win {
-    R sw, s, se, w, c, e, nw, n, ne;
+struct F2 {
+    float2 v;
+    F2() = default;
+    __device__ __forceinline__ F2(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ explicit F2(float2 p) : v(p) {}
 };
-
-// Second-order isotropic differences on the D2Q9 neighbourhood (Sec. 4, closing remark):
-// grad a = 3 sum_a w_a e_a a(x + e_a) and lap a = 6 sum_a w_a (a(x + e_a) - a(x)), with
-// w = 1/9 (axis) and 1/36 (diagonal).  The Hessian is the 1-10-1 weighted second difference
-// across the three rows (columns) of the window; its trace equals the Laplacian.
-template <typename R>
-__device__ __forceinline__ void grad_iso(const Win<R>& a, R& gx, R& gy)
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+// a - b as one fused a + (-1) b
+__device__ __forceinline__ F2 operator-(F2 a, F2 b)
 {
-    const R third = R(1) / R(3), twelfth = R(1) / R(12);
-    gx = (a.e - a.w) * third + ((a.ne + a.se) - (a.nw + a.sw)) * twelfth;
-    gy = (a.n - a.s) * third + ((a.ne + a.nw) - (a.se + a.sw)) * twelfth;
+    return F2(__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v));
 }
+__device__ __forceinline__ F2& operator+=(F2& a, F2 b) { return a = a + b; }
 
-template <typename R>
-__device__ __forceinline__ void lap_hess(const Win<R>& a, R& lap, R& hxx, R& hyy, R& hxy)
-{
-    const R sixth = R(1) / R(6), twelfth = R(1) / R(12);
-    const R axis = (a.e + a.w) + (a.n + a.s);
-    const R diag = (a.ne + a.nw) + (a.se + a.sw);
-    lap = (R(4) * axis + diag - R(20) * a.c) * sixth;
-    const R dxx_mid = a.e - R(2) * a.c + a.w;
-    const R dyy_mid = a.n - R(2) * a.c + a.s;
-    const R dxx_side = (a.ne - R(2) * a.n + a.nw) + (a.se - R(2) * a.s + a.sw);
-    const R dyy_side = (a.ne - R(2) * a.e + a.se) + (a.nw - R(2) * a.w + a.sw);
-    hxx = (R(10) * dxx_mid + dxx_side) * twelfth;
-    hyy = (R(10) * dyy_mid + dyy_side) * twelfth;
-    hxy = ((a.ne - a.nw) - (a.se - a.sw)) * R(0.25);
-}
+__device__ __forceinline__ float fmad(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmad(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ F2 fmad(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+
+template <typename T> struct ScalarOf { using type = T; };
+template <> struct ScalarOf<F2> { using type = float; };
+template <typename T> using scalar_t = typename ScalarOf<T>::type;
 
 template <typename R> __device__ __forceinline__ R log_(R v) { return log(v); }
 template <> __device__ __forceinline__ float log_<float>(float v) { return logf(v); }
+__device__ __forceinline__ F2 log_(F2 v) { return F2(logf(v.v.x), logf(v.v.y)); }
 template <typename R> __device__ __forceinline__ void sincospi_(R v, R* s, R* c)
 {
     sincospi(v, s, c);
@@ -172,90 +168,145 @@ template <> __device__ __forceinline__ void sincospi_<float>(float v, float* s, 
 }
 template <typename R> __device__ __forceinline__ R rcp_(R v) { return R(1) / v; }
 template <> __device__ __forceinline__ float rcp_<float>(float v) { return __fdividef(1.0f, v); }
-template <typename R> __device__ __forceinline__ R rsqrt_(R v) { return R(1) / sqrt(v); }
-template <> __device__ __forceinline__ float rsqrt_<float>(float v) { return rsqrtf(v); }
+__device__ __forceinline__ F2 rcp_(F2 v)
+{
+    return F2(__fdividef(1.0f, v.v.x), __fdividef(1.0f, v.v.y));
+}
 // sqrt(v) for v >= 0: exact in double; v * rsqrt(v) in float (0 for v = 0)
 template <typename R> __device__ __forceinline__ R norm_(R v) { return sqrt(v); }
 template <> __device__ __forceinline__ float norm_<float>(float v)
 {
     return v * rsqrtf(fmaxf(v, 1e-37f));
 }
+__device__ __forceinline__ F2 norm_(F2 v)
+{
+    return v * F2(rsqrtf(fmaxf(v.v.x, 1e-37f)), rsqrtf(fmaxf(v.v.y, 1e-37f)));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Nine-point stencil window of a nodal field: value at (x + i, y + j), i, j in {-1, 0, 1}.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct Win {
+    T sw, s, se, w, c, e, nw, n, ne;
+};
+
+// Second-order isotropic differences on the D2Q9 neighbourhood (Sec. 4, closing remark):
+// grad a = 3 sum_a w_a e_a a(x + e_a) and lap a = 6 sum_a w_a (a(x + e_a) - a(x)), with
+// w = 1/9 (axis) and 1/36 (diagonal).  The Hessian is the 1-10-1 weighted second difference
+// across the three rows (columns) of the window; its trace equals the Laplacian.
+template <typename T>
+__device__ __forceinline__ void grad_iso(const Win<T>& a, T& gx, T& gy)
+{
+    using R = scalar_t<T>;
+    const T third = T(R(1) / R(3)), twelfth = T(R(1) / R(12));
+    gx = fmad(a.e - a.w, third, ((a.ne + a.se) - (a.nw + a.sw)) * twelfth);
+    gy = fmad(a.n - a.s, third, ((a.ne + a.nw) - (a.se + a.sw)) * twelfth);
+}
+
+// Gradient, Laplacian and Hessian of one window, sharing the partial sums of its corners.
+template <typename T>
+__device__ __forceinline__ void stencils(const Win<T>& a, T& gx, T& gy, T& lap, T& hxx, T& hyy,
+                                         T& hxy)
+{
+    using R = scalar_t<T>;
+    const T third = T(R(1) / R(3)), sixth = T(R(1) / R(6)), twelfth = T(R(1) / R(12));
+    const T m2 = T(R(-2));
+    const T ee = a.ne + a.se, ww = a.nw + a.sw, nn = a.ne + a.nw, ss = a.se + a.sw;
+    gx = fmad(a.e - a.w, third, (ee - ww) * twelfth);
+    gy = fmad(a.n - a.s, third, (nn - ss) * twelfth);
+    const T axis = (a.e + a.w) + (a.n + a.s);
+    lap = fmad(T(R(4)), axis, fmad(T(R(-20)), a.c, nn + ss)) * sixth;
+    const T mc = m2 * a.c;
+    const T dxx_mid = (a.e + mc) + a.w;
+    const T dyy_mid = (a.n + mc) + a.s;
+    const T dxx_side = fmad(m2, a.n, nn) + fmad(m2, a.s, ss);
+    const T dyy_side = fmad(m2, a.e, ee) + fmad(m2, a.w, ww);
+    hxx = fmad(T(R(10)), dxx_mid, dxx_side) * twelfth;
+    hyy = fmad(T(R(10)), dyy_mid, dyy_side) * twelfth;
+    hxy = ((a.ne - a.nw) - (a.se - a.sw)) * T(R(0.25));
+}
 
 // Macroscopic quantities of one node that the collisions need.
-template <typename R>
+template <typename T>
 struct Macro {
-    R rho, omega;          // density, shear relaxation rate omega_4 = omega_5
-    R ux, uy, p;           // corrected velocity and pressure (Sec. 4 Eq. hydrodynamicfields)
-    R Ftx, Fty, Fpx, Fpy;  // total force and net gradient pressure force
-    R jx, jy;              // M_phi theta n, the interface first-order equilibrium moment
+    T rho, omega;          // density, shear relaxation rate omega_4 = omega_5
+    T ux, uy, p;           // corrected velocity and pressure (Sec. 4 Eq. hydrodynamicfields)
+    T Ftx, Fty, Fpx, Fpy;  // total force and net gradient pressure force
+    T jx, jy;              // M_phi theta n, the interface first-order equilibrium moment
 };
 
 // Forces and corrected fields of one node, from the phi and p* windows and the streamed g-bar
 // first moments (Sec. 2 properties and surface tension, Sec. 6.7 Marangoni components, Sec. 3
 // net gradient pressure force, Sec. 4 Eqs. hydrodynamicfields and fluidviscosity).
-template <typename R, bool LANGMUIR = false>
-__device__ __forceinline__ void node_macro(const Win<R>& ph, const Win<R>& ps, R jgx, R jgy,
-                                           R xf, R yf, const Consts<R>& K, Macro<R>& m)
+template <typename T, bool LANGMUIR = false>
+__device__ __forceinline__ void node_macro(const Win<T>& ph, const Win<T>& ps, T jgx, T jgy,
+                                           T xf, T yf, const Consts<scalar_t<T>>& K, Macro<T>& m)
 {
-    const R phi = ph.c;
-    m.rho = K.rho_b + phi * K.drho;
-    const R mu = K.mu_b + phi * K.dmu;
-    const R inv_rho = rcp_(m.rho);
+    using R = scalar_t<T>;
+    const T one = T(R(1));
+    const T phi = ph.c;
+    m.rho = fmad(phi, T(K.drho), T(K.rho_b));
+    const T mu = fmad(phi, T(K.dmu), T(K.mu_b));
+    const T inv_rho = rcp_(m.rho);
     // omega = 1 / (nu / c_s^2 + 1/2), nu = mu / rho
-    m.omega = rcp_(R(3) * mu * inv_rho + R(0.5));
+    m.omega = rcp_(fmad(T(R(3)) * mu, inv_rho, T(R(0.5))));
 
-    R dphx, dphy, lap, hxx, hyy, hxy, dpx, dpy;
-    grad_iso(ph, dphx, dphy);
-    lap_hess(ph, lap, hxx, hyy, hxy);
+    T dphx, dphy, lap, hxx, hyy, hxy, dpx, dpy;
+    stencils(ph, dphx, dphy, lap, hxx, hyy, hxy);
     grad_iso(ps, dpx, dpy);
 
     // regularised normal n = grad phi / (|grad phi| + 1e-6): defined everywhere, and rounding
     // noise in the bulk phases cannot set its direction
-    const R g2 = dphx * dphx + dphy * dphy;
-    const R gm = norm_(g2);
-    const R ig = rcp_(gm + R(1e-6));
-    const R nx = dphx * ig, ny = dphy * ig;
-    const R nHn = nx * nx * hxx + R(2) * nx * ny * hxy + ny * ny * hyy;
-    R kt, dktx, dkty;   // kappa-tilde and its gradient at the node
+    const T g2 = fmad(dphx, dphx, dphy * dphy);
+    const T gm = norm_(g2);
+    const T ig = rcp_(gm + T(R(1e-6)));
+    const T nx = dphx * ig, ny = dphy * ig;
+    const T nHn = fmad(nx * nx, hxx, fmad(T(R(2)) * nx * ny, hxy, ny * ny * hyy));
+    T kt, dktx, dkty;   // kappa-tilde and its gradient at the node
     if constexpr (LANGMUIR) {
-        const R om = R(1) - (K.psi0 + K.gpsx * xf + K.gpsy * yf);   // 1 - psi
-        kt = K.kt0 * (R(1) + K.beta * log_(om));
-        const R s = -K.kt0 * K.beta * rcp_(om);                      // d kappa-tilde / d psi
-        dktx = s * K.gpsx;
-        dkty = s * K.gpsy;
+        const T om = one - fmad(T(K.gpsx), xf, fmad(T(K.gpsy), yf, T(K.psi0)));   // 1 - psi
+        kt = T(K.kt0) * fmad(T(K.beta), log_(om), one);
+        const T s = T(-K.kt0 * K.beta) * rcp_(om);                               // d kt / d psi
+        dktx = s * T(K.gpsx);
+        dkty = s * T(K.gpsy);
     } else {
-        kt = K.kt0 + K.dktx * xf + K.dkty * yf;
-        dktx = K.dktx;
-        dkty = K.dkty;
+        kt = fmad(T(K.dktx), xf, fmad(T(K.dkty), yf, T(K.kt0)));
+        dktx = T(K.dktx);
+        dkty = T(K.dkty);
     }
-    const R cap = -kt * gm * (lap - nHn);          // -kappa-tilde |grad phi|^2 div n
-    const R nd = nx * dktx + ny * dkty;             // n . grad kappa-tilde
-    const R Fsx = cap * nx + g2 * (dktx - nx * nd);   // + |grad phi|^2 (I - n n) grad kappa-tilde
-    const R Fsy = cap * ny + g2 * (dkty - ny * nd);
-    const R dr = m.rho - K.rho_ref;
-    m.Ftx = Fsx + dr * K.gx;
-    m.Fty = Fsy + dr * K.gy;
-    m.Fpx = K.cs2_drho * dphx - dpx;
-    m.Fpy = K.cs2_drho * dphy - dpy;
+    const T cap = (kt * gm) * (nHn - lap);          // -kappa-tilde |grad phi|^2 div n
+    const T mnd = T(R(0)) - fmad(nx, dktx, ny * dkty);   // -n . grad kappa-tilde
+    // + |grad phi|^2 (I - n n) grad kappa-tilde
+    const T Fsx = fmad(cap, nx, g2 * fmad(nx, mnd, dktx));
+    const T Fsy = fmad(cap, ny, g2 * fmad(ny, mnd, dkty));
+    const T dr = m.rho - T(K.rho_ref);
+    m.Ftx = fmad(dr, T(K.gx), Fsx);
+    m.Fty = fmad(dr, T(K.gy), Fsy);
+    m.Fpx = T(K.cs2_drho) * dphx - dpx;
+    m.Fpy = T(K.cs2_drho) * dphy - dpy;
     // rho c_s^2 u = sum g-bar e + c_s^2 F_t / 2
-    m.ux = R(3) * inv_rho * (jgx + m.Ftx * R(1.0 / 6.0));
-    m.uy = R(3) * inv_rho * (jgy + m.Fty * R(1.0 / 6.0));
-    m.p = ps.c + R(0.5) * (m.Fpx * m.ux + m.Fpy * m.uy);
-    const R theta_m = K.mob * K.four_over_w * phi * (R(1) - phi);
+    const T three_inv_rho = T(R(3)) * inv_rho;
+    m.ux = three_inv_rho * fmad(m.Ftx, T(R(1.0 / 6.0)), jgx);
+    m.uy = three_inv_rho * fmad(m.Fty, T(R(1.0 / 6.0)), jgy);
+    m.p = fmad(T(R(0.5)), fmad(m.Fpx, m.ux, m.Fpy * m.uy), ps.c);
+    const T theta_m = T(K.mob * K.four_over_w) * (phi * (one - phi));
     m.jx = theta_m * nx;
     m.jy = theta_m * ny;
 }
 
 // Interface quantities of one node for the interface lattice alone (imposed flow): the
 // sharpening flux M_phi theta n from the phi window, as in node_macro.
-template <typename R>
-__device__ __forceinline__ void interface_flux(const Win<R>& ph, const Consts<R>& K, R& jx, R& jy)
+template <typename T>
+__device__ __forceinline__ void interface_flux(const Win<T>& ph, const Consts<scalar_t<T>>& K,
+                                               T& jx, T& jy)
 {
-    R dphx, dphy;
+    using R = scalar_t<T>;
+    T dphx, dphy;
     grad_iso(ph, dphx, dphy);
-    const R gm = norm_(dphx * dphx + dphy * dphy);
-    const R ig = rcp_(gm + R(1e-6));
-    const R theta_m = K.mob * K.four_over_w * ph.c * (R(1) - ph.c);
+    const T gm = norm_(fmad(dphx, dphx, dphy * dphy));
+    const T ig = rcp_(gm + T(R(1e-6)));
+    const T theta_m = T(K.mob * K.four_over_w) * (ph.c * (T(R(1)) - ph.c));
     jx = theta_m * (dphx * ig);
     jy = theta_m * (dphy * ig);
 }
@@ -273,22 +324,24 @@ __device__ __forceinline__ void imposed_velocity(R sx, R cx, R sy, R cy, R sign,
 
 // Populations from the nine raw moments (00,10,01,20,02,11,21,12,22) of D2Q9: the closed-form
 // inverse of the moment matrix, with shared partial sums.
-template <typename R>
-__device__ __forceinline__ void raw_to_pop_fast(R r00, R r10, R r01, R r20, R r02, R r11, R r21,
-                                                R r12, R r22, R q[9])
+template <typename T>
+__device__ __forceinline__ void raw_to_pop_fast(T r00, T r10, T r01, T r20, T r02, T r11, T r21,
+                                                T r12, T r22, T q[9])
 {
-    const R a = r20 - r22, b = r02 - r22;
-    const R sx = r10 - r12, sy = r01 - r21;
+    using R = scalar_t<T>;
+    const T half = T(R(0.5)), quarter = T(R(0.25));
+    const T a = r20 - r22, b = r02 - r22;
+    const T sx = r10 - r12, sy = r01 - r21;
     q[0] = (r00 - a) - (b + r22);
-    q[1] = R(0.5) * (a + sx);
-    q[3] = R(0.5) * (a - sx);
-    q[2] = R(0.5) * (b + sy);
-    q[4] = R(0.5) * (b - sy);
-    const R s = r22 + r21, t = r22 - r21, u = r11 + r12, v = r12 - r11;
-    q[5] = R(0.25) * (s + u);
-    q[6] = R(0.25) * (s - u);
-    q[7] = R(0.25) * (t - v);
-    q[8] = R(0.25) * (t + v);
+    q[1] = half * (a + sx);
+    q[3] = half * (a - sx);
+    q[2] = half * (b + sy);
+    q[4] = half * (b - sy);
+    const T s = r22 + r21, t = r22 - r21, u = r11 + r12, v = r12 - r11;
+    q[5] = quarter * (s + u);
+    q[6] = quarter * (s - u);
+    q[7] = quarter * (t - v);
+    q[8] = quarter * (t + v);
 }
 
 // Fluid-lattice collision (Sec. 4), evaluated in raw-moment space.  The printed update
@@ -304,54 +357,61 @@ __device__ __forceinline__ void raw_to_pop_fast(R r00, R r10, R r01, R r20, R r0
 //  * g-bar itself differs from V only in the zeroth and first raw moments.
 // The nine raw moments of the result are assembled and inverted once.  Inputs: the streamed
 // g-bar (overwritten with the post-collision populations) and p* = sum g-bar.
-template <typename R>
-__device__ __forceinline__ void collide_fluid(R g[9], R pstar, const Macro<R>& m)
+template <typename T>
+__device__ __forceinline__ void collide_fluid(T g[9], T pstar, const Macro<T>& m)
 {
-    const R third = R(1) / R(3), ninth = R(1) / R(9);
-    const R ux = m.ux, uy = m.uy, p = m.p, rho = m.rho, om = m.omega;
-    const R ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
-    const R rc2 = rho * third;                 // rho c^2
-    const R psi = p - rc2;                     // p - rho c^2
+    using R = scalar_t<T>;
+    const T third = T(R(1) / R(3)), ninth = T(R(1) / R(9)), half = T(R(0.5));
+    const T two = T(R(2));
+    const T ux = m.ux, uy = m.uy, p = m.p, rho = m.rho, om = m.omega;
+    const T ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const T rc2 = rho * third;                 // rho c^2
+    const T psi = p - rc2;                     // p - rho c^2
     // second-order raw moments of g-bar that survive the collision (deviator and 11)
-    const R dev = (g[1] + g[3]) - (g[2] + g[4]);
-    const R e11 = (g[5] - g[6]) + (g[7] - g[8]);
+    const T dev = (g[1] + g[3]) - (g[2] + g[4]);
+    const T e11 = (g[5] - g[6]) + (g[7] - g[8]);
     // central moments of V: deviator and 11, relaxed at omega
-    const R a2 = p - R(2) * rc2;
-    const R dV = dev + a2 * (ux2 - uy2);
-    const R cV = e11 + a2 * uxy;
-    const R dP = dV + om * (psi * (ux2 - uy2) - dV);
-    const R cP = cV + om * (psi * uxy - cV);
+    const T a2 = fmad(T(R(-2)), rc2, p);
+    const T dxy = ux2 - uy2, sxy = ux2 + uy2;
+    const T keep = T(R(1)) - om, ompsi = om * psi;
+    const T dP = fmad(keep, fmad(a2, dxy, dev), ompsi * dxy);
+    const T cP = fmad(keep, fmad(a2, uxy, e11), ompsi * uxy);
     // post-collision central moments of order >= 2 (equilibria except dP, cP)
-    const R tP = R(2) * p * third + psi * (ux2 + uy2);
-    const R c20 = R(0.5) * (tP + dP), c02 = R(0.5) * (tP - dP);
-    const R c21 = -psi * (third + ux2) * uy;
-    const R c12 = -psi * (third + uy2) * ux;
-    const R c22 = ninth * p + third * psi * (ux2 + uy2) + psi * ux2 * uy2;
+    const T tP = fmad(psi, sxy, T(R(2) / R(3)) * p);
+    const T c20 = half * (tP + dP), c02 = half * (tP - dP);
+    const T mpsi = T(R(0)) - psi;
+    const T c21 = (mpsi * uy) * (third + ux2);
+    const T c12 = (mpsi * ux) * (third + uy2);
+    const T c22 = fmad(ninth, p, psi * fmad(third, sxy, ux2 * uy2));
     // back to raw moments about 0 (lower central moments: p, -psi u)
-    const R b2 = p - R(2) * psi, b3 = p - R(3) * psi, b4 = p - R(4) * psi;
-    R r20 = c20 + ux2 * b2;
-    R r02 = c02 + uy2 * b2;
-    R r11 = cP + uxy * b2;
-    R r21 = c21 + uy * c20 + R(2) * ux * cP + ux2 * uy * b3;
-    R r12 = c12 + ux * c02 + R(2) * uy * cP + ux * uy2 * b3;
-    R r22 = c22 + R(2) * (uy * c21 + ux * c12) + uy2 * c20 + ux2 * c02 + R(4) * uxy * cP
-            + ux2 * uy2 * b4;
+    const T b2 = fmad(T(R(-2)), psi, p), b3 = fmad(T(R(-3)), psi, p);
+    const T b4 = fmad(T(R(-4)), psi, p);
+    T r20 = fmad(ux2, b2, c20);
+    T r02 = fmad(uy2, b2, c02);
+    T r11 = fmad(uxy, b2, cP);
+    T r21 = fmad(uy, c20, fmad(ux2 * uy, b3, fmad(two * ux, cP, c21)));
+    T r12 = fmad(ux, c02, fmad(ux * uy2, b3, fmad(two * uy, cP, c12)));
+    T r22 = fmad(two, fmad(uy, c21, ux * c12), c22);
+    r22 = fmad(uy2, c20, fmad(ux2, c02, r22));
+    r22 = fmad(T(R(4)) * uxy, cP, fmad(ux2 * uy2, b4, r22));
     // sources: sigma' (Gamma^t + Gamma^p matched, truncated), h-hat_0..2 and delta g^s
-    const R G00 = m.Fpx * ux + m.Fpy * uy;
-    const R Ftx = m.Ftx, Fty = m.Fty;
-    const R s20 = R(2) * third * (Ftx + m.Fpx) * ux + third * G00;
-    const R s02 = R(2) * third * (Fty + m.Fpy) * uy + third * G00;
-    const R s11 = third * ((Ftx + m.Fpx) * uy + (Fty + m.Fpy) * ux);
-    const R kq = R(0.25) * (R(1) - om) * (s20 - s02);   // (1/2 - omega/2)(s20 - s02)/2
-    r20 += third * G00 + R(0.5) * s20 + kq;
-    r02 += third * G00 + R(0.5) * s02 - kq;
-    r11 += (R(1) - R(0.5) * om) * s11;
-    r21 += third * third * Fty;
-    r12 += third * third * Ftx;
-    r22 += R(2) * ninth * G00;
-    const R r00 = pstar + G00;
-    const R r10 = rc2 * ux + R(0.5) * third * Ftx;
-    const R r01 = rc2 * uy + R(0.5) * third * Fty;
+    const T G00 = fmad(m.Fpx, ux, m.Fpy * uy);
+    const T Ftx = m.Ftx, Fty = m.Fty;
+    const T FTx = Ftx + m.Fpx, FTy = Fty + m.Fpy;
+    const T G3 = third * G00;
+    const T s20 = fmad(T(R(2) / R(3)) * FTx, ux, G3);
+    const T s02 = fmad(T(R(2) / R(3)) * FTy, uy, G3);
+    const T s11 = third * fmad(FTx, uy, FTy * ux);
+    const T kq = (T(R(0.25)) * keep) * (s20 - s02);   // (1/2 - omega/2)(s20 - s02)/2
+    r20 = r20 + fmad(half, s20, G3 + kq);
+    r02 = r02 + fmad(half, s02, G3 - kq);
+    r11 = fmad(fmad(T(R(-0.5)), om, T(R(1))), s11, r11);
+    r21 = fmad(ninth, Fty, r21);
+    r12 = fmad(ninth, Ftx, r12);
+    r22 = fmad(T(R(2) / R(9)), G00, r22);
+    const T r00 = pstar + G00;
+    const T r10 = fmad(rc2, ux, T(R(1) / R(6)) * Ftx);
+    const T r01 = fmad(rc2, uy, T(R(1) / R(6)) * Fty);
     raw_to_pop_fast(r00, r10, r01, r20, r02, r11, r21, r12, r22, g);
 }
 
@@ -361,105 +421,124 @@ __device__ __forceinline__ void collide_fluid(R g[9], R pstar, const Macro<R>& m
 // zeroth and first replaced by p and rho c^2 u), here all of orders >= 2 at omega; K (h-hat_0,
 // h-hat_1, h-hat_2) adds omega G00 / 18 K_0 and omega c^2 F_t / 12 (K_1, K_2); with equal rates
 // the cumulative source is (1 - omega/2) times the source itself, whose raw moments are sigma'.
-template <typename R>
-__device__ __forceinline__ void collide_fluid_srt(R g[9], R pstar, const Macro<R>& m)
+template <typename T>
+__device__ __forceinline__ void collide_fluid_srt(T g[9], T pstar, const Macro<T>& m)
 {
-    const R third = R(1) / R(3), ninth = R(1) / R(9);
-    const R ux = m.ux, uy = m.uy, p = m.p, rho = m.rho, om = m.omega;
-    const R ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
-    const R rc2 = rho * third;
-    const R psi = p - rc2;
+    using R = scalar_t<T>;
+    const T third = T(R(1) / R(3)), ninth = T(R(1) / R(9));
+    const T two = T(R(2)), m2 = T(R(-2));
+    const T ux = m.ux, uy = m.uy, p = m.p, rho = m.rho, om = m.omega;
+    const T ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const T rc2 = rho * third;
+    const T psi = p - rc2;
     // raw moments of g-bar of orders >= 2
-    const R s56 = g[5] + g[6], s78 = g[7] + g[8], d56 = g[5] - g[6], d78 = g[7] - g[8];
-    const R e20 = (g[1] + g[3]) + (s56 + s78);
-    const R e02 = (g[2] + g[4]) + (s56 + s78);
-    const R e11 = d56 + d78, e21 = s56 - s78, e12 = d56 - d78, e22 = s56 + s78;
+    const T s56 = g[5] + g[6], s78 = g[7] + g[8], d56 = g[5] - g[6], d78 = g[7] - g[8];
+    const T e20 = (g[1] + g[3]) + (s56 + s78);
+    const T e02 = (g[2] + g[4]) + (s56 + s78);
+    const T e11 = d56 + d78, e21 = s56 - s78, e12 = d56 - d78, e22 = s56 + s78;
     // central moments of V about u
-    const R a2 = p - R(2) * rc2, a3 = R(3) * rc2 - p, a4 = p - R(4) * rc2;
-    const R v20 = e20 + ux2 * a2, v02 = e02 + uy2 * a2, v11 = e11 + uxy * a2;
-    const R v21 = e21 - R(2) * ux * e11 - uy * e20 + ux2 * uy * a3;
-    const R v12 = e12 - R(2) * uy * e11 - ux * e02 + ux * uy2 * a3;
-    const R v22 = e22 - R(2) * (ux * e12 + uy * e21) + ux2 * e02 + uy2 * e20
-                  + R(4) * uxy * e11 + ux2 * uy2 * a4;
+    const T a2 = fmad(m2, rc2, p), a3 = fmad(T(R(3)), rc2, T(R(0)) - p);
+    const T a4 = fmad(T(R(-4)), rc2, p);
+    const T v20 = fmad(ux2, a2, e20), v02 = fmad(uy2, a2, e02), v11 = fmad(uxy, a2, e11);
+    const T v21 = fmad(m2 * ux, e11, fmad(T(R(0)) - uy, e20, fmad(ux2 * uy, a3, e21)));
+    const T v12 = fmad(m2 * uy, e11, fmad(T(R(0)) - ux, e02, fmad(ux * uy2, a3, e12)));
+    T v22 = fmad(m2, fmad(ux, e12, uy * e21), e22);
+    v22 = fmad(ux2, e02, fmad(uy2, e20, v22));
+    v22 = fmad(T(R(4)) * uxy, e11, fmad(ux2 * uy2, a4, v22));
     // relaxed towards the transformed Maxwellian's central moments
-    const R c20 = v20 + om * (p * third + psi * ux2 - v20);
-    const R c02 = v02 + om * (p * third + psi * uy2 - v02);
-    const R c11 = v11 + om * (psi * uxy - v11);
-    const R c21 = v21 + om * (-psi * (third + ux2) * uy - v21);
-    const R c12 = v12 + om * (-psi * (third + uy2) * ux - v12);
-    const R c22 = v22 + om * (ninth * p + third * psi * (ux2 + uy2) + psi * ux2 * uy2 - v22);
+    const T keep = T(R(1)) - om;
+    const T c20 = fmad(keep, v20, om * fmad(psi, ux2, third * p));
+    const T c02 = fmad(keep, v02, om * fmad(psi, uy2, third * p));
+    const T c11 = fmad(keep, v11, om * (psi * uxy));
+    const T mpsi = T(R(0)) - psi;
+    const T c21 = fmad(keep, v21, om * ((mpsi * uy) * (third + ux2)));
+    const T c12 = fmad(keep, v12, om * ((mpsi * ux) * (third + uy2)));
+    const T c22 = fmad(keep, v22, om * fmad(ninth, p, psi * fmad(third, ux2 + uy2, ux2 * uy2)));
     // back to raw moments about 0 (lower central moments: p, -psi u)
-    const R b2 = p - R(2) * psi, b3 = p - R(3) * psi, b4 = p - R(4) * psi;
-    R r20 = c20 + ux2 * b2;
-    R r02 = c02 + uy2 * b2;
-    R r11 = c11 + uxy * b2;
-    R r21 = c21 + uy * c20 + R(2) * ux * c11 + ux2 * uy * b3;
-    R r12 = c12 + ux * c02 + R(2) * uy * c11 + ux * uy2 * b3;
-    R r22 = c22 + R(2) * (uy * c21 + ux * c12) + uy2 * c20 + ux2 * c02 + R(4) * uxy * c11
-            + ux2 * uy2 * b4;
+    const T b2 = fmad(m2, psi, p), b3 = fmad(T(R(-3)), psi, p), b4 = fmad(T(R(-4)), psi, p);
+    T r20 = fmad(ux2, b2, c20);
+    T r02 = fmad(uy2, b2, c02);
+    T r11 = fmad(uxy, b2, c11);
+    T r21 = fmad(uy, c20, fmad(ux2 * uy, b3, fmad(two * ux, c11, c21)));
+    T r12 = fmad(ux, c02, fmad(ux * uy2, b3, fmad(two * uy, c11, c12)));
+    T r22 = fmad(two, fmad(uy, c21, ux * c12), c22);
+    r22 = fmad(uy2, c20, fmad(ux2, c02, r22));
+    r22 = fmad(T(R(4)) * uxy, c11, fmad(ux2 * uy2, b4, r22));
     // h-hat_0..2 and (1 - omega/2) sigma'
-    const R G00 = m.Fpx * ux + m.Fpy * uy;
-    const R Ftx = m.Ftx, Fty = m.Fty;
-    const R hs = R(1) - R(0.5) * om;
-    const R s20 = R(2) * third * (Ftx + m.Fpx) * ux + third * G00;
-    const R s02 = R(2) * third * (Fty + m.Fpy) * uy + third * G00;
-    const R s11 = third * ((Ftx + m.Fpx) * uy + (Fty + m.Fpy) * ux);
-    r20 += om * third * G00 + hs * s20;
-    r02 += om * third * G00 + hs * s02;
-    r11 += hs * s11;
-    r21 += om * ninth * Fty;
-    r12 += om * ninth * Ftx;
-    r22 += R(2) * ninth * om * G00;
-    const R r00 = pstar + G00;
-    const R r10 = rc2 * ux + R(0.5) * third * Ftx;
-    const R r01 = rc2 * uy + R(0.5) * third * Fty;
+    const T G00 = fmad(m.Fpx, ux, m.Fpy * uy);
+    const T Ftx = m.Ftx, Fty = m.Fty;
+    const T hs = fmad(T(R(-0.5)), om, T(R(1)));
+    const T FTx = Ftx + m.Fpx, FTy = Fty + m.Fpy;
+    const T G3 = third * G00;
+    const T s20 = fmad(T(R(2) / R(3)) * FTx, ux, G3);
+    const T s02 = fmad(T(R(2) / R(3)) * FTy, uy, G3);
+    const T s11 = third * fmad(FTx, uy, FTy * ux);
+    const T omG3 = om * G3;
+    r20 = fmad(hs, s20, r20 + omG3);
+    r02 = fmad(hs, s02, r02 + omG3);
+    r11 = fmad(hs, s11, r11);
+    r21 = fmad(om * ninth, Fty, r21);
+    r12 = fmad(om * ninth, Ftx, r12);
+    r22 = fmad(T(R(2) / R(9)) * om, G00, r22);
+    const T r00 = pstar + G00;
+    const T r10 = fmad(rc2, ux, T(R(1) / R(6)) * Ftx);
+    const T r01 = fmad(rc2, uy, T(R(1) / R(6)) * Fty);
     raw_to_pop_fast(r00, r10, r01, r20, r02, r11, r21, r12, r22, g);
 }
 
 // Interface-lattice operator of Sec. 5 with every rate equal to omega^phi (Sec. 7): all central
 // moments about u relax at omega^phi towards the equilibria (first order M_phi theta n,
 // c20 = c02 = c^2 phi, c22 = c^4 phi, the others 0), in raw-moment space.
-template <typename R>
-__device__ __forceinline__ void collide_ace_srt(R f[9], R phi, const Macro<R>& m, R omega_phi)
+template <typename T>
+__device__ __forceinline__ void collide_ace_srt(T f[9], T phi, const Macro<T>& m, T omega_phi)
 {
-    const R third = R(1) / R(3), ninth = R(1) / R(9);
-    const R ux = m.ux, uy = m.uy, om = omega_phi;
-    const R ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
-    const R s56 = f[5] + f[6], s78 = f[7] + f[8], d56 = f[5] - f[6], d78 = f[7] - f[8];
-    const R k10 = (f[1] - f[3]) + (d56 - d78);
-    const R k01 = (f[2] - f[4]) + (s56 - s78);
-    const R k20 = (f[1] + f[3]) + (s56 + s78);
-    const R k02 = (f[2] + f[4]) + (s56 + s78);
-    const R k11 = d56 + d78, k21 = s56 - s78, k12 = d56 - d78, k22 = s56 + s78;
+    using R = scalar_t<T>;
+    const T third = T(R(1) / R(3)), ninth = T(R(1) / R(9));
+    const T two = T(R(2)), m2 = T(R(-2)), zero = T(R(0));
+    const T ux = m.ux, uy = m.uy, om = omega_phi;
+    const T ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const T s56 = f[5] + f[6], s78 = f[7] + f[8], d56 = f[5] - f[6], d78 = f[7] - f[8];
+    const T k10 = (f[1] - f[3]) + (d56 - d78);
+    const T k01 = (f[2] - f[4]) + (s56 - s78);
+    const T k20 = (f[1] + f[3]) + (s56 + s78);
+    const T k02 = (f[2] + f[4]) + (s56 + s78);
+    const T k11 = d56 + d78, k21 = s56 - s78, k12 = d56 - d78, k22 = s56 + s78;
     // central moments about u
-    const R c10 = k10 - ux * phi, c01 = k01 - uy * phi;
-    const R c20 = k20 - R(2) * ux * k10 + ux2 * phi;
-    const R c02 = k02 - R(2) * uy * k01 + uy2 * phi;
-    const R c11 = k11 - ux * k01 - uy * k10 + uxy * phi;
-    const R c21 = k21 - R(2) * ux * k11 - uy * k20 + R(2) * uxy * k10 + ux2 * k01
-                  - ux2 * uy * phi;
-    const R c12 = k12 - R(2) * uy * k11 - ux * k02 + R(2) * uxy * k01 + uy2 * k10
-                  - ux * uy2 * phi;
-    const R c22 = k22 - R(2) * (ux * k12 + uy * k21) + ux2 * k02 + uy2 * k20 + R(4) * uxy * k11
-                  - R(2) * uxy * (uy * k10 + ux * k01) + ux2 * uy2 * phi;
+    const T mux = zero - ux, muy = zero - uy;
+    const T c10 = fmad(mux, phi, k10), c01 = fmad(muy, phi, k01);
+    const T c20 = fmad(m2 * ux, k10, fmad(ux2, phi, k20));
+    const T c02 = fmad(m2 * uy, k01, fmad(uy2, phi, k02));
+    const T c11 = fmad(mux, k01, fmad(muy, k10, fmad(uxy, phi, k11)));
+    const T c21 = fmad(m2 * ux, k11, fmad(muy, k20, fmad(two * uxy, k10,
+                       fmad(ux2, k01, fmad(ux2 * muy, phi, k21)))));
+    const T c12 = fmad(m2 * uy, k11, fmad(mux, k02, fmad(two * uxy, k01,
+                       fmad(uy2, k10, fmad(uy2 * mux, phi, k12)))));
+    T c22 = fmad(m2, fmad(ux, k12, uy * k21), k22);
+    c22 = fmad(ux2, k02, fmad(uy2, k20, c22));
+    c22 = fmad(T(R(4)) * uxy, k11, fmad(m2 * uxy, fmad(uy, k10, ux * k01),
+                                          fmad(ux2 * uy2, phi, c22)));
     // relaxation at one rate
-    const R a = c10 + om * (m.jx - c10);
-    const R b = c01 + om * (m.jy - c01);
-    const R keep = R(1) - om;
-    const R d20 = c20 + om * (third * phi - c20);
-    const R d02 = c02 + om * (third * phi - c02);
-    const R d11 = keep * c11, d21 = keep * c21, d12 = keep * c12;
-    const R d22 = c22 + om * (ninth * phi - c22);
+    const T keep = T(R(1)) - om;
+    const T a = fmad(keep, c10, om * m.jx);
+    const T b = fmad(keep, c01, om * m.jy);
+    const T d20 = fmad(keep, c20, om * (third * phi));
+    const T d02 = fmad(keep, c02, om * (third * phi));
+    const T d11 = keep * c11, d21 = keep * c21, d12 = keep * c12;
+    const T d22 = fmad(keep, c22, om * (ninth * phi));
     // back to raw moments about 0
-    const R r10 = a + ux * phi;
-    const R r01 = b + uy * phi;
-    const R r20 = d20 + R(2) * ux * a + ux2 * phi;
-    const R r02 = d02 + R(2) * uy * b + uy2 * phi;
-    const R r11 = d11 + ux * b + uy * a + uxy * phi;
-    const R r21 = d21 + uy * d20 + R(2) * ux * d11 + R(2) * uxy * a + ux2 * b + ux2 * uy * phi;
-    const R r12 = d12 + ux * d02 + R(2) * uy * d11 + R(2) * uxy * b + uy2 * a + ux * uy2 * phi;
-    const R r22 = d22 + R(2) * (uy * d21 + ux * d12) + uy2 * d20 + ux2 * d02 + R(4) * uxy * d11
-                  + R(2) * uxy * (uy * a + ux * b) + ux2 * uy2 * phi;
+    const T r10 = fmad(ux, phi, a);
+    const T r01 = fmad(uy, phi, b);
+    const T r20 = fmad(two * ux, a, fmad(ux2, phi, d20));
+    const T r02 = fmad(two * uy, b, fmad(uy2, phi, d02));
+    const T r11 = fmad(ux, b, fmad(uy, a, fmad(uxy, phi, d11)));
+    const T r21 = fmad(uy, d20, fmad(two * ux, d11, fmad(two * uxy, a,
+                       fmad(ux2, b, fmad(ux2 * uy, phi, d21)))));
+    const T r12 = fmad(ux, d02, fmad(two * uy, d11, fmad(two * uxy, b,
+                       fmad(uy2, a, fmad(ux * uy2, phi, d12)))));
+    T r22 = fmad(two, fmad(uy, d21, ux * d12), d22);
+    r22 = fmad(uy2, d20, fmad(ux2, d02, r22));
+    r22 = fmad(T(R(4)) * uxy, d11, fmad(two * uxy, fmad(uy, a, ux * b),
+                                          fmad(ux2 * uy2, phi, r22)));
     raw_to_pop_fast(phi, r10, r01, r20, r02, r11, r21, r12, r22, f);
 }
 
@@ -468,27 +547,30 @@ __device__ __forceinline__ void collide_ace_srt(R f[9], R phi, const Macro<R>& m
 // higher central moments to their equilibria (rates 1): c20 = c02 = c^2 phi, c22 = c^4 phi,
 // c11 = c21 = c12 = 0.  The closed-form g-hat of Sec. 5 is exactly this relaxation.  phi = sum f
 // (the node's zeroth moment, already formed for the stencil window).
-template <typename R>
-__device__ __forceinline__ void collide_ace(R f[9], R phi, const Macro<R>& m, R omega_phi)
+template <typename T>
+__device__ __forceinline__ void collide_ace(T f[9], T phi, const Macro<T>& m, T omega_phi)
 {
-    const R third = R(1) / R(3), ninth = R(1) / R(9);
-    const R ux = m.ux, uy = m.uy;
-    const R ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
-    const R k10 = (f[1] - f[3]) + (f[5] - f[6]) - (f[7] - f[8]);
-    const R k01 = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-    const R c10 = k10 - ux * phi, c01 = k01 - uy * phi;
-    const R a = c10 + omega_phi * (m.jx - c10);
-    const R b = c01 + omega_phi * (m.jy - c01);
-    const R cp = third * phi;
-    const R r10 = a + ux * phi;
-    const R r01 = b + uy * phi;
-    const R r20 = cp + R(2) * ux * a + ux2 * phi;
-    const R r02 = cp + R(2) * uy * b + uy2 * phi;
-    const R r11 = ux * b + uy * a + uxy * phi;
-    const R r21 = uy * cp + R(2) * uxy * a + ux2 * b + ux2 * uy * phi;
-    const R r12 = ux * cp + R(2) * uxy * b + uy2 * a + ux * uy2 * phi;
-    const R r22 = ninth * phi + (ux2 + uy2) * cp + R(2) * uxy * (uy * a + ux * b)
-                  + ux2 * uy2 * phi;
+    using R = scalar_t<T>;
+    const T third = T(R(1) / R(3)), ninth = T(R(1) / R(9)), two = T(R(2));
+    const T ux = m.ux, uy = m.uy;
+    const T ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const T k10 = ((f[1] - f[3]) + (f[5] - f[6])) - (f[7] - f[8]);
+    const T k01 = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
+    const T keep = T(R(1)) - omega_phi;
+    const T mux = T(R(0)) - ux, muy = T(R(0)) - uy;
+    // a = c10 + omega (jx - c10) with c10 = k10 - ux phi
+    const T a = fmad(keep, fmad(mux, phi, k10), omega_phi * m.jx);
+    const T b = fmad(keep, fmad(muy, phi, k01), omega_phi * m.jy);
+    const T cp = third * phi;
+    const T r10 = fmad(ux, phi, a);
+    const T r01 = fmad(uy, phi, b);
+    const T r20 = fmad(two * ux, a, fmad(ux2, phi, cp));
+    const T r02 = fmad(two * uy, b, fmad(uy2, phi, cp));
+    const T r11 = fmad(ux, b, fmad(uy, a, uxy * phi));
+    const T r21 = fmad(uy, cp, fmad(two * uxy, a, fmad(ux2, b, (ux2 * uy) * phi)));
+    const T r12 = fmad(ux, cp, fmad(two * uxy, b, fmad(uy2, a, (ux * uy2) * phi)));
+    const T r22 = fmad(ninth, phi, fmad(ux2 + uy2, cp, fmad(two * uxy, fmad(uy, a, ux * b),
+                                                             (ux2 * uy2) * phi)));
     raw_to_pop_fast(phi, r10, r01, r20, r02, r11, r21, r12, r22, f);
 }
 

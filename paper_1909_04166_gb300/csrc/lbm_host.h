@@ -23,6 +23,8 @@ cudaError_t configure_step(int block);
 template <typename R, typename S, int V>
 int step_blocks_per_sm(int block);
 template <typename R, typename S, int V>
+int step_warp_strips(int nstrips);
+template <typename R, typename S, int V>
 cudaError_t build_step_graph(const void*, const void*, const Geometry&, const Consts<R>&, int,
                              int, int*, int, int, cudaGraphExec_t*);
 template <typename R, typename S>

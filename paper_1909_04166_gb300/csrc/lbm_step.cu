@@ -25,6 +25,8 @@
 //     bounded) for its copies in flight and returns.
 #include "lbm_device.cuh"
 
+#include <type_traits>
+
 namespace cmlbm {
 
 static constexpr unsigned FULL = 0xffffffffu;
@@ -46,12 +48,12 @@ enum : int { kVarSRT = 1, kVarShear = 2, kVarLangmuir = 4 };
 template <typename S> struct Stages { static constexpr int value = 4; };
 template <> struct Stages<double> { static constexpr int value = 3; };
 
-// Per-warp shared memory: the stage tiles, then one mbarrier per stage; 128-byte multiple so that
-// every warp's tiles stay 16-byte aligned for the bulk copies.
-template <typename S>
+// Per-warp shared memory: the stage tiles (NT adjacent tiles per stage), then one mbarrier per
+// stage; 128-byte multiple so that every warp's tiles stay 16-byte aligned for the bulk copies.
+template <typename S, int NT = 1>
 __host__ __device__ constexpr int warp_smem_bytes()
 {
-    return (Stages<S>::value * (TILE * (int)sizeof(S) + 8) + 127) / 128 * 128;
+    return (Stages<S>::value * (NT * TILE * (int)sizeof(S) + 8) + 127) / 128 * 128;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -180,6 +182,54 @@ __device__ __forceinline__ void ld_pops_t(const S* tile, int lane, const Consts<
     for (int a = 0; a < 9; ++a) {
         if (!F_ONLY) g[a] = decode<S, R>(tile[a * 32 + lane], 0, a, K);
         f[a] = decode<S, R>(tile[(9 + a) * 32 + lane], 1, a, K);
+    }
+}
+
+// Push the 18 post-collision populations of one node to x + e_a in the row buffers rS, rC, rN
+// (rows y - 1, y, y + 1) at the column offsets cw, cc, ce (columns x - 1, x, x + 1).  fast:
+// warp-uniform, no wall is crossed by any node of this warp row.  Otherwise a population crossing
+// a no-slip wall returns to this node reversed (half-way bounce-back); one crossing only free-slip
+// walls has its normal components reversed and stays on this side of them (specular reflection).
+// bxw / bxe / bys / byn: the node lies next to the west / east / south / north wall.
+template <typename S, typename R, bool F_ONLY>
+__device__ __forceinline__ void push_node(const R g[9], const R f[9], S* rS, S* rC, S* rN, int cw,
+                                          int cc, int ce, bool bxw, bool bxe, bool bys,
+                                          bool byn, int slip, bool fast, const Consts<R>& K)
+{
+    S* pc = rC + cc;
+    S* p[9] = {pc, rC + ce, rN + cc, rC + cw, rS + cc, rN + ce, rN + cw, rS + cw, rS + ce};
+    if (fast) {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            if (!F_ONLY) p[a][a * 32] = encode<S, R>(g[a], 0, a, K);
+            p[a][(9 + a) * 32] = encode<S, R>(f[a], 1, a, K);
+        }
+        return;
+    }
+    constexpr int EXc[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    constexpr int EYc[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    constexpr int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    constexpr int MX[9] = {0, 3, 2, 1, 4, 6, 5, 8, 7};    // e_x reversed
+    constexpr int MY[9] = {0, 1, 4, 3, 2, 8, 7, 6, 5};    // e_y reversed
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const int ex = EXc[a], ey = EYc[a];
+        const bool cx = (ex < 0 && bxw) || (ex > 0 && bxe);
+        const bool cy = (ey < 0 && bys) || (ey > 0 && byn);
+        const bool sx = ((slip >> (ex < 0 ? 0 : 1)) & 1) != 0;
+        const bool sy = ((slip >> (ey < 0 ? 2 : 3)) & 1) != 0;
+        int plane = a;
+        S* q = p[a];
+        if ((cx && !sx) || (cy && !sy)) {
+            plane = OPP[a];
+            q = pc;
+        } else if (cx || cy) {
+            plane = cx ? (cy ? OPP[a] : MX[a]) : MY[a];
+            S* row = cy ? rC : (ey > 0 ? rN : (ey < 0 ? rS : rC));
+            q = row + (cx ? cc : (ex > 0 ? ce : (ex < 0 ? cw : cc)));
+        }
+        if (!F_ONLY) q[plane * 32] = encode<S, R>(g[a], 0, a, K);
+        q[(9 + plane) * 32] = encode<S, R>(f[a], 1, a, K);
     }
 }
 
@@ -328,46 +378,9 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
         S* rS = const_cast<S*>(row_ptr(dst, ym));
         S* rC = const_cast<S*>(row_ptr(dst, y));
         S* rN = const_cast<S*>(row_ptr(dst, yp));
-        S* pc = rC + cc;
-        S* p[9] = {pc, rC + ce, rN + cc, rC + cw, rS + cc, rN + ce, rN + cw, rS + cw, rS + ce};
-        if (!(bys || byn) && !xwall_warp) {      // warp-uniform: no wall crossed by this row
-            if (active) {
-#pragma unroll
-                for (int a = 0; a < 9; ++a) {
-                    if (!SHEAR) p[a][a * 32] = encode<S, R>(g[a], 0, a, K);
-                    p[a][(9 + a) * 32] = encode<S, R>(f[a], 1, a, K);
-                }
-            }
-        } else if (active) {
-            // a population crossing a no-slip wall returns to this node reversed (half-way
-            // bounce-back); one crossing only free-slip walls has its normal components
-            // reversed and stays on this side of them (specular reflection)
-            constexpr int EXc[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-            constexpr int EYc[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-            constexpr int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-            constexpr int MX[9] = {0, 3, 2, 1, 4, 6, 5, 8, 7};    // e_x reversed
-            constexpr int MY[9] = {0, 1, 4, 3, 2, 8, 7, 6, 5};    // e_y reversed
-#pragma unroll
-            for (int a = 0; a < 9; ++a) {
-                const int ex = EXc[a], ey = EYc[a];
-                const bool cx = (ex < 0 && bxw) || (ex > 0 && bxe);
-                const bool cy = (ey < 0 && bys) || (ey > 0 && byn);
-                const bool sx = ((G.slip >> (ex < 0 ? 0 : 1)) & 1) != 0;
-                const bool sy = ((G.slip >> (ey < 0 ? 2 : 3)) & 1) != 0;
-                int plane = a;
-                S* q = p[a];
-                if ((cx && !sx) || (cy && !sy)) {
-                    plane = OPP[a];
-                    q = pc;
-                } else if (cx || cy) {
-                    plane = cx ? (cy ? OPP[a] : MX[a]) : MY[a];
-                    S* row = cy ? rC : (ey > 0 ? rN : (ey < 0 ? rS : rC));
-                    q = row + (cx ? cc : (ex > 0 ? ce : (ex < 0 ? cw : cc)));
-                }
-                if (!SHEAR) q[plane * 32] = encode<S, R>(g[a], 0, a, K);
-                q[(9 + plane) * 32] = encode<S, R>(f[a], 1, a, K);
-            }
-        }
+        if (active)
+            push_node<S, R, SHEAR>(g, f, rS, rC, rN, cw, cc, ce, bxw, bxe, bys, byn, G.slip,
+                                   !(bys || byn) && !xwall_warp, K);
         issue(i + NS, st);      // the tile of row i is consumed: refill its stage
         rb = rc;
         rc = rn;
@@ -381,16 +394,259 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Paired FP32 march: a warp owns two adjacent tiles (64 columns) and lane l the columns x0 + l
+// (node A) and x0 + 32 + l (node B); both nodes go through the update at once in the packed FP32x2
+// arithmetic (F2), which halves the issued floating-point instructions per node, and the per-row
+// work of the pipeline (waits, copies, halo, row addressing) is shared by 64 nodes.  One bulk copy
+// per row brings both tiles (they are adjacent in memory).  An odd last strip has one tile; its
+// B half then repeats A (and stores nothing).
+// ---------------------------------------------------------------------------------------------
+struct Row3P {
+    F2 phw, phc, phe, psw, psc, pse;
+};
+
+// Sums of a lane's two columns and their east / west neighbours; hl / hr: this lane's halo
+// loads (one plane of the left / right halo column, or 0); lastA / lastB: this lane's node A / B
+// is the last active column of the warp (its east neighbour is the right halo column).
+__device__ __forceinline__ void window_row2(const float* ta, const float* tb, int lane,
+                                            bool lastA, bool lastB, float hl, float hr,
+                                            Row3P& row)
+{
+    F2 ps(ta[lane], tb[lane]);
+    F2 ph(ta[9 * 32 + lane], tb[9 * 32 + lane]);
+#pragma unroll
+    for (int a = 1; a < 9; ++a) {
+        ps += F2(ta[a * 32 + lane], tb[a * 32 + lane]);
+        ph += F2(ta[(9 + a) * 32 + lane], tb[(9 + a) * 32 + lane]);
+    }
+    F2 h(hl, hr);
+#pragma unroll
+    for (int off = 8; off >= 1; off >>= 1)
+        h += F2(__shfl_xor_sync(FULL, h.v.x, off), __shfl_xor_sync(FULL, h.v.y, off));
+    const float psl = __shfl_sync(FULL, h.v.x, 0), phl = __shfl_sync(FULL, h.v.x, 16);
+    const float psr = __shfl_sync(FULL, h.v.y, 0), phr = __shfl_sync(FULL, h.v.y, 16);
+    auto neighbours = [&](F2 c, float left, float right, F2& w, F2& e) {
+        const float upA = __shfl_up_sync(FULL, c.v.x, 1), upB = __shfl_up_sync(FULL, c.v.y, 1);
+        const float dnA = __shfl_down_sync(FULL, c.v.x, 1);
+        const float dnB = __shfl_down_sync(FULL, c.v.y, 1);
+        const float a31 = __shfl_sync(FULL, c.v.x, 31), b0 = __shfl_sync(FULL, c.v.y, 0);
+        w = F2(lane == 0 ? left : upA, lane == 0 ? a31 : upB);
+        e = F2(lastA ? right : (lane == 31 ? b0 : dnA), lastB ? right : dnB);
+    };
+    row.psc = ps;
+    row.phc = ph;
+    neighbours(ps, psl, psr, row.psw, row.pse);
+    neighbours(ph, phl, phr, row.phw, row.phe);
+}
+
+__device__ __forceinline__ void make_window2(const Row3P& s, const Row3P& c, const Row3P& n,
+                                             Win<F2>& ph, Win<F2>& ps)
+{
+    ph.sw = s.phw; ph.s = s.phc; ph.se = s.phe;
+    ph.w = c.phw;  ph.c = c.phc; ph.e = c.phe;
+    ph.nw = n.phw; ph.n = n.phc; ph.ne = n.phe;
+    ps.sw = s.psw; ps.s = s.psc; ps.se = s.pse;
+    ps.w = c.psw;  ps.c = c.psc; ps.e = c.pse;
+    ps.nw = n.psw; ps.n = n.psc; ps.ne = n.pse;
+}
+
+template <int V>
+__device__ __forceinline__ void march2(const float* __restrict__ src, float* __restrict__ dst,
+                                       const Geometry& G, const Consts<float>& K, int wstrip,
+                                       int seg, int seg_h, int* err)
+{
+    constexpr int NS = Stages<float>::value;
+    constexpr bool SRT = (V & kVarSRT) != 0;
+    constexpr bool LANGMUIR = (V & kVarLangmuir) != 0;
+    constexpr int STAGE = 2 * TILE;                  // floats per stage (two tiles)
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+
+    float* tiles = reinterpret_cast<float*>(smem_raw + wib * warp_smem_bytes<float, 2>());
+    const uint32_t bar0 = smem_u32(tiles + NS * STAGE);
+    if (lane == 0)
+        for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8 * s, 1);
+    mbar_init_fence();
+    __syncwarp();
+
+    const int t0 = 2 * wstrip;                       // first tile of the warp
+    const int nt = min(2, G.nstrips - t0);           // tiles present
+    const int x0 = t0 * 32;
+    const int w = min(64, G.nx - x0);                // active columns
+    const int wl = w - 1;                            // last active column (0..63)
+    const bool actA = lane < w, actB = lane + 32 < w;
+    const bool lastA = lane == wl, lastB = lane + 32 == wl;
+    const int TB = nt == 2 ? TILE : 0;               // offset of tile B in a stage
+    const int xA = actA ? x0 + lane : x0 + wl;       // idle lanes shadow the last column
+    const int xB = actB ? x0 + 32 + lane : x0 + wl;
+    const int xl = map_col(x0 - 1, G), xr = map_col(x0 + w, G);
+    const int row_elems = G.nstrips * TILE;
+    auto row_ptr = [&](const float* base, int row) { return base + (long long)row * row_elems; };
+
+    const int ys = seg * seg_h;
+    const int ye = min(ys + seg_h, G.ny);
+    const int nrows = ye - ys;
+    const bool up = (seg & 1) == 0;
+    auto row_of = [&](int k) { return map_row(up ? ys + k : ye - 1 - k, G); };
+
+    // halo: lanes 0..8 load g-bar plane q, lanes 16..24 f plane q, at columns xl and xr
+    const int hq = lane & 15;
+    const bool hlane = hq < 9;
+    const int hplane = (lane >> 4) * 9 + hq;
+    const int hoffl = col_off(xl) + hplane * 32;
+    const int hoffr = col_off(xr) + hplane * 32;
+    auto halo_load = [&](int k, float& hl, float& hr) {
+        hl = 0.0f;
+        hr = 0.0f;
+        if (hlane) {
+            const float* rb = row_ptr(src, row_of(k));
+            hl = __ldg(rb + hoffl);
+            hr = __ldg(rb + hoffr);
+        }
+    };
+
+    int issued = -2;
+    const uint32_t copy_bytes = (uint32_t)(nt * TILE * sizeof(float));
+    auto issue = [&](int k, int st) {
+        if (k > nrows) return;
+        __syncwarp();
+        if (lane == 0) {
+            fence_proxy_async();
+            const uint32_t bar = bar0 + 8 * st;
+            mbar_expect_tx(bar, copy_bytes);
+            bulk_g2s(smem_u32(tiles + st * STAGE), row_ptr(src, row_of(k)) + t0 * TILE,
+                     copy_bytes, bar);
+        }
+        issued = k;
+    };
+    auto wait_k = [&](int k, int st) -> bool {
+        return warp_wait(bar0 + 8 * st, (uint32_t)(((k + 1) / NS) & 1));
+    };
+    auto fail = [&](int k_failed) {
+        if (lane == 0) atomicCAS(err, 0, 1);
+        for (int k = k_failed; k <= issued; ++k) wait_k(k, (k + 1) % NS);
+    };
+
+    for (int k = -1; k <= NS - 2; ++k) issue(k, (k + 1) % NS);
+
+    Row3P rb, rc, rn;
+    float hl, hr, hl2, hr2;
+    halo_load(-1, hl, hr);
+    if (!wait_k(-1, 0)) { fail(-1); return; }
+    window_row2(tiles, tiles + TB, lane, lastA, lastB, hl, hr, rb);
+    issue(NS - 1, 0);
+    halo_load(0, hl, hr);
+    if (!wait_k(0, 1)) { fail(0); return; }
+    window_row2(tiles + STAGE, tiles + STAGE + TB, lane, lastA, lastB, hl, hr, rc);
+    halo_load(1, hl2, hr2);
+
+    // neighbour columns of the two nodes (periodic wrap; walls handled by the push)
+    auto cols = [&](int x, int& cw, int& cc, int& ce, bool& bxw, bool& bxe) {
+        int xm = x - 1, xp = x + 1;
+        bxw = xm < 0 && G.wall_x;
+        bxe = xp >= G.nx && G.wall_x;
+        if (xm < 0) xm += G.nx;
+        if (xp >= G.nx) xp -= G.nx;
+        cw = col_off(xm);
+        cc = col_off(x);
+        ce = col_off(xp);
+    };
+    int cwA, ccA, ceA, cwB, ccB, ceB;
+    bool bxwA, bxeA, bxwB, bxeB;
+    cols(xA, cwA, ccA, ceA, bxwA, bxeA);
+    cols(xB, cwB, ccB, ceB, bxwB, bxeB);
+    const bool xwall_warp = __any_sync(FULL, bxwA || bxeA || bxwB || bxeB);
+    const F2 xf{static_cast<float>(xA), static_cast<float>(xB)};
+    const F2 omega_phi(K.omega_phi);
+    bool ok = true;
+
+    auto body = [&](int i, int st) {
+        const int st1 = st + 1 == NS ? 0 : st + 1;
+        if (!wait_k(i + 1, st1)) { fail(i + 1); ok = false; return; }
+        window_row2(tiles + st1 * STAGE, tiles + st1 * STAGE + TB, lane, lastA, lastB, hl2, hr2,
+                    rn);
+        if (i + 2 <= nrows) halo_load(i + 2, hl2, hr2);
+
+        const int y = up ? ys + i : ye - 1 - i;
+        Win<F2> ph, ps;
+        if (up) make_window2(rb, rc, rn, ph, ps);
+        else make_window2(rn, rc, rb, ph, ps);
+        const float* ta = tiles + st * STAGE;
+        const float* tb = ta + TB;
+        F2 g[9], f[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            g[a] = F2(ta[a * 32 + lane], tb[a * 32 + lane]);
+            f[a] = F2(ta[(9 + a) * 32 + lane], tb[(9 + a) * 32 + lane]);
+        }
+        const F2 jgx = ((g[1] - g[3]) + (g[5] - g[6])) - (g[7] - g[8]);
+        const F2 jgy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
+        Macro<F2> m;
+        node_macro<F2, LANGMUIR>(ph, ps, jgx, jgy, xf, F2(float(y)), K, m);
+        if constexpr (SRT) collide_fluid_srt<F2>(g, ps.c, m);
+        else collide_fluid<F2>(g, ps.c, m);
+        if constexpr (SRT) collide_ace_srt<F2>(f, ph.c, m, omega_phi);
+        else collide_ace<F2>(f, ph.c, m, omega_phi);
+
+        int ym = y - 1, yp = y + 1;
+        const bool bys = ym < 0 && G.wall_y, byn = yp >= G.ny && G.wall_y;
+        if (ym < 0) ym += G.ny;
+        if (yp >= G.ny) yp -= G.ny;
+        float* rS = const_cast<float*>(row_ptr(dst, ym));
+        float* rC = const_cast<float*>(row_ptr(dst, y));
+        float* rN = const_cast<float*>(row_ptr(dst, yp));
+        const bool fast = !(bys || byn) && !xwall_warp;
+        if (actA) {
+            const float gA[9] = {g[0].v.x, g[1].v.x, g[2].v.x, g[3].v.x, g[4].v.x,
+                                 g[5].v.x, g[6].v.x, g[7].v.x, g[8].v.x};
+            const float fA[9] = {f[0].v.x, f[1].v.x, f[2].v.x, f[3].v.x, f[4].v.x,
+                                 f[5].v.x, f[6].v.x, f[7].v.x, f[8].v.x};
+            push_node<float, float, false>(gA, fA, rS, rC, rN, cwA, ccA, ceA, bxwA, bxeA, bys,
+                                           byn, G.slip, fast, K);
+        }
+        if (actB) {
+            const float gB[9] = {g[0].v.y, g[1].v.y, g[2].v.y, g[3].v.y, g[4].v.y,
+                                 g[5].v.y, g[6].v.y, g[7].v.y, g[8].v.y};
+            const float fB[9] = {f[0].v.y, f[1].v.y, f[2].v.y, f[3].v.y, f[4].v.y,
+                                 f[5].v.y, f[6].v.y, f[7].v.y, f[8].v.y};
+            push_node<float, float, false>(gB, fB, rS, rC, rN, cwB, ccB, ceB, bxwB, bxeB, bys,
+                                           byn, G.slip, fast, K);
+        }
+        issue(i + NS, st);
+        rb = rc;
+        rc = rn;
+    };
+
+    for (int i = 0, st = 1; i < nrows; ++i, st = (st + 1 == NS ? 0 : st + 1)) {
+        body(i, st);
+        if (!ok) return;
+    }
+}
+
+// The FP32 coupled step variants run paired (two tiles per warp); the others one tile per warp.
+template <typename R, typename S, int V>
+struct Paired {
+    static constexpr bool value =
+        std::is_same<R, float>::value && std::is_same<S, float>::value && (V & kVarShear) == 0;
+};
+template <typename R, typename S, int V>
+__host__ __device__ constexpr int tiles_per_warp() { return Paired<R, S, V>::value ? 2 : 1; }
+
 template <typename R, typename S, int V>
 __global__ void __launch_bounds__(256)
 step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R> K,
             StepLaunch L)
 {
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    const int strip = warp % G.nstrips;
-    const int seg = warp / G.nstrips;
+    constexpr int NT = tiles_per_warp<R, S, V>();
+    const int wstrips = (G.nstrips + NT - 1) / NT;   // strips of NT tiles
+    const int strip = warp % wstrips;
+    const int seg = warp / wstrips;
     if (seg >= L.nseg) return;                       // warp-uniform
-    march<R, S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign);
+    if constexpr (NT == 2) march2<V>(src, dst, G, K, strip, seg, L.seg_h, L.err);
+    else march<R, S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign);
 }
 
 // One time step of many independent grids in one launch: warp w takes task w = (case, local
@@ -522,8 +778,18 @@ __global__ void unpack_kernel(const double* __restrict__ in, S* __restrict__ sta
 // ---------------------------------------------------------------------------------------------
 // Host-side launchers (called from lbm_api.cu)
 // ---------------------------------------------------------------------------------------------
-template <typename S>
-size_t step_smem_bytes(int block) { return (size_t)(block / 32) * warp_smem_bytes<S>(); }
+template <typename S, int NT>
+size_t tile_smem_bytes(int block) { return (size_t)(block / 32) * warp_smem_bytes<S, NT>(); }
+template <typename R, typename S, int V>
+size_t step_smem_bytes(int block) { return tile_smem_bytes<S, tiles_per_warp<R, S, V>()>(block); }
+
+// Warp strips of a row: tiles per warp for this variant.
+template <typename R, typename S, int V>
+int step_warp_strips(int nstrips)
+{
+    constexpr int NT = tiles_per_warp<R, S, V>();
+    return (nstrips + NT - 1) / NT;
+}
 
 // Allow the dynamic shared memory of a block of `block` threads (call once per device).
 template <typename R, typename S, int V>
@@ -531,7 +797,7 @@ cudaError_t configure_step(int block)
 {
     cudaError_t e = cudaFuncSetAttribute(step_kernel<R, S, V>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)step_smem_bytes<S>(block));
+                                         (int)step_smem_bytes<R, S, V>(block));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(step_kernel<R, S, V>,
                                 cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -544,7 +810,8 @@ int step_blocks_per_sm(int block)
 {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<R, S, V>, block,
-                                                      step_smem_bytes<S>(block)) != cudaSuccess)
+                                                      step_smem_bytes<R, S, V>(block)) !=
+        cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
@@ -558,10 +825,10 @@ cudaError_t launch_step(const void* src, void* dst, const Geometry& G, const Con
     L.nseg = (G.ny + seg_h - 1) / seg_h;
     L.err = err;
     L.flow_sign = flow_sign;
-    const long long warps = (long long)G.nstrips * L.nseg;
+    const long long warps = (long long)step_warp_strips<R, S, V>(G.nstrips) * L.nseg;
     const int wpb = block / 32;
     const long long grid = (warps + wpb - 1) / wpb;
-    step_kernel<R, S, V><<<(unsigned)grid, block, step_smem_bytes<S>(block), st>>>(
+    step_kernel<R, S, V><<<(unsigned)grid, block, step_smem_bytes<R, S, V>(block), st>>>(
         static_cast<const S*>(src), static_cast<S*>(dst), G, K, L);
     return cudaGetLastError();
 }
@@ -578,7 +845,7 @@ cudaError_t build_step_graph(const void* a, const void* b, const Geometry& G, co
     L.nseg = (G.ny + seg_h - 1) / seg_h;
     L.err = err;
     L.flow_sign = flow_sign;
-    const long long warps = (long long)G.nstrips * L.nseg;
+    const long long warps = (long long)step_warp_strips<R, S, V>(G.nstrips) * L.nseg;
     const int wpb = block / 32;
     const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
     cudaGraph_t graph = nullptr;
@@ -595,7 +862,7 @@ cudaError_t build_step_graph(const void* a, const void* b, const Geometry& G, co
         p.func = (void*)step_kernel<R, S, V>;
         p.gridDim = dim3(grid);
         p.blockDim = dim3(block);
-        p.sharedMemBytes = (unsigned)step_smem_bytes<S>(block);
+        p.sharedMemBytes = (unsigned)step_smem_bytes<R, S, V>(block);
         p.kernelParams = args;
         cudaGraphNode_t node;
         e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &p);
@@ -611,7 +878,7 @@ cudaError_t configure_batch(int block)
 {
     cudaError_t e = cudaFuncSetAttribute(batch_step_kernel<R, S>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)step_smem_bytes<S>(block));
+                                         (int)tile_smem_bytes<S, 1>(block));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(batch_step_kernel<R, S>,
                                 cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -624,7 +891,7 @@ cudaError_t launch_batch_step(void* base, const BatchCase<R>* cases, const int2*
 {
     const int wpb = block / 32;
     const unsigned grid = (unsigned)((ntasks + wpb - 1) / wpb);
-    batch_step_kernel<R, S><<<grid, block, step_smem_bytes<S>(block), st>>>(
+    batch_step_kernel<R, S><<<grid, block, tile_smem_bytes<S, 1>(block), st>>>(
         static_cast<S*>(base), cases, tasks, ntasks, parity, err);
     return cudaGetLastError();
 }
@@ -651,7 +918,7 @@ cudaError_t build_batch_graph(void* base, const BatchCase<R>* cases, const int2*
         p.func = (void*)batch_step_kernel<R, S>;
         p.gridDim = dim3(grid);
         p.blockDim = dim3(block);
-        p.sharedMemBytes = (unsigned)step_smem_bytes<S>(block);
+        p.sharedMemBytes = (unsigned)tile_smem_bytes<S, 1>(block);
         p.kernelParams = args;
         cudaGraphNode_t node;
         e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &p);
@@ -704,6 +971,7 @@ cudaError_t launch_unpack(const double* in, void* state, const Geometry& G, cons
 }
 
 #define CMLBM_INSTANTIATE_STEP(R, S, V)                                                           \
+    template int step_warp_strips<R, S, V>(int);                                                \
     template cudaError_t configure_step<R, S, V>(int);                                          \
     template int step_blocks_per_sm<R, S, V>(int);                                              \
     template cudaError_t build_step_graph<R, S, V>(const void*, const void*, const Geometry&,   \
@@ -714,7 +982,6 @@ cudaError_t launch_unpack(const double* in, void* state, const Geometry& G, cons
                                               cudaStream_t);
 
 #define CMLBM_INSTANTIATE(R, S)                                                                   \
-    template size_t step_smem_bytes<S>(int);                                                    \
     template cudaError_t configure_batch<R, S>(int);                                            \
     template cudaError_t build_batch_graph<R, S>(void*, const BatchCase<R>*, const int2*, int,  \
                                                  int, int, int*, int, cudaGraphExec_t*);        \

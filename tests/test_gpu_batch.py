@@ -1,9 +1,10 @@
 """Batched stepping (lbm_batch_*): one launch per step over many independent cases.
 
-Each case must evolve as in its own context (the batched kernel inlines the same per-node
-arithmetic; the compiler may contract a few multiply-adds differently in the two kernels, so
-the comparison allows rounding-level differences), match the FP64 oracle, and survive the
-autotuner bit for bit (within one kernel the launch shape does not change any result)."""
+Each case must evolve as in its own context (the batched kernel runs the same per-node
+arithmetic one node per lane, while the single-grid FP32 step updates two columns per lane on
+the packed FP32x2 instructions, so the two round differently: the comparison allows FP32
+rounding-level differences after 37 steps), match the FP64 oracle, and survive the autotuner
+bit for bit (within one kernel the launch shape does not change any result)."""
 import numpy as np
 import pytest
 
@@ -25,7 +26,7 @@ def mixed_cases():
     ]
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-6), ("fp64", 1e-14)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp64", 1e-14)])
 def test_batch_cases_match_their_own_contexts(prec, tol):
     cases = mixed_cases()
     with lbm.Batch(cases, precision=prec) as b:
