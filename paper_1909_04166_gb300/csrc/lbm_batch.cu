@@ -75,7 +75,10 @@ int build_tasks(lbm_batch* b, int h)
     for (int c = 0; c < n; ++c) {
         const HostCase& hc = b->cases[c];
         const int nseg = (hc.G.ny + h - 1) / h;
-        const int nw = hc.G.nstrips * nseg;
+        const int wstrips = with_types(b->precision, [&](auto r, auto s) {
+            return step_warp_strips<decltype(r), decltype(s), 0>(hc.G.nstrips);
+        });
+        const int nw = wstrips * nseg;
         for (int k = 0; k < nw; ++k) tasks.push_back(make_int2(c, k));
         if (b->precision == LBM_FP64)
             cd[c] = BatchCase<double>{hc.G, h, nseg, hc.off0, hc.off1, hc.Kd};

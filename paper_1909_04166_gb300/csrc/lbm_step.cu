@@ -662,11 +662,14 @@ batch_step_kernel(S* __restrict__ base, const BatchCase<R>* __restrict__ cases,
     const int2 t = tasks[warp];
     const BatchCase<R>& c = cases[t.x];
     const Geometry G = c.G;
-    const int strip = t.y % G.nstrips;
-    const int seg = t.y / G.nstrips;
+    constexpr int NT = tiles_per_warp<R, S, 0>();
+    const int wstrips = (G.nstrips + NT - 1) / NT;
+    const int strip = t.y % wstrips;
+    const int seg = t.y / wstrips;
     const S* src = base + (parity ? c.off1 : c.off0);
     S* dst = base + (parity ? c.off0 : c.off1);
-    march<R, S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1);
+    if constexpr (NT == 2) march2<0>(src, dst, G, c.K, strip, seg, c.seg_h, err);
+    else march<R, S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -878,7 +881,7 @@ cudaError_t configure_batch(int block)
 {
     cudaError_t e = cudaFuncSetAttribute(batch_step_kernel<R, S>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tile_smem_bytes<S, 1>(block));
+                                         (int)step_smem_bytes<R, S, 0>(block));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(batch_step_kernel<R, S>,
                                 cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -891,7 +894,7 @@ cudaError_t launch_batch_step(void* base, const BatchCase<R>* cases, const int2*
 {
     const int wpb = block / 32;
     const unsigned grid = (unsigned)((ntasks + wpb - 1) / wpb);
-    batch_step_kernel<R, S><<<grid, block, tile_smem_bytes<S, 1>(block), st>>>(
+    batch_step_kernel<R, S><<<grid, block, step_smem_bytes<R, S, 0>(block), st>>>(
         static_cast<S*>(base), cases, tasks, ntasks, parity, err);
     return cudaGetLastError();
 }
@@ -918,7 +921,7 @@ cudaError_t build_batch_graph(void* base, const BatchCase<R>* cases, const int2*
         p.func = (void*)batch_step_kernel<R, S>;
         p.gridDim = dim3(grid);
         p.blockDim = dim3(block);
-        p.sharedMemBytes = (unsigned)tile_smem_bytes<S, 1>(block);
+        p.sharedMemBytes = (unsigned)step_smem_bytes<R, S, 0>(block);
         p.kernelParams = args;
         cudaGraphNode_t node;
         e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &p);
