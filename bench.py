@@ -79,8 +79,8 @@ def kernel_source_hash() -> str:
 # DRAM traffic per launch of the step kernel from an ncu capture (profiles/), keyed by the
 # hash of the kernel sources it was taken on; scaled by node count to the bench workload.
 NCU_TRAFFIC = {
-    # profiles/step_kernel_impact_2048x1024_fp32.md (read 152.59 MB + write 98.80 MB)
-    ("111f7b57711cb659", "impact", "fp32"): 251_388_416,
+    # profiles/step_kernel_impact_2048x1024_fp32.md (read 152.09 MB + write 98.38 MB)
+    ("60e78babbd4d22ad", "impact", "fp32"): 250_467_584,
 }
 
 
