@@ -27,7 +27,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_LU = {"fp32": 144, "fp64": 288}       # 18 populations read + written once per node
+# bytes read + written once per node update: 18 populations (FP32 / FP64); 16-bit: 18 deviations
+# plus the two FP32 zeroth-moment planes
+BYTES_PER_LU = {"fp32": 144, "fp64": 288, "fp16": 88, "bf16": 88}
 HBM_FALLBACK_GBS = 6800.0
 L2_BYTES = 129e6
 METRIC = "MLUPS (million node updates of both lattices per second)"
@@ -359,7 +361,7 @@ def measure_storage(case, steps, device=0, stream=0):
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / steps
-        bpl = {"fp32": 144, "fp16": 72, "bf16": 72}[prec]
+        bpl = BYTES_PER_LU[prec]
         out[f"storage_{prec}"] = {
             "mlups": round(case.nodes / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms, 5),
             "algorithmic_gbs": round(bpl * case.nodes / (ms * 1e-3) / 1e9, 1),

@@ -77,11 +77,16 @@ typedef enum {
     LBM_FP32_FP16 = 2,  /* collided in float; stored as IEEE half deviations (see below) */
     LBM_FP32_BF16 = 3   /* collided in float; stored as bfloat16 deviations (see below) */
 } lbm_precision;
-/* 16-bit storage: population a of lattice L is stored as (q_a - w_a ref_L) * scale_L, w the
- * D2Q9 weights (4/9, 1/9, 1/36), ref_g = params.store_ref_g (a reference pressure, default 0),
- * ref_f = 1/2 (the mid phase), scale_L = params.store_scale_g / store_scale_f, or when those are
- * 0 the defaults 2^14 / 2^8 for FP16 (|g-bar| up to ~4 without overflow, deviations above
- * ~4e-9 kept normal) and 1 / 1 for BF16.  Collisions, forces and stencils stay in float. */
+/* 16-bit storage: every tile (32 columns of one row) holds two FP32 planes with each node's
+ * zeroth moments of the previous time level, Z_g = p* and Z_f = phi, and then the 18 populations
+ * as 16-bit deviations d_a = (q_a - w_a Z_L) scale_L from the rest-state populations w_a Z_L of
+ * the node they sit on (w the D2Q9 weights 4/9, 1/9, 1/36; L the lattice).  The kernel that
+ * pushes a population knows its destination's Z from its stencil window, so the pressure level
+ * and the phase fraction are carried in FP32 and only the departures from rest are rounded, the
+ * floating exponent keeping the light phase's momentum significant.  scale_L =
+ * params.store_scale_g / store_scale_f, or when those are 0 the defaults 2^14 / 2^12 for FP16
+ * (deviations from ~1e-6 to ~4 in the normal range) and 1 / 1 for BF16.  Collisions, forces and
+ * stencils stay in float. */
 
 /* Boundary kind of the sides of one axis. */
 typedef enum {
@@ -139,7 +144,6 @@ typedef struct {
     int32_t device;                 /* CUDA device ordinal */
     void* stream;                   /* cudaStream_t for all work of the context */
     double store_scale_g, store_scale_f;  /* 16-bit storage scales; 0 = default */
-    double store_ref_g;             /* 16-bit storage reference pressure of the fluid lattice */
     /* Further forms of the paper's cases; all zero gives the coupled cascaded step above. */
     int32_t bc_x_hi, bc_y_hi;       /* lbm_bc of the right (x = nx - 1) / top (y = ny - 1) side
                                        when it differs from bc_x / bc_y (which then name the
@@ -203,15 +207,28 @@ int lbm_set_graphs(lbm_ctx* ctx, int32_t enable);
  * rho as defined by Sec. 4 Eq. hydrodynamicfields.  Any pointer may be NULL.  Synchronises. */
 int lbm_get_fields(lbm_ctx* ctx, double* phi, double* p, double* ux, double* uy, double* rho);
 
-/* Checkpoint / restore of the raw state: g and f as [9][ny][nx] doubles each (converted from /
- * to the storage precision).  Synchronises.  A restored state steps exactly as the saved one. */
+/* The populations of the current state: g and f as [9][ny][nx] doubles each (decoded from /
+ * encoded to the storage format).  Synchronises.  In FP32 / FP64 storage a state written back
+ * steps exactly as the one read out.  The 16-bit modes re-derive each node's zeroth-moment
+ * planes from the populations given, so there a write-back is exact to one 16-bit rounding of
+ * the deviations; use lbm_save_state / lbm_load_state for exact checkpoints. */
 int lbm_get_populations(lbm_ctx* ctx, double* g, double* f);
 int lbm_set_populations(lbm_ctx* ctx, const double* g, const double* f);
 
+/* Exact checkpoint: the current state buffer byte for byte (bytes = lbm_state_bytes / 2) and
+ * the step counter, to / from caller-owned host memory.  Synchronises.  A loaded state steps
+ * exactly as the saved one in every precision mode.  LBM_ERR_ARG if bytes differs. */
+int lbm_save_state(lbm_ctx* ctx, void* host, size_t bytes, int64_t* steps);
+int lbm_load_state(lbm_ctx* ctx, const void* host, size_t bytes, int64_t steps);
+
 /* Device pointer of the current state, valid until the next lbm_step.  Element type double for
- * LBM_FP64, float for LBM_FP32, half / bfloat16 (encoded as above) for the 16-bit modes.  Layout: tiles of 32 columns; population a (0..8 fluid g-bar,
- * 9..17 interface f) of node (x, y) is element ((y * nstrips + x / 32) * 18 + a) * 32 + x % 32,
- * nstrips = ceil(nx / 32).  *elements receives the element count of one state buffer. */
+ * LBM_FP64, float for LBM_FP32, half / bfloat16 (encoded as above) for the 16-bit modes.
+ * Layout: tiles of 32 columns, nstrips = ceil(nx / 32) per row, E elements per tile (E = 576 for
+ * FP32 / FP64, 704 for the 16-bit modes).  Population a (0..8 fluid g-bar, 9..17 interface f) of
+ * node (x, y) is element (y * nstrips + x / 32) * E + P0 + 32 a + x % 32 with P0 = 0 (FP32 /
+ * FP64) or 128 (16-bit); in the 16-bit modes Z_g / Z_f of the node is the float at element
+ * (y * nstrips + x / 32) * E + 2 (x % 32) + 64 L, L = 0 / 1.  *elements receives the element
+ * count of one state buffer. */
 int lbm_state_device(lbm_ctx* ctx, void** state, int32_t* nstrips, int64_t* elements);
 
 /* Synchronise the stream and report LBM_ERR_TIMEOUT if any step since creation gave up on a

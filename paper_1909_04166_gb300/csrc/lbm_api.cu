@@ -155,7 +155,7 @@ int make_ctx(const lbm_params* params, void* ext, size_t ext_bytes, lbm_ctx** ou
     c->Kd = make_consts<double>(*params);
     c->Kf = make_consts<float>(*params);
     c->elem = elem_bytes(params->precision);
-    c->state_bytes = buffer_elems(params->nx, params->ny) * c->elem;
+    c->state_bytes = buffer_elems(params->nx, params->ny, params->precision) * c->elem;
     c->st = static_cast<cudaStream_t>(params->stream);
     int dev = params->device, nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -340,7 +340,8 @@ int lbm_state_bytes(const lbm_params* params, size_t* bytes)
     if (!bytes) return LBM_ERR_ARG;
     int s = validate(params);
     if (s) return s;
-    *bytes = 2 * buffer_elems(params->nx, params->ny) * elem_bytes(params->precision);
+    *bytes = 2 * buffer_elems(params->nx, params->ny, params->precision) *
+             elem_bytes(params->precision);
     return LBM_OK;
 }
 
@@ -506,13 +507,38 @@ int lbm_set_populations(lbm_ctx* c, const double* g, const double* f)
     return LBM_OK;
 }
 
+int lbm_save_state(lbm_ctx* c, void* host, size_t bytes, int64_t* steps)
+{
+    if (!c || !host || bytes != c->state_bytes) return LBM_ERR_ARG;
+    if (!c->initialised) return LBM_ERR_STATE;
+    cudaSetDevice(c->P.device);
+    cudaError_t e = cudaMemcpyAsync(host, cur_state(c), bytes, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    if (steps) *steps = c->steps;
+    return check_device_error(c);
+}
+
+int lbm_load_state(lbm_ctx* c, const void* host, size_t bytes, int64_t steps)
+{
+    if (!c || !host || bytes != c->state_bytes || steps < 0) return LBM_ERR_ARG;
+    cudaSetDevice(c->P.device);
+    c->cur = 0;
+    cudaError_t e = cudaMemcpyAsync(cur_state(c), host, bytes, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    c->initialised = true;
+    c->steps = steps;
+    return LBM_OK;
+}
+
 int lbm_state_device(lbm_ctx* c, void** state, int32_t* nstrips, int64_t* elements)
 {
     if (!c || !state) return LBM_ERR_ARG;
     if (!c->initialised) return LBM_ERR_STATE;
     *state = cur_state(c);
     if (nstrips) *nstrips = c->G.nstrips;
-    if (elements) *elements = (int64_t)buffer_elems(c->G.nx, c->G.ny);
+    if (elements) *elements = (int64_t)buffer_elems(c->G.nx, c->G.ny, c->P.precision);
     return LBM_OK;
 }
 

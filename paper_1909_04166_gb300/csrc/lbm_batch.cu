@@ -189,10 +189,10 @@ int lbm_batch_create(const lbm_params* params, int32_t ncases, lbm_batch** out)
         hc.G = make_geometry(params[c]);
         hc.Kd = make_consts<double>(params[c]);
         hc.Kf = make_consts<float>(params[c]);
-        const long long elems = (long long)hc.G.ny * hc.G.nstrips * 18 * 32;
+        const long long elems = (long long)buffer_elems(hc.G.nx, hc.G.ny, b->precision);
         hc.off0 = off;
         hc.off1 = off + elems;
-        off += 2 * elems;      // multiples of 576 elements keep every buffer 16-byte aligned
+        off += 2 * elems;      // whole tiles (multiples of 16 bytes) keep every buffer aligned
         hc.nodes = (long long)hc.G.nx * hc.G.ny;
         b->max_nodes = std::max(b->max_nodes, hc.nodes);
         b->total_nodes += hc.nodes;

@@ -36,9 +36,9 @@ struct Consts {
     R beta, psi0, gpsx, gpsy;
     R u0pi;              // imposed shear flow (Sec. 6.1): U_0 pi
     R inv_nx, inv_ny;    // 1 / L0 along x and y for the imposed flow
-    // 16-bit storage codec, lattice 0 = fluid g-bar, 1 = interface f: the stored number is
-    // (q_a - w_a ref) * scale; unused for FP32 / FP64 storage
-    R st_scale[2], st_inv[2], st_ref[2];
+    // 16-bit storage, lattice 0 = fluid g-bar, 1 = interface f: deviation scale and its inverse
+    // (unused for FP32 / FP64 storage)
+    R st_scale[2], st_inv[2];
 };
 
 // D2Q9 weights (the populations of the rest state are w_a times the zeroth moment).
@@ -48,10 +48,26 @@ __host__ __device__ constexpr double d2q9_w(int a)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Storage codec.  FP32 and FP64 states hold the populations themselves; FP16 / BF16 states
-// hold scaled deviations from the rest-state weights times a per-lattice reference.
+// Storage.  FP32 and FP64 states hold the populations themselves.  The 16-bit states hold, per
+// tile, two FP32 planes with every node's zeroth moments of the previous time level (Z_g = p*,
+// Z_f = phi) and 18 planes of scaled deviations d_a = (q_a - w_a Z) s_L from the rest-state
+// populations w_a Z of the node a population sits on (s_L per lattice).  Whoever writes a pushed
+// population knows the destination's Z (it is in the writer's stencil window), so the reference
+// costs no extra traffic, the pressure level and the phase fraction stay in FP32, and only the
+// (small) departures from rest are rounded to 16 bits, with the floating exponent keeping the
+// light phase's momentum significant.  sum_a q_a = Z + (sum_a d_a) / s_L.
 // ---------------------------------------------------------------------------------------------
 template <typename S> struct Narrow { static constexpr bool value = sizeof(S) < 4; };
+
+// Tile geometry in elements of S: population plane p (0..17) of column c of a tile is element
+// P0 + 32 p + c; in the 16-bit form the FP32 planes Z_g, Z_f fill the first 256 bytes.
+template <typename S>
+struct Tile {
+    static constexpr int ZBYTES = Narrow<S>::value ? 2 * 32 * 4 : 0;
+    static constexpr int BYTES = ZBYTES + 18 * 32 * (int)sizeof(S);
+    static constexpr int ELEMS = BYTES / (int)sizeof(S);
+    static constexpr int P0 = ZBYTES / (int)sizeof(S);
+};
 
 __device__ __forceinline__ float narrow_to_f(__half v) { return __half2float(v); }
 __device__ __forceinline__ float narrow_to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -65,45 +81,29 @@ template <> __device__ __forceinline__ __nv_bfloat16 f_to_narrow<__nv_bfloat16>(
     return __float2bfloat16_rn(v);
 }
 
+// Population a of lattice lat from its stored value; z: the node's stored zeroth moment (16-bit
+// forms only).
 template <typename S, typename R>
-__device__ __forceinline__ R decode(S v, int lat, int a, const Consts<R>& K)
+__device__ __forceinline__ R decode(S v, R z, int lat, int a, const Consts<R>& K)
 {
     if constexpr (!Narrow<S>::value) {
         return static_cast<R>(v);
     } else {
         const R inv = lat ? K.st_inv[1] : K.st_inv[0];
-        const R ref = lat ? K.st_ref[1] : K.st_ref[0];
-        return narrow_to_f(v) * inv + R(d2q9_w(a)) * ref;
+        return R(narrow_to_f(v)) * inv + R(d2q9_w(a)) * z;
     }
 }
 
+// Stored value of population a of lattice lat that will sit on a node whose zeroth moment (the
+// reference the reader uses) is z.
 template <typename S, typename R>
-__device__ __forceinline__ S encode(R v, int lat, int a, const Consts<R>& K)
+__device__ __forceinline__ S encode(R v, R z, int lat, int a, const Consts<R>& K)
 {
     if constexpr (!Narrow<S>::value) {
         return static_cast<S>(v);
     } else {
         const R scale = lat ? K.st_scale[1] : K.st_scale[0];
-        const R ref = lat ? K.st_ref[1] : K.st_ref[0];
-        return f_to_narrow<S>((v - R(d2q9_w(a)) * ref) * scale);
-    }
-}
-
-// Sum of the nine decoded populations of one lattice from their stored values (the weights
-// sum to one, so the reference enters once).
-template <typename S, typename R>
-__device__ __forceinline__ R decode_sum(const S* q, int stride, int lat, const Consts<R>& K)
-{
-    if constexpr (!Narrow<S>::value) {
-        R s = R(0);
-#pragma unroll
-        for (int a = 0; a < 9; ++a) s += static_cast<R>(q[a * stride]);
-        return s;
-    } else {
-        float s = 0.0f;
-#pragma unroll
-        for (int a = 0; a < 9; ++a) s += narrow_to_f(q[a * stride]);
-        return s * (lat ? K.st_inv[1] : K.st_inv[0]) + (lat ? K.st_ref[1] : K.st_ref[0]);
+        return f_to_narrow<S>(float((v - R(d2q9_w(a)) * z) * scale));
     }
 }
 

@@ -90,7 +90,7 @@ inline int validate_params(const lbm_params* P)
         return LBM_ERR_UNSUPPORTED;
     const double v[] = {P->rho_a, P->rho_b, P->mu_a, P->mu_b, P->sigma0, P->dsigma_dT, P->T0,
                         P->gradT_x, P->gradT_y, P->mobility, P->width, P->gx, P->gy,
-                        P->rho_ref, P->store_scale_g, P->store_scale_f, P->store_ref_g,
+                        P->rho_ref, P->store_scale_g, P->store_scale_f,
                         P->beta, P->psi0, P->gradpsi_x, P->gradpsi_y, P->u0};
     for (double d : v)
         if (!std::isfinite(d)) return LBM_ERR_PARAM;
@@ -137,7 +137,22 @@ inline size_t elem_bytes(int precision)
 
 inline int strips_of(int nx) { return (nx + 31) / 32; }
 
-inline size_t buffer_elems(int nx, int ny) { return (size_t)ny * strips_of(nx) * 18 * 32; }
+// Bytes of one tile (32 columns of one row) of a state: 18 population planes, and in the 16-bit
+// forms two FP32 zeroth-moment planes in front (Tile<S> in the device header).
+inline size_t tile_bytes(int precision)
+{
+    switch (precision) {
+    case LBM_FP64: return (size_t)Tile<double>::BYTES;
+    case LBM_FP32: return (size_t)Tile<float>::BYTES;
+    default: return (size_t)Tile<__half>::BYTES;
+    }
+}
+
+// Elements (of the storage type) of one state buffer.
+inline size_t buffer_elems(int nx, int ny, int precision)
+{
+    return (size_t)ny * strips_of(nx) * tile_bytes(precision) / elem_bytes(precision);
+}
 
 // Per-case constants (definitions in include/cmlbm.h and the device header).
 template <typename R>
@@ -160,11 +175,12 @@ Consts<R> make_consts(const lbm_params& P)
     K.gy = R(P.gy);
     K.rho_ref = R(P.rho_ref);
     K.cs2_drho = R((P.rho_a - P.rho_b) / 3.0);
-    // 16-bit storage: deviations from w_a * ref, scaled (defaults per format)
+    // 16-bit storage: deviations from the rest state of the node, scaled (defaults per format:
+    // FP16 keeps the light phase's deviations, ~1e-6 and up, in its normal range)
     double sg = 1.0, sf = 1.0;
     if (P.precision == LBM_FP32_FP16) {
         sg = P.store_scale_g > 0 ? P.store_scale_g : 16384.0;
-        sf = P.store_scale_f > 0 ? P.store_scale_f : 256.0;
+        sf = P.store_scale_f > 0 ? P.store_scale_f : 4096.0;
     } else if (P.precision == LBM_FP32_BF16) {
         sg = P.store_scale_g > 0 ? P.store_scale_g : 1.0;
         sf = P.store_scale_f > 0 ? P.store_scale_f : 1.0;
@@ -173,8 +189,6 @@ Consts<R> make_consts(const lbm_params& P)
     K.st_scale[1] = R(sf);
     K.st_inv[0] = R(1.0 / sg);
     K.st_inv[1] = R(1.0 / sf);
-    K.st_ref[0] = R(P.store_ref_g);
-    K.st_ref[1] = R(0.5);
     K.langmuir = P.sigma_model == LBM_SIGMA_LANGMUIR ? 1 : 0;
     K.beta = R(P.beta);
     K.psi0 = R(P.psi0);

@@ -53,7 +53,7 @@ template <> struct Stages<double> { static constexpr int value = 3; };
 template <typename S, int NT = 1>
 __host__ __device__ constexpr int warp_smem_bytes()
 {
-    return (Stages<S>::value * (NT * TILE * (int)sizeof(S) + 8) + 127) / 128 * 128;
+    return (Stages<S>::value * (NT * Tile<S>::BYTES + 8) + 127) / 128 * 128;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -128,8 +128,15 @@ __device__ __forceinline__ int map_col(int x, const Geometry& G)
     return x;
 }
 
-// Element offset of column x within a row of tiles.
-__device__ __forceinline__ int col_off(int x) { return (x >> 5) * TILE + (x & 31); }
+// Element offset of column x (population plane 0) within a row of tiles.
+template <typename S = float>
+__device__ __forceinline__ int col_off(int x)
+{
+    return (x >> 5) * Tile<S>::ELEMS + Tile<S>::P0 + (x & 31);
+}
+// 16-bit forms: element offset of column x's value in the Z_g plane (Z_f follows 64 elements on).
+template <typename S>
+__device__ __forceinline__ int z_off(int x) { return (x >> 5) * Tile<S>::ELEMS + 2 * (x & 31); }
 
 // One (phi, p*) row of the window for this lane: own column, west and east neighbours.
 template <typename R>
@@ -143,8 +150,25 @@ template <typename R, typename S, bool PHI_ONLY = false>
 __device__ __forceinline__ void window_row(const S* tile, int lane, int wlast, R hl, R hr,
                                            const Consts<R>& K, Row3<R>& row)
 {
-    const R ps = PHI_ONLY ? R(0) : decode_sum<S, R>(tile + lane, 32, 0, K);
-    const R ph = decode_sum<S, R>(tile + 9 * 32 + lane, 32, 1, K);
+    R ps = R(0), ph = R(0);
+    const S* q = tile + Tile<S>::P0 + lane;
+    if constexpr (Narrow<S>::value) {       // Z + (sum of the deviations) / s
+        const float* z = reinterpret_cast<const float*>(tile);
+        float dg = 0.0f, df = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            dg += narrow_to_f(q[a * 32]);
+            df += narrow_to_f(q[(9 + a) * 32]);
+        }
+        ps = fmad(R(dg), K.st_inv[0], R(z[lane]));
+        ph = fmad(R(df), K.st_inv[1], R(z[32 + lane]));
+    } else {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            if (!PHI_ONLY) ps += R(q[a * 32]);
+            ph += R(q[(9 + a) * 32]);
+        }
+    }
 #pragma unroll
     for (int off = 8; off >= 1; off >>= 1) {
         hl += __shfl_xor_sync(FULL, hl, off);
@@ -178,11 +202,28 @@ template <typename S, typename R, bool F_ONLY = false>
 __device__ __forceinline__ void ld_pops_t(const S* tile, int lane, const Consts<R>& K, R g[9],
                                           R f[9])
 {
+    R zg = R(0), zf = R(0);
+    if constexpr (Narrow<S>::value) {
+        const float* z = reinterpret_cast<const float*>(tile);
+        zg = R(z[lane]);
+        zf = R(z[32 + lane]);
+    }
+    const S* q = tile + Tile<S>::P0 + lane;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-        if (!F_ONLY) g[a] = decode<S, R>(tile[a * 32 + lane], 0, a, K);
-        f[a] = decode<S, R>(tile[(9 + a) * 32 + lane], 1, a, K);
+        if (!F_ONLY) g[a] = decode<S, R>(q[a * 32], zg, 0, a, K);
+        f[a] = decode<S, R>(q[(9 + a) * 32], zf, 1, a, K);
     }
+}
+
+// Value of a window at offset (dx, dy) in {-1, 0, 1}^2.
+template <typename R>
+__device__ __forceinline__ R win_at(const Win<R>& w, int dx, int dy)
+{
+    const R s = dx < 0 ? w.sw : (dx > 0 ? w.se : w.s);
+    const R c = dx < 0 ? w.w : (dx > 0 ? w.e : w.c);
+    const R n = dx < 0 ? w.nw : (dx > 0 ? w.ne : w.n);
+    return dy < 0 ? s : (dy > 0 ? n : c);
 }
 
 // Push the 18 post-collision populations of one node to x + e_a in the row buffers rS, rC, rN
@@ -201,8 +242,8 @@ __device__ __forceinline__ void push_node(const R g[9], const R f[9], S* rS, S* 
     if (fast) {
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            if (!F_ONLY) p[a][a * 32] = encode<S, R>(g[a], 0, a, K);
-            p[a][(9 + a) * 32] = encode<S, R>(f[a], 1, a, K);
+            if (!F_ONLY) p[a][a * 32] = static_cast<S>(g[a]);
+            p[a][(9 + a) * 32] = static_cast<S>(f[a]);
         }
         return;
     }
@@ -228,8 +269,71 @@ __device__ __forceinline__ void push_node(const R g[9], const R f[9], S* rS, S* 
             S* row = cy ? rC : (ey > 0 ? rN : (ey < 0 ? rS : rC));
             q = row + (cx ? cc : (ex > 0 ? ce : (ex < 0 ? cw : cc)));
         }
-        if (!F_ONLY) q[plane * 32] = encode<S, R>(g[a], 0, a, K);
-        q[(9 + plane) * 32] = encode<S, R>(f[a], 1, a, K);
+        if (!F_ONLY) q[plane * 32] = static_cast<S>(g[a]);
+        q[(9 + plane) * 32] = static_cast<S>(f[a]);
+    }
+}
+
+// As push_node for the 16-bit forms: every population is stored as its deviation from the rest
+// state of the node it lands on, whose zeroth moments are the window values ps (p*) and ph (phi)
+// at the landing offset; the node's own zeroth moments go to its Z planes (element offset zc).
+template <typename S, typename R>
+__device__ __forceinline__ void push_node_z(const R g[9], const R f[9], const Win<R>& ps,
+                                            const Win<R>& ph, S* rS, S* rC, S* rN, int cw,
+                                            int cc, int ce, int zc, bool bxw, bool bxe,
+                                            bool bys, bool byn, int slip, bool fast,
+                                            const Consts<R>& K)
+{
+    float* zp = reinterpret_cast<float*>(rC + zc);
+    zp[0] = float(ps.c);
+    zp[32] = float(ph.c);
+    S* pc = rC + cc;
+    S* p[9] = {pc, rC + ce, rN + cc, rC + cw, rS + cc, rN + ce, rN + cw, rS + cw, rS + ce};
+    constexpr int EXc[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    constexpr int EYc[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    if (fast) {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            p[a][a * 32] = encode<S, R>(g[a], win_at(ps, EXc[a], EYc[a]), 0, a, K);
+            p[a][(9 + a) * 32] = encode<S, R>(f[a], win_at(ph, EXc[a], EYc[a]), 1, a, K);
+        }
+        return;
+    }
+    constexpr int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    constexpr int MX[9] = {0, 3, 2, 1, 4, 6, 5, 8, 7};
+    constexpr int MY[9] = {0, 1, 4, 3, 2, 8, 7, 6, 5};
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const int ex = EXc[a], ey = EYc[a];
+        const bool cx = (ex < 0 && bxw) || (ex > 0 && bxe);
+        const bool cy = (ey < 0 && bys) || (ey > 0 && byn);
+        const bool sx = ((slip >> (ex < 0 ? 0 : 1)) & 1) != 0;
+        const bool sy = ((slip >> (ey < 0 ? 2 : 3)) & 1) != 0;
+        // landing node: x + e_a, or this node (bounce-back, or both components reflected), or
+        // the tangential neighbour (one component reflected); its zeroth moments are window
+        // values at constant offsets, chosen by selects
+        const bool bounce = (cx && !sx) || (cy && !sy) || (cx && cy);
+        int plane = a;
+        S* q = p[a];
+        R zg = win_at(ps, ex, ey), zf = win_at(ph, ex, ey);
+        if (bounce) {
+            plane = OPP[a];
+            q = pc;
+            zg = ps.c;
+            zf = ph.c;
+        } else if (cx) {
+            plane = MX[a];
+            q = (ey > 0 ? rN : (ey < 0 ? rS : rC)) + cc;
+            zg = win_at(ps, 0, ey);
+            zf = win_at(ph, 0, ey);
+        } else if (cy) {
+            plane = MY[a];
+            q = rC + (ex > 0 ? ce : (ex < 0 ? cw : cc));
+            zg = win_at(ps, ex, 0);
+            zf = win_at(ph, ex, 0);
+        }
+        q[plane * 32] = encode<S, R>(g[a], zg, 0, a, K);
+        q[(9 + plane) * 32] = encode<S, R>(f[a], zf, 1, a, K);
     }
 }
 
@@ -244,15 +348,17 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     constexpr bool SRT = (V & kVarSRT) != 0;
     constexpr bool SHEAR = (V & kVarShear) != 0;
     constexpr bool LANGMUIR = (V & kVarLangmuir) != 0;
+    constexpr bool NARROW = Narrow<S>::value;
+    constexpr int TE = Tile<S>::ELEMS;               // elements per tile
     // the interface lattice alone copies only the f half of every tile (planes 9..17)
-    constexpr int COPY_OFF = SHEAR ? 9 * 32 : 0;
-    constexpr uint32_t COPY_BYTES = (SHEAR ? 9 * 32 : TILE) * sizeof(S);
+    constexpr int COPY_OFF = SHEAR ? Tile<S>::P0 + 9 * 32 : 0;
+    constexpr uint32_t COPY_BYTES = SHEAR ? 9 * 32 * sizeof(S) : Tile<S>::BYTES;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
 
     S* tiles = reinterpret_cast<S*>(smem_raw + wib * warp_smem_bytes<S>());
-    const uint32_t bar0 = smem_u32(tiles + NS * TILE);
+    const uint32_t bar0 = smem_u32(tiles + NS * TE);
     if (lane == 0)
         for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8 * s, 1);
     mbar_init_fence();
@@ -264,7 +370,7 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     const bool active = lane < w;
     const int x = active ? x0 + lane : x0 + wlast;   // idle lanes shadow the last column
     const int xl = map_col(x0 - 1, G), xr = map_col(x0 + w, G);
-    const int row_elems = G.nstrips * TILE;          // < 2^31 for nx <= 65536
+    const int row_elems = G.nstrips * TE;            // < 2^31 for nx <= 65536
     auto row_ptr = [&](const S* base, int row) { return base + (long long)row * row_elems; };
 
     const int ys = seg * seg_h;
@@ -274,19 +380,30 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     // row visited at step k (k = -1 .. nrows): behind/current/ahead rows of the march
     auto row_of = [&](int k) { return map_row(up ? ys + k : ye - 1 - k, G); };
 
-    // halo: lanes 0..8 load g-bar plane q, lanes 16..24 f plane q, at columns xl and xr
-    const int hq = lane & 15;
+    // halo: lanes 0..8 load g-bar plane q, lanes 16..24 f plane q, at columns xl and xr; in
+    // the 16-bit forms lanes 9 and 25 add the columns' Z_g and Z_f to the scaled deviations
+    const int hq = lane & 15, hlat = lane >> 4;
     const bool hlane = hq < 9 && (!SHEAR || lane >= 16);
-    const int hplane = (lane >> 4) * 9 + hq;
-    const int hoffl = col_off(xl) + hplane * 32;
-    const int hoffr = col_off(xr) + hplane * 32;
+    const bool zlane = NARROW && hq == 9;
+    const int hplane = hlat * 9 + hq;
+    const int hoffl = zlane ? z_off<S>(xl) + 64 * hlat : col_off<S>(xl) + hplane * 32;
+    const int hoffr = zlane ? z_off<S>(xr) + 64 * hlat : col_off<S>(xr) + hplane * 32;
+    const R hinv = NARROW ? (hlat ? K.st_inv[1] : K.st_inv[0]) : R(1);
     auto halo_load = [&](int k, R& hl, R& hr) {
         hl = R(0);
         hr = R(0);
+        const S* rb = row_ptr(src, row_of(k));
         if (hlane) {
-            const S* rb = row_ptr(src, row_of(k));
-            hl = decode<S, R>(__ldg(rb + hoffl), lane >> 4, hq, K);
-            hr = decode<S, R>(__ldg(rb + hoffr), lane >> 4, hq, K);
+            if constexpr (NARROW) {
+                hl = R(narrow_to_f(__ldg(rb + hoffl))) * hinv;
+                hr = R(narrow_to_f(__ldg(rb + hoffr))) * hinv;
+            } else {
+                hl = R(__ldg(rb + hoffl));
+                hr = R(__ldg(rb + hoffr));
+            }
+        } else if (zlane) {
+            hl = R(__ldg(reinterpret_cast<const float*>(rb + hoffl)));
+            hr = R(__ldg(reinterpret_cast<const float*>(rb + hoffr)));
         }
     };
 
@@ -300,8 +417,8 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
             fence_proxy_async();
             const uint32_t bar = bar0 + 8 * st;
             mbar_expect_tx(bar, COPY_BYTES);
-            bulk_g2s(smem_u32(tiles + st * TILE + COPY_OFF),
-                     row_ptr(src, row_of(k)) + strip * TILE + COPY_OFF, COPY_BYTES, bar);
+            bulk_g2s(smem_u32(tiles + st * TE + COPY_OFF),
+                     row_ptr(src, row_of(k)) + strip * TE + COPY_OFF, COPY_BYTES, bar);
         }
         issued = k;
     };
@@ -324,7 +441,7 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     issue(NS - 1, 0);
     halo_load(0, hl, hr);
     if (!wait_k(0, 1)) { fail(0); return; }
-    window_row<R, S, SHEAR>(tiles + TILE, lane, wlast, hl, hr, K, rc);
+    window_row<R, S, SHEAR>(tiles + TE, lane, wlast, hl, hr, K, rc);
     halo_load(1, hl2, hr2);
 
     // neighbour columns of this lane (periodic wrap; walls handled by bounce flags)
@@ -332,7 +449,8 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     const bool bxw = xm < 0 && G.wall_x, bxe = xp >= G.nx && G.wall_x;
     if (xm < 0) xm += G.nx;
     if (xp >= G.nx) xp -= G.nx;
-    const int cw = col_off(xm), cc = col_off(x), ce = col_off(xp);
+    const int cw = col_off<S>(xm), cc = col_off<S>(x), ce = col_off<S>(xp);
+    const int zc = NARROW ? z_off<S>(x) : 0;
     const bool xwall_warp = __any_sync(FULL, bxw || bxe);
     const R xf = R(x);
     bool ok = true;
@@ -345,7 +463,7 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     auto body = [&](int i, int st) {
         const int st1 = st + 1 == NS ? 0 : st + 1;       // stage of row i + 1
         if (!wait_k(i + 1, st1)) { fail(i + 1); ok = false; return; }
-        window_row<R, S, SHEAR>(tiles + st1 * TILE, lane, wlast, hl2, hr2, K, rn);
+        window_row<R, S, SHEAR>(tiles + st1 * TE, lane, wlast, hl2, hr2, K, rn);
         if (i + 2 <= nrows) halo_load(i + 2, hl2, hr2);
 
         const int y = up ? ys + i : ye - 1 - i;
@@ -353,7 +471,7 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
         if (up) make_window(rb, rc, rn, ph, ps);
         else make_window(rn, rc, rb, ph, ps);
         R g[9], f[9];
-        ld_pops_t<S, R, SHEAR>(tiles + st * TILE, lane, K, g, f);
+        ld_pops_t<S, R, SHEAR>(tiles + st * TE, lane, K, g, f);
         Macro<R> m;
         if constexpr (SHEAR) {
             R syr, cyr;
@@ -378,9 +496,15 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
         S* rS = const_cast<S*>(row_ptr(dst, ym));
         S* rC = const_cast<S*>(row_ptr(dst, y));
         S* rN = const_cast<S*>(row_ptr(dst, yp));
-        if (active)
-            push_node<S, R, SHEAR>(g, f, rS, rC, rN, cw, cc, ce, bxw, bxe, bys, byn, G.slip,
-                                   !(bys || byn) && !xwall_warp, K);
+        if (active) {
+            const bool fast = !(bys || byn) && !xwall_warp;
+            if constexpr (NARROW)
+                push_node_z<S, R>(g, f, ps, ph, rS, rC, rN, cw, cc, ce, zc, bxw, bxe, bys, byn,
+                                  G.slip, fast, K);
+            else
+                push_node<S, R, SHEAR>(g, f, rS, rC, rN, cw, cc, ce, bxw, bxe, bys, byn,
+                                       G.slip, fast, K);
+        }
         issue(i + NS, st);      // the tile of row i is consumed: refill its stage
         rb = rc;
         rc = rn;
@@ -675,9 +799,57 @@ batch_step_kernel(S* __restrict__ base, const BatchCase<R>* __restrict__ cases,
 // ---------------------------------------------------------------------------------------------
 // Initialisation, field extraction, packing (one thread per node; not on the hot path)
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ long long elem_index(const Geometry& G, int a, int x, int y)
+// Element index of population plane p (0..17) of node (x, y) in a state of storage type S, and
+// (16-bit forms) of the node's Z plane lat (an FP32 value spanning two elements).
+template <typename S>
+__device__ __forceinline__ long long elem_index(const Geometry& G, int p, int x, int y)
 {
-    return ((long long)y * G.nstrips + (x >> 5)) * TILE + a * 32 + (x & 31);
+    return ((long long)y * G.nstrips + (x >> 5)) * Tile<S>::ELEMS + Tile<S>::P0 + p * 32 +
+           (x & 31);
+}
+template <typename S>
+__device__ __forceinline__ long long z_index(const Geometry& G, int lat, int x, int y)
+{
+    return ((long long)y * G.nstrips + (x >> 5)) * Tile<S>::ELEMS + 64 * lat + 2 * (x & 31);
+}
+
+// The 18 populations of node (x, y) (decoded).
+template <typename R, typename S>
+__device__ __forceinline__ void load_node(const S* state, const Geometry& G, const Consts<R>& K,
+                                          int x, int y, R g[9], R f[9])
+{
+    R zg = R(0), zf = R(0);
+    if constexpr (Narrow<S>::value) {
+        zg = R(*reinterpret_cast<const float*>(state + z_index<S>(G, 0, x, y)));
+        zf = R(*reinterpret_cast<const float*>(state + z_index<S>(G, 1, x, y)));
+    }
+    for (int a = 0; a < 9; ++a) {
+        g[a] = decode<S, R>(state[elem_index<S>(G, a, x, y)], zg, 0, a, K);
+        f[a] = decode<S, R>(state[elem_index<S>(G, 9 + a, x, y)], zf, 1, a, K);
+    }
+}
+
+// Store the 18 populations of node (x, y); the 16-bit forms take the node's own zeroth moments
+// as their references.
+template <typename R, typename S>
+__device__ __forceinline__ void store_node(S* state, const Geometry& G, const Consts<R>& K,
+                                           int x, int y, const R g[9], const R f[9])
+{
+    R zg = R(0), zf = R(0);
+    if constexpr (Narrow<S>::value) {
+        for (int a = 0; a < 9; ++a) {
+            zg += g[a];
+            zf += f[a];
+        }
+        *reinterpret_cast<float*>(state + z_index<S>(G, 0, x, y)) = float(zg);
+        *reinterpret_cast<float*>(state + z_index<S>(G, 1, x, y)) = float(zf);
+        zg = R(float(zg));   // the reader decodes against the stored FP32 value
+        zf = R(float(zf));
+    }
+    for (int a = 0; a < 9; ++a) {
+        state[elem_index<S>(G, a, x, y)] = encode<S, R>(g[a], zg, 0, a, K);
+        state[elem_index<S>(G, 9 + a, x, y)] = encode<S, R>(f[a], zf, 1, a, K);
+    }
 }
 
 template <typename R, typename S>
@@ -692,11 +864,7 @@ __global__ void init_kernel(const double* __restrict__ phi, const double* __rest
     const R rho = K.rho_b + ph * K.drho;
     R g[9], f[9];
     equilibria<R>(ph, R(p[n]), R(ux[n]), R(uy[n]), rho, g, f);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        state[elem_index(G, a, x, y)] = encode<S, R>(g[a], 0, a, K);
-        state[elem_index(G, 9 + a, x, y)] = encode<S, R>(f[a], 1, a, K);
-    }
+    store_node<R, S>(state, G, K, x, y, g, f);
 }
 
 // Macroscopic fields of a state: phi, corrected p, u, rho (double outputs, [ny][nx]).  One
@@ -716,10 +884,7 @@ __global__ void fields_kernel(const S* __restrict__ state, Geometry G, Consts<R>
         for (int i = -1; i <= 1; ++i) {
             const int xx = map_col(x + i, G);
             R gq[9], fq[9];
-            for (int a = 0; a < 9; ++a) {
-                gq[a] = decode<S, R>(state[elem_index(G, a, xx, yy)], 0, a, K);
-                fq[a] = decode<S, R>(state[elem_index(G, 9 + a, xx, yy)], 1, a, K);
-            }
+            load_node<R, S>(state, G, K, xx, yy, gq, fq);
             vph[j + 1][i + 1] =
                 ((fq[0] + fq[1]) + (fq[2] + fq[3])) + ((fq[4] + fq[5]) + (fq[6] + fq[7])) + fq[8];
             vps[j + 1][i + 1] =
@@ -730,8 +895,8 @@ __global__ void fields_kernel(const S* __restrict__ state, Geometry G, Consts<R>
                  vph[2][0], vph[2][1], vph[2][2]};
     Win<R> ps = {vps[0][0], vps[0][1], vps[0][2], vps[1][0], vps[1][1], vps[1][2],
                  vps[2][0], vps[2][1], vps[2][2]};
-    R gq[9];
-    for (int a = 0; a < 9; ++a) gq[a] = decode<S, R>(state[elem_index(G, a, x, y)], 0, a, K);
+    R gq[9], fq[9];
+    load_node<R, S>(state, G, K, x, y, gq, fq);
     const R jgx = (gq[1] - gq[3]) + (gq[5] - gq[6]) - (gq[7] - gq[8]);
     const R jgy = (gq[2] - gq[4]) + (gq[5] + gq[6]) - (gq[7] + gq[8]);
     Macro<R> m;
@@ -751,18 +916,21 @@ __global__ void fields_kernel(const S* __restrict__ state, Geometry G, Consts<R>
     if (rho_o) rho_o[n] = double(m.rho);
 }
 
-// Copy between the tiled device state and a dense [18][ny][nx] double array (decoded values).
+// Copy between the tiled device state and a dense [18][ny][nx] double array (decoded values);
+// one thread per node.
 template <typename R, typename S>
 __global__ void pack_kernel(const S* __restrict__ state, double* __restrict__ out, Geometry G,
                             Consts<R> K)
 {
     const long long N = (long long)G.nx * G.ny;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 18 * N) return;
-    const int a = (int)(t / N);
-    const long long n = t % N;
-    out[t] = double(decode<S, R>(state[elem_index(G, a, (int)(n % G.nx), (int)(n / G.nx))],
-                                 a >= 9, a % 9, K));
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    R g[9], f[9];
+    load_node<R, S>(state, G, K, (int)(n % G.nx), (int)(n / G.nx), g, f);
+    for (int a = 0; a < 9; ++a) {
+        out[a * N + n] = double(g[a]);
+        out[(9 + a) * N + n] = double(f[a]);
+    }
 }
 
 template <typename R, typename S>
@@ -770,12 +938,14 @@ __global__ void unpack_kernel(const double* __restrict__ in, S* __restrict__ sta
                               Consts<R> K)
 {
     const long long N = (long long)G.nx * G.ny;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 18 * N) return;
-    const int a = (int)(t / N);
-    const long long n = t % N;
-    state[elem_index(G, a, (int)(n % G.nx), (int)(n / G.nx))] =
-        encode<S, R>(R(in[t]), a >= 9, a % 9, K);
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    R g[9], f[9];
+    for (int a = 0; a < 9; ++a) {
+        g[a] = R(in[a * N + n]);
+        f[a] = R(in[(9 + a) * N + n]);
+    }
+    store_node<R, S>(state, G, K, (int)(n % G.nx), (int)(n / G.nx), g, f);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -957,7 +1127,7 @@ template <typename R, typename S>
 cudaError_t launch_pack(const void* state, double* out, const Geometry& G, const Consts<R>& K,
                         cudaStream_t st)
 {
-    const long long T = 18LL * G.nx * G.ny;
+    const long long T = (long long)G.nx * G.ny;
     pack_kernel<R, S><<<(unsigned)((T + 255) / 256), 256, 0, st>>>(
         static_cast<const S*>(state), out, G, K);
     return cudaGetLastError();
@@ -967,7 +1137,7 @@ template <typename R, typename S>
 cudaError_t launch_unpack(const double* in, void* state, const Geometry& G, const Consts<R>& K,
                           cudaStream_t st)
 {
-    const long long T = 18LL * G.nx * G.ny;
+    const long long T = (long long)G.nx * G.ny;
     unpack_kernel<R, S><<<(unsigned)((T + 255) / 256), 256, 0, st>>>(in, static_cast<S*>(state),
                                                                      G, K);
     return cudaGetLastError();

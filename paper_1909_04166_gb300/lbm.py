@@ -44,7 +44,8 @@ LBM_FLOW_SHEAR = 1
 EXPORTS = [
     "lbm_state_bytes", "lbm_create", "lbm_create_with_buffer", "lbm_init_fields",
     "lbm_init_fields_device", "lbm_step", "lbm_get_fields", "lbm_get_populations",
-    "lbm_set_populations", "lbm_state_device", "lbm_diagnostics", "lbm_set_launch",
+    "lbm_set_populations", "lbm_save_state", "lbm_load_state", "lbm_state_device",
+    "lbm_diagnostics", "lbm_set_launch",
     "lbm_get_launch", "lbm_steps_done", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error",
     "lbm_check", "lbm_set_graphs", "lbm_diagnostics_noalloc",
     "lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_get_fields",
@@ -72,7 +73,6 @@ class lbm_params(ctypes.Structure):
         ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
         ("store_scale_g", ctypes.c_double), ("store_scale_f", ctypes.c_double),
-        ("store_ref_g", ctypes.c_double),
         ("bc_x_hi", ctypes.c_int32), ("bc_y_hi", ctypes.c_int32),
         ("collision", ctypes.c_int32), ("sigma_model", ctypes.c_int32),
         ("beta", ctypes.c_double), ("psi0", ctypes.c_double),
@@ -117,6 +117,8 @@ def lib(build_if_missing: bool = True):
     L.lbm_get_fields.argtypes = [vp, dp, dp, dp, dp, dp]
     L.lbm_get_populations.argtypes = [vp, dp, dp]
     L.lbm_set_populations.argtypes = [vp, dp, dp]
+    L.lbm_save_state.argtypes = [vp, vp, ctypes.c_size_t, P(i64)]
+    L.lbm_load_state.argtypes = [vp, vp, ctypes.c_size_t, i64]
     L.lbm_state_device.argtypes = [vp, P(vp), P(i32), P(i64)]
     L.lbm_diagnostics.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_double, P(lbm_diag)]
@@ -179,7 +181,6 @@ def make_params(case: dict, precision="fp32", device=0, stream=0) -> lbm_params:
         float(case.get("gx", 0.0)), float(case.get("gy", 0.0)), float(case.get("rho_ref", 0.0)),
         prec, int(device), ctypes.c_void_p(int(stream)),
         float(case.get("store_scale_g", 0.0)), float(case.get("store_scale_f", 0.0)),
-        float(case.get("store_ref_g", 0.0)),
         0 if hi_x is None else int(hi_x), 0 if hi_y is None else int(hi_y),
         int(case.get("collision", 0)), int(case.get("sigma_model", 0)),
         float(case.get("beta", 0.0)), float(case.get("psi0", 0.0)),
@@ -239,6 +240,21 @@ def lbm_get_populations(ctx, g, f) -> None:
 
 def lbm_set_populations(ctx, g, f) -> None:
     _check(lib().lbm_set_populations(ctx, _dptr(g), _dptr(f)), "lbm_set_populations")
+
+
+def lbm_save_state(ctx, nbytes: int):
+    """Exact checkpoint: (bytes of the current state buffer, step counter)."""
+    buf = np.empty(int(nbytes), dtype=np.uint8)
+    steps = ctypes.c_int64()
+    _check(lib().lbm_save_state(ctx, buf.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(buf.size),
+                                ctypes.byref(steps)), "lbm_save_state")
+    return buf, int(steps.value)
+
+
+def lbm_load_state(ctx, buf: np.ndarray, steps: int) -> None:
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(lib().lbm_load_state(ctx, buf.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(buf.size),
+                                ctypes.c_int64(int(steps))), "lbm_load_state")
 
 
 def lbm_state_device(ctx):
@@ -456,6 +472,14 @@ class Simulation:
     def set_populations(self, g, f):
         lbm_set_populations(self.ctx, np.ascontiguousarray(g, np.float64),
                             np.ascontiguousarray(f, np.float64))
+        return self
+
+    def save_state(self):
+        """Exact checkpoint (raw state bytes, step counter)."""
+        return lbm_save_state(self.ctx, lbm_state_bytes(self.params) // 2)
+
+    def load_state(self, checkpoint):
+        lbm_load_state(self.ctx, *checkpoint)
         return self
 
     def diagnostics(self, xc=0.0, yc=0.0, r_in=-1.0, r_out=0.0) -> dict:

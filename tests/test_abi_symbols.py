@@ -39,6 +39,9 @@ def test_host_only_calls_work_without_a_device():
     assert lbm.lbm_state_bytes(p) == 2 * 2 * 40 * 18 * 32 * 4
     p64 = lbm.make_params(W.laplace(n=40), "fp64")
     assert lbm.lbm_state_bytes(p64) == 2 * lbm.lbm_state_bytes(p)
+    # 16-bit: two FP32 zeroth-moment planes and 18 planes of 16-bit deviations per tile
+    p16 = lbm.make_params(W.laplace(n=40), "fp16")
+    assert lbm.lbm_state_bytes(p16) == 2 * 2 * 40 * (2 * 32 * 4 + 18 * 32 * 2)
     bad = lbm.make_params(W.laplace(n=40), "fp32")
     bad.width = 0.0
     with pytest.raises(lbm.LbmError) as e:

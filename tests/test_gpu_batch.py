@@ -26,7 +26,7 @@ def mixed_cases():
     ]
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp64", 1e-14)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp64", 1e-14), ("fp16", 1e-4)])
 def test_batch_cases_match_their_own_contexts(prec, tol):
     cases = mixed_cases()
     with lbm.Batch(cases, precision=prec) as b:

@@ -1,12 +1,14 @@
-"""16-bit storage modes (LBM_FP32_FP16, LBM_FP32_BF16): populations stored as scaled deviations
-from w_a * ref in half / bfloat16, collided in float.
+"""16-bit storage modes (LBM_FP32_FP16, LBM_FP32_BF16): per tile, two FP32 planes with each
+node's zeroth moments of the previous time level and 18 planes of scaled 16-bit deviations of
+the populations from the rest state w_a Z of the node they sit on; collisions in float.
 
-What is pinned: the codec round trip is exact (a state read out and written back is stored
-bit for bit as before); one step from a representable state differs from the FP64 step of the
-same state only by the storage rounding of the result; over 1000 steps the fields stay within
-the stated bounds of the FP64 oracle (bounds measured on this path and recorded in the
-design notes; 16-bit storage is far less accurate than FP32 storage for slow flows, because
-the stored values carry the pressure level while the momentum is much smaller)."""
+What is pinned: the raw checkpoint (lbm_save_state / lbm_load_state) is exact in every mode; a
+population-level write-back re-derives the zeroth-moment planes and so changes the state by one
+16-bit rounding of the deviations at most; one step from a state differs from the FP64 step of
+the same populations only by that storage rounding; over 1000 steps the fields stay within the
+stated bounds of the FP64 oracle (bounds measured on this path, about three times the measured
+error, and recorded in the design notes); and the density-ratio-1000 impact stays finite and
+close to the FP64 mode in both formats."""
 import numpy as np
 import pytest
 
@@ -22,24 +24,32 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("prec", FORMATS)
-def test_codec_round_trip_is_exact(prec):
+@pytest.mark.parametrize("prec", ["fp64", "fp32"] + FORMATS)
+def test_raw_checkpoint_is_exact(prec):
     case = W.random_drop(70, 45, seed=3, wall_y=True, rho_ratio=10.0)
     with lbm.Simulation(case, precision=prec) as s:
         s.init_case().step(30)
-        g, f = s.populations()
-        s.set_populations(g, f)
-        g2, f2 = s.populations()
-        assert np.array_equal(g, g2) and np.array_equal(f, f2)
-        s.step(7)
-        g3, f3 = s.populations()
+        ck = s.save_state()
+        assert ck[1] == 30
+        g1, f1 = s.step(7).populations()
     with lbm.Simulation(case, precision=prec) as t:
-        t.set_populations(g, f).step(7)
-        g4, f4 = t.populations()
-    assert np.array_equal(g3, g4) and np.array_equal(f3, f4)
+        g2, f2 = t.load_state(ck).step(7).populations()
+        assert lbm.lbm_steps_done(t.ctx) == 37
+    assert np.array_equal(g1, g2) and np.array_equal(f1, f2)
 
 
-@pytest.mark.parametrize("prec,tol_g,tol_f", [("fp16", 5e-4, 2e-4), ("bf16", 4e-3, 1e-3)])
+@pytest.mark.parametrize("prec,tol_g,tol_f", [("fp16", 2e-4, 2e-5), ("bf16", 2e-3, 5e-5)])
+def test_population_write_back_is_one_rounding(prec, tol_g, tol_f):
+    case = W.marangoni()
+    with lbm.Simulation(case, precision=prec) as s:
+        s.init_case().step(50)
+        g, f = s.populations()
+        g2, f2 = s.set_populations(g, f).populations()
+    assert rel_l2(g2, g) <= tol_g
+    assert rel_l2(f2, f) <= tol_f
+
+
+@pytest.mark.parametrize("prec,tol_g,tol_f", [("fp16", 2e-4, 2e-5), ("bf16", 2e-3, 1e-4)])
 def test_one_step_differs_by_storage_rounding_only(prec, tol_g, tol_f):
     case = W.marangoni()
     with lbm.Simulation(case, precision=prec) as s:
@@ -53,8 +63,8 @@ def test_one_step_differs_by_storage_rounding_only(prec, tol_g, tol_f):
 
 
 BOUNDS = {  # 1000 steps of the Marangoni drop (density ratio 10) against the FP64 oracle
-    "fp16": {"phi": 5e-3, "p": 2.5e-2, "ux": 0.25, "uy": 0.25, "mass": 5e-5},
-    "bf16": {"phi": 1.5e-2, "p": 2.5e-2, "ux": 0.4, "uy": 0.4, "mass": 2e-4},
+    "fp16": {"phi": 2e-4, "p": 1e-3, "ux": 3e-2, "uy": 3e-2, "mass": 6e-5},
+    "bf16": {"phi": 1e-3, "p": 1e-2, "ux": 0.3, "uy": 0.3, "mass": 4e-4},
 }
 
 
@@ -75,11 +85,18 @@ def test_1000_steps_within_stated_bounds(prec):
     assert abs(m1 - m0) <= BOUNDS[prec]["mass"] * m0
 
 
-def test_fp16_impact_at_density_ratio_1000():
+IMPACT_BOUNDS = {  # 1000 steps of the density-ratio-1000 impact against the FP64 mode
+    "fp16": (("phi", 5e-3), ("p", 6e-2), ("ux", 0.1), ("uy", 0.1)),
+    "bf16": (("phi", 2.5e-2), ("p", 0.25), ("ux", 0.15), ("uy", 0.15)),
+}
+
+
+@pytest.mark.parametrize("prec", FORMATS)
+def test_impact_at_density_ratio_1000(prec):
     case = W.impact()
-    with lbm.Simulation(case, precision="fp64") as a, lbm.Simulation(case, precision="fp16") as b:
+    with lbm.Simulation(case, precision="fp64") as a, lbm.Simulation(case, precision=prec) as b:
         ref = a.init_case().step(1000).fields()
         got = b.init_case().step(1000).fields()
-    for k, bound in (("phi", 1e-2), ("p", 3e-2), ("ux", 0.25), ("uy", 0.25)):
+    for k, bound in IMPACT_BOUNDS[prec]:
         assert np.isfinite(got[k]).all()
         assert rel_l2(got[k], ref[k]) <= bound, k
