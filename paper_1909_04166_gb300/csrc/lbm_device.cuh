@@ -71,6 +71,9 @@ struct Tile {
 
 __device__ __forceinline__ float narrow_to_f(__half v) { return __half2float(v); }
 __device__ __forceinline__ float narrow_to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float narrow_to_f_or_self(__half v) { return __half2float(v); }
+__device__ __forceinline__ float narrow_to_f_or_self(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float narrow_to_f_or_self(float v) { return v; }
 template <typename S> __device__ __forceinline__ S f_to_narrow(float v);
 template <> __device__ __forceinline__ __half f_to_narrow<__half>(float v)
 {

@@ -531,18 +531,28 @@ struct Row3P {
 };
 
 // Sums of a lane's two columns and their east / west neighbours; hl / hr: this lane's halo
-// loads (one plane of the left / right halo column, or 0); lastA / lastB: this lane's node A / B
-// is the last active column of the warp (its east neighbour is the right halo column).
-__device__ __forceinline__ void window_row2(const float* ta, const float* tb, int lane,
-                                            bool lastA, bool lastB, float hl, float hr,
-                                            Row3P& row)
+// loads (summed over the half warp into the halo columns' zeroth moments); lastA / lastB: this
+// lane's node A / B is the last active column of the warp (its east neighbour is the right halo
+// column).  ta / tb: the two tiles of the row in shared memory.
+template <typename S>
+__device__ __forceinline__ void window_row2(const S* ta, const S* tb, int lane, bool lastA,
+                                            bool lastB, float hl, float hr,
+                                            const Consts<float>& K, Row3P& row)
 {
-    F2 ps(ta[lane], tb[lane]);
-    F2 ph(ta[9 * 32 + lane], tb[9 * 32 + lane]);
+    constexpr int P0 = Tile<S>::P0;
+    auto val = [&](const S* t, int p) { return float(narrow_to_f_or_self(t[P0 + p * 32 + lane])); };
+    F2 ps(val(ta, 0), val(tb, 0));
+    F2 ph(val(ta, 9), val(tb, 9));
 #pragma unroll
     for (int a = 1; a < 9; ++a) {
-        ps += F2(ta[a * 32 + lane], tb[a * 32 + lane]);
-        ph += F2(ta[(9 + a) * 32 + lane], tb[(9 + a) * 32 + lane]);
+        ps += F2(val(ta, a), val(tb, a));
+        ph += F2(val(ta, 9 + a), val(tb, 9 + a));
+    }
+    if constexpr (Narrow<S>::value) {   // Z + (sum of the deviations) / s
+        const float* za = reinterpret_cast<const float*>(ta);
+        const float* zb = reinterpret_cast<const float*>(tb);
+        ps = fmad(ps, F2(K.st_inv[0]), F2(za[lane], zb[lane]));
+        ph = fmad(ph, F2(K.st_inv[1]), F2(za[32 + lane], zb[32 + lane]));
     }
     F2 h(hl, hr);
 #pragma unroll
@@ -575,20 +585,29 @@ __device__ __forceinline__ void make_window2(const Row3P& s, const Row3P& c, con
     ps.nw = n.psw; ps.n = n.psc; ps.ne = n.pse;
 }
 
-template <int V>
-__device__ __forceinline__ void march2(const float* __restrict__ src, float* __restrict__ dst,
+// One half (node A: x, node B: y) of a pair window.
+__device__ __forceinline__ Win<float> half_win(const Win<F2>& w, bool b)
+{
+    auto h = [b](F2 v) { return b ? v.v.y : v.v.x; };
+    return Win<float>{h(w.sw), h(w.s), h(w.se), h(w.w), h(w.c), h(w.e), h(w.nw), h(w.n), h(w.ne)};
+}
+
+template <typename S, int V>
+__device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict__ dst,
                                        const Geometry& G, const Consts<float>& K, int wstrip,
                                        int seg, int seg_h, int* err)
 {
-    constexpr int NS = Stages<float>::value;
+    constexpr int NS = Stages<S>::value;
     constexpr bool SRT = (V & kVarSRT) != 0;
     constexpr bool LANGMUIR = (V & kVarLangmuir) != 0;
-    constexpr int STAGE = 2 * TILE;                  // floats per stage (two tiles)
+    constexpr bool NARROW = Narrow<S>::value;
+    constexpr int TE = Tile<S>::ELEMS;               // elements per tile
+    constexpr int STAGE = 2 * TE;                    // elements per stage (two tiles)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
 
-    float* tiles = reinterpret_cast<float*>(smem_raw + wib * warp_smem_bytes<float, 2>());
+    S* tiles = reinterpret_cast<S*>(smem_raw + wib * warp_smem_bytes<S, 2>());
     const uint32_t bar0 = smem_u32(tiles + NS * STAGE);
     if (lane == 0)
         for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8 * s, 1);
@@ -602,12 +621,12 @@ __device__ __forceinline__ void march2(const float* __restrict__ src, float* __r
     const int wl = w - 1;                            // last active column (0..63)
     const bool actA = lane < w, actB = lane + 32 < w;
     const bool lastA = lane == wl, lastB = lane + 32 == wl;
-    const int TB = nt == 2 ? TILE : 0;               // offset of tile B in a stage
+    const int TB = nt == 2 ? TE : 0;                 // offset of tile B in a stage
     const int xA = actA ? x0 + lane : x0 + wl;       // idle lanes shadow the last column
     const int xB = actB ? x0 + 32 + lane : x0 + wl;
     const int xl = map_col(x0 - 1, G), xr = map_col(x0 + w, G);
-    const int row_elems = G.nstrips * TILE;
-    auto row_ptr = [&](const float* base, int row) { return base + (long long)row * row_elems; };
+    const int row_elems = G.nstrips * TE;
+    auto row_ptr = [&](const S* base, int row) { return base + (long long)row * row_elems; };
 
     const int ys = seg * seg_h;
     const int ye = min(ys + seg_h, G.ny);
@@ -615,24 +634,30 @@ __device__ __forceinline__ void march2(const float* __restrict__ src, float* __r
     const bool up = (seg & 1) == 0;
     auto row_of = [&](int k) { return map_row(up ? ys + k : ye - 1 - k, G); };
 
-    // halo: lanes 0..8 load g-bar plane q, lanes 16..24 f plane q, at columns xl and xr
-    const int hq = lane & 15;
+    // halo: lanes 0..8 load g-bar plane q, lanes 16..24 f plane q, at columns xl and xr; in
+    // the 16-bit forms lanes 9 and 25 add the columns' Z_g and Z_f to the scaled deviations
+    const int hq = lane & 15, hlat = lane >> 4;
     const bool hlane = hq < 9;
-    const int hplane = (lane >> 4) * 9 + hq;
-    const int hoffl = col_off(xl) + hplane * 32;
-    const int hoffr = col_off(xr) + hplane * 32;
+    const bool zlane = NARROW && hq == 9;
+    const int hplane = hlat * 9 + hq;
+    const int hoffl = zlane ? z_off<S>(xl) + 64 * hlat : col_off<S>(xl) + hplane * 32;
+    const int hoffr = zlane ? z_off<S>(xr) + 64 * hlat : col_off<S>(xr) + hplane * 32;
+    const float hinv = NARROW ? (hlat ? K.st_inv[1] : K.st_inv[0]) : 1.0f;
     auto halo_load = [&](int k, float& hl, float& hr) {
         hl = 0.0f;
         hr = 0.0f;
+        const S* rb = row_ptr(src, row_of(k));
         if (hlane) {
-            const float* rb = row_ptr(src, row_of(k));
-            hl = __ldg(rb + hoffl);
-            hr = __ldg(rb + hoffr);
+            hl = narrow_to_f_or_self(__ldg(rb + hoffl)) * hinv;
+            hr = narrow_to_f_or_self(__ldg(rb + hoffr)) * hinv;
+        } else if (zlane) {
+            hl = __ldg(reinterpret_cast<const float*>(rb + hoffl));
+            hr = __ldg(reinterpret_cast<const float*>(rb + hoffr));
         }
     };
 
     int issued = -2;
-    const uint32_t copy_bytes = (uint32_t)(nt * TILE * sizeof(float));
+    const uint32_t copy_bytes = (uint32_t)(nt * Tile<S>::BYTES);
     auto issue = [&](int k, int st) {
         if (k > nrows) return;
         __syncwarp();
@@ -640,7 +665,7 @@ __device__ __forceinline__ void march2(const float* __restrict__ src, float* __r
             fence_proxy_async();
             const uint32_t bar = bar0 + 8 * st;
             mbar_expect_tx(bar, copy_bytes);
-            bulk_g2s(smem_u32(tiles + st * STAGE), row_ptr(src, row_of(k)) + t0 * TILE,
+            bulk_g2s(smem_u32(tiles + st * STAGE), row_ptr(src, row_of(k)) + t0 * TE,
                      copy_bytes, bar);
         }
         issued = k;
@@ -659,11 +684,11 @@ __device__ __forceinline__ void march2(const float* __restrict__ src, float* __r
     float hl, hr, hl2, hr2;
     halo_load(-1, hl, hr);
     if (!wait_k(-1, 0)) { fail(-1); return; }
-    window_row2(tiles, tiles + TB, lane, lastA, lastB, hl, hr, rb);
+    window_row2<S>(tiles, tiles + TB, lane, lastA, lastB, hl, hr, K, rb);
     issue(NS - 1, 0);
     halo_load(0, hl, hr);
     if (!wait_k(0, 1)) { fail(0); return; }
-    window_row2(tiles + STAGE, tiles + STAGE + TB, lane, lastA, lastB, hl, hr, rc);
+    window_row2<S>(tiles + STAGE, tiles + STAGE + TB, lane, lastA, lastB, hl, hr, K, rc);
     halo_load(1, hl2, hr2);
 
     // neighbour columns of the two nodes (periodic wrap; walls handled by the push)
@@ -673,14 +698,15 @@ __device__ __forceinline__ void march2(const float* __restrict__ src, float* __r
         bxe = xp >= G.nx && G.wall_x;
         if (xm < 0) xm += G.nx;
         if (xp >= G.nx) xp -= G.nx;
-        cw = col_off(xm);
-        cc = col_off(x);
-        ce = col_off(xp);
+        cw = col_off<S>(xm);
+        cc = col_off<S>(x);
+        ce = col_off<S>(xp);
     };
     int cwA, ccA, ceA, cwB, ccB, ceB;
     bool bxwA, bxeA, bxwB, bxeB;
     cols(xA, cwA, ccA, ceA, bxwA, bxeA);
     cols(xB, cwB, ccB, ceB, bxwB, bxeB);
+    const int zcA = NARROW ? z_off<S>(xA) : 0, zcB = NARROW ? z_off<S>(xB) : 0;
     const bool xwall_warp = __any_sync(FULL, bxwA || bxeA || bxwB || bxeB);
     const F2 xf{static_cast<float>(xA), static_cast<float>(xB)};
     const F2 omega_phi(K.omega_phi);
@@ -689,21 +715,36 @@ __device__ __forceinline__ void march2(const float* __restrict__ src, float* __r
     auto body = [&](int i, int st) {
         const int st1 = st + 1 == NS ? 0 : st + 1;
         if (!wait_k(i + 1, st1)) { fail(i + 1); ok = false; return; }
-        window_row2(tiles + st1 * STAGE, tiles + st1 * STAGE + TB, lane, lastA, lastB, hl2, hr2,
-                    rn);
+        window_row2<S>(tiles + st1 * STAGE, tiles + st1 * STAGE + TB, lane, lastA, lastB, hl2,
+                       hr2, K, rn);
         if (i + 2 <= nrows) halo_load(i + 2, hl2, hr2);
 
         const int y = up ? ys + i : ye - 1 - i;
         Win<F2> ph, ps;
         if (up) make_window2(rb, rc, rn, ph, ps);
         else make_window2(rn, rc, rb, ph, ps);
-        const float* ta = tiles + st * STAGE;
-        const float* tb = ta + TB;
+        const S* ta = tiles + st * STAGE;
+        const S* tb = ta + TB;
+        constexpr int P0 = Tile<S>::P0;
         F2 g[9], f[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            g[a] = F2(ta[a * 32 + lane], tb[a * 32 + lane]);
-            f[a] = F2(ta[(9 + a) * 32 + lane], tb[(9 + a) * 32 + lane]);
+            g[a] = F2(narrow_to_f_or_self(ta[P0 + a * 32 + lane]),
+                      narrow_to_f_or_self(tb[P0 + a * 32 + lane]));
+            f[a] = F2(narrow_to_f_or_self(ta[P0 + (9 + a) * 32 + lane]),
+                      narrow_to_f_or_self(tb[P0 + (9 + a) * 32 + lane]));
+        }
+        if constexpr (NARROW) {   // q_a = w_a Z + d_a / s
+            const float* za = reinterpret_cast<const float*>(ta);
+            const float* zb = reinterpret_cast<const float*>(tb);
+            const F2 zg(za[lane], zb[lane]), zf(za[32 + lane], zb[32 + lane]);
+            const F2 ig(K.st_inv[0]), ifl(K.st_inv[1]);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                const F2 wa(float(d2q9_w(a)));
+                g[a] = fmad(g[a], ig, wa * zg);
+                f[a] = fmad(f[a], ifl, wa * zf);
+            }
         }
         const F2 jgx = ((g[1] - g[3]) + (g[5] - g[6])) - (g[7] - g[8]);
         const F2 jgy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
@@ -718,26 +759,26 @@ __device__ __forceinline__ void march2(const float* __restrict__ src, float* __r
         const bool bys = ym < 0 && G.wall_y, byn = yp >= G.ny && G.wall_y;
         if (ym < 0) ym += G.ny;
         if (yp >= G.ny) yp -= G.ny;
-        float* rS = const_cast<float*>(row_ptr(dst, ym));
-        float* rC = const_cast<float*>(row_ptr(dst, y));
-        float* rN = const_cast<float*>(row_ptr(dst, yp));
+        S* rS = const_cast<S*>(row_ptr(dst, ym));
+        S* rC = const_cast<S*>(row_ptr(dst, y));
+        S* rN = const_cast<S*>(row_ptr(dst, yp));
         const bool fast = !(bys || byn) && !xwall_warp;
-        if (actA) {
-            const float gA[9] = {g[0].v.x, g[1].v.x, g[2].v.x, g[3].v.x, g[4].v.x,
-                                 g[5].v.x, g[6].v.x, g[7].v.x, g[8].v.x};
-            const float fA[9] = {f[0].v.x, f[1].v.x, f[2].v.x, f[3].v.x, f[4].v.x,
-                                 f[5].v.x, f[6].v.x, f[7].v.x, f[8].v.x};
-            push_node<float, float, false>(gA, fA, rS, rC, rN, cwA, ccA, ceA, bxwA, bxeA, bys,
-                                           byn, G.slip, fast, K);
-        }
-        if (actB) {
-            const float gB[9] = {g[0].v.y, g[1].v.y, g[2].v.y, g[3].v.y, g[4].v.y,
-                                 g[5].v.y, g[6].v.y, g[7].v.y, g[8].v.y};
-            const float fB[9] = {f[0].v.y, f[1].v.y, f[2].v.y, f[3].v.y, f[4].v.y,
-                                 f[5].v.y, f[6].v.y, f[7].v.y, f[8].v.y};
-            push_node<float, float, false>(gB, fB, rS, rC, rN, cwB, ccB, ceB, bxwB, bxeB, bys,
-                                           byn, G.slip, fast, K);
-        }
+        auto push = [&](bool b, int cw, int cc, int ce, int zc, bool bxw, bool bxe) {
+            float gq[9], fq[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                gq[a] = b ? g[a].v.y : g[a].v.x;
+                fq[a] = b ? f[a].v.y : f[a].v.x;
+            }
+            if constexpr (NARROW)
+                push_node_z<S, float>(gq, fq, half_win(ps, b), half_win(ph, b), rS, rC, rN, cw,
+                                      cc, ce, zc, bxw, bxe, bys, byn, G.slip, fast, K);
+            else
+                push_node<S, float, false>(gq, fq, rS, rC, rN, cw, cc, ce, bxw, bxe, bys, byn,
+                                           G.slip, fast, K);
+        };
+        if (actA) push(false, cwA, ccA, ceA, zcA, bxwA, bxeA);
+        if (actB) push(true, cwB, ccB, ceB, zcB, bxwB, bxeB);
         issue(i + NS, st);
         rb = rc;
         rc = rn;
@@ -749,11 +790,11 @@ __device__ __forceinline__ void march2(const float* __restrict__ src, float* __r
     }
 }
 
-// The FP32 coupled step variants run paired (two tiles per warp); the others one tile per warp.
+// The coupled step variants with FP32 arithmetic run paired (two tiles per warp); FP64 and the
+// interface-only variants one tile per warp.
 template <typename R, typename S, int V>
 struct Paired {
-    static constexpr bool value =
-        std::is_same<R, float>::value && std::is_same<S, float>::value && (V & kVarShear) == 0;
+    static constexpr bool value = std::is_same<R, float>::value && (V & kVarShear) == 0;
 };
 template <typename R, typename S, int V>
 __host__ __device__ constexpr int tiles_per_warp() { return Paired<R, S, V>::value ? 2 : 1; }
@@ -769,7 +810,7 @@ step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R
     const int strip = warp % wstrips;
     const int seg = warp / wstrips;
     if (seg >= L.nseg) return;                       // warp-uniform
-    if constexpr (NT == 2) march2<V>(src, dst, G, K, strip, seg, L.seg_h, L.err);
+    if constexpr (NT == 2) march2<S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err);
     else march<R, S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign);
 }
 
@@ -792,7 +833,7 @@ batch_step_kernel(S* __restrict__ base, const BatchCase<R>* __restrict__ cases,
     const int seg = t.y / wstrips;
     const S* src = base + (parity ? c.off1 : c.off0);
     S* dst = base + (parity ? c.off0 : c.off1);
-    if constexpr (NT == 2) march2<0>(src, dst, G, c.K, strip, seg, c.seg_h, err);
+    if constexpr (NT == 2) march2<S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err);
     else march<R, S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1);
 }
 
