@@ -534,18 +534,18 @@ struct Row3P {
 // loads (summed over the half warp into the halo columns' zeroth moments); lastA / lastB: this
 // lane's node A / B is the last active column of the warp (its east neighbour is the right halo
 // column).  ta / tb: the two tiles of the row in shared memory.
-template <typename S>
+template <typename S, bool PHI_ONLY = false>
 __device__ __forceinline__ void window_row2(const S* ta, const S* tb, int lane, bool lastA,
                                             bool lastB, float hl, float hr,
                                             const Consts<float>& K, Row3P& row)
 {
     constexpr int P0 = Tile<S>::P0;
     auto val = [&](const S* t, int p) { return float(narrow_to_f_or_self(t[P0 + p * 32 + lane])); };
-    F2 ps(val(ta, 0), val(tb, 0));
-    F2 ph(val(ta, 9), val(tb, 9));
+    F2 ps(0.0f), ph(val(ta, 9), val(tb, 9));
+    if (!PHI_ONLY) ps = F2(val(ta, 0), val(tb, 0));
 #pragma unroll
     for (int a = 1; a < 9; ++a) {
-        ps += F2(val(ta, a), val(tb, a));
+        if (!PHI_ONLY) ps += F2(val(ta, a), val(tb, a));
         ph += F2(val(ta, 9 + a), val(tb, 9 + a));
     }
     if constexpr (Narrow<S>::value) {   // Z + (sum of the deviations) / s
@@ -595,11 +595,13 @@ __device__ __forceinline__ Win<float> half_win(const Win<F2>& w, bool b)
 template <typename S, int V>
 __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict__ dst,
                                        const Geometry& G, const Consts<float>& K, int wstrip,
-                                       int seg, int seg_h, int* err)
+                                       int seg, int seg_h, int* err, int flow_sign)
 {
     constexpr int NS = Stages<S>::value;
     constexpr bool SRT = (V & kVarSRT) != 0;
+    constexpr bool SHEAR = (V & kVarShear) != 0;
     constexpr bool LANGMUIR = (V & kVarLangmuir) != 0;
+    static_assert(!(SHEAR && Narrow<S>::value), "the imposed flow runs in FP32 storage");
     constexpr bool NARROW = Narrow<S>::value;
     constexpr int TE = Tile<S>::ELEMS;               // elements per tile
     constexpr int STAGE = 2 * TE;                    // elements per stage (two tiles)
@@ -637,7 +639,7 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
     // halo: lanes 0..8 load g-bar plane q, lanes 16..24 f plane q, at columns xl and xr; in
     // the 16-bit forms lanes 9 and 25 add the columns' Z_g and Z_f to the scaled deviations
     const int hq = lane & 15, hlat = lane >> 4;
-    const bool hlane = hq < 9;
+    const bool hlane = hq < 9 && (!SHEAR || hlat == 1);
     const bool zlane = NARROW && hq == 9;
     const int hplane = hlat * 9 + hq;
     const int hoffl = zlane ? z_off<S>(xl) + 64 * hlat : col_off<S>(xl) + hplane * 32;
@@ -657,7 +659,9 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
     };
 
     int issued = -2;
-    const uint32_t copy_bytes = (uint32_t)(nt * Tile<S>::BYTES);
+    // the interface lattice alone copies only the f half (planes 9..17) of each of the tiles
+    const uint32_t copy_bytes = SHEAR ? (uint32_t)(nt * 9 * 32 * sizeof(S))
+                                      : (uint32_t)(nt * Tile<S>::BYTES);
     auto issue = [&](int k, int st) {
         if (k > nrows) return;
         __syncwarp();
@@ -665,8 +669,16 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
             fence_proxy_async();
             const uint32_t bar = bar0 + 8 * st;
             mbar_expect_tx(bar, copy_bytes);
-            bulk_g2s(smem_u32(tiles + st * STAGE), row_ptr(src, row_of(k)) + t0 * TE,
-                     copy_bytes, bar);
+            const S* rowk = row_ptr(src, row_of(k)) + t0 * TE;
+            if constexpr (SHEAR) {
+                constexpr int FOFF = 9 * 32;
+                constexpr uint32_t FB = 9 * 32 * sizeof(S);
+                bulk_g2s(smem_u32(tiles + st * STAGE + FOFF), rowk + FOFF, FB, bar);
+                if (nt == 2)
+                    bulk_g2s(smem_u32(tiles + st * STAGE + TE + FOFF), rowk + TE + FOFF, FB, bar);
+            } else {
+                bulk_g2s(smem_u32(tiles + st * STAGE), rowk, copy_bytes, bar);
+            }
         }
         issued = k;
     };
@@ -684,11 +696,11 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
     float hl, hr, hl2, hr2;
     halo_load(-1, hl, hr);
     if (!wait_k(-1, 0)) { fail(-1); return; }
-    window_row2<S>(tiles, tiles + TB, lane, lastA, lastB, hl, hr, K, rb);
+    window_row2<S, SHEAR>(tiles, tiles + TB, lane, lastA, lastB, hl, hr, K, rb);
     issue(NS - 1, 0);
     halo_load(0, hl, hr);
     if (!wait_k(0, 1)) { fail(0); return; }
-    window_row2<S>(tiles + STAGE, tiles + STAGE + TB, lane, lastA, lastB, hl, hr, K, rc);
+    window_row2<S, SHEAR>(tiles + STAGE, tiles + STAGE + TB, lane, lastA, lastB, hl, hr, K, rc);
     halo_load(1, hl2, hr2);
 
     // neighbour columns of the two nodes (periodic wrap; walls handled by the push)
@@ -711,12 +723,22 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
     const F2 xf{static_cast<float>(xA), static_cast<float>(xB)};
     const F2 omega_phi(K.omega_phi);
     bool ok = true;
+    // imposed flow: sin / cos of pi (x / L0 - 1/2) for the two columns, and the signed U_0 pi
+    F2 sxl(0.0f), cxl(0.0f);
+    if constexpr (SHEAR) {
+        float sa, ca, sb, cb;
+        sincospif(float(xA) * K.inv_nx - 0.5f, &sa, &ca);
+        sincospif(float(xB) * K.inv_nx - 0.5f, &sb, &cb);
+        sxl = F2(sa, sb);
+        cxl = F2(ca, cb);
+    }
+    const float u0s = float(flow_sign) * K.u0pi;
 
     auto body = [&](int i, int st) {
         const int st1 = st + 1 == NS ? 0 : st + 1;
         if (!wait_k(i + 1, st1)) { fail(i + 1); ok = false; return; }
-        window_row2<S>(tiles + st1 * STAGE, tiles + st1 * STAGE + TB, lane, lastA, lastB, hl2,
-                       hr2, K, rn);
+        window_row2<S, SHEAR>(tiles + st1 * STAGE, tiles + st1 * STAGE + TB, lane, lastA, lastB,
+                              hl2, hr2, K, rn);
         if (i + 2 <= nrows) halo_load(i + 2, hl2, hr2);
 
         const int y = up ? ys + i : ye - 1 - i;
@@ -729,8 +751,9 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
         F2 g[9], f[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            g[a] = F2(narrow_to_f_or_self(ta[P0 + a * 32 + lane]),
-                      narrow_to_f_or_self(tb[P0 + a * 32 + lane]));
+            if (!SHEAR)
+                g[a] = F2(narrow_to_f_or_self(ta[P0 + a * 32 + lane]),
+                          narrow_to_f_or_self(tb[P0 + a * 32 + lane]));
             f[a] = F2(narrow_to_f_or_self(ta[P0 + (9 + a) * 32 + lane]),
                       narrow_to_f_or_self(tb[P0 + (9 + a) * 32 + lane]));
         }
@@ -746,12 +769,20 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
                 f[a] = fmad(f[a], ifl, wa * zf);
             }
         }
-        const F2 jgx = ((g[1] - g[3]) + (g[5] - g[6])) - (g[7] - g[8]);
-        const F2 jgy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
         Macro<F2> m;
-        node_macro<F2, LANGMUIR>(ph, ps, jgx, jgy, xf, F2(float(y)), K, m);
-        if constexpr (SRT) collide_fluid_srt<F2>(g, ps.c, m);
-        else collide_fluid<F2>(g, ps.c, m);
+        if constexpr (SHEAR) {
+            float syr, cyr;
+            sincospif(float(y) * K.inv_ny - 0.5f, &syr, &cyr);
+            m.ux = F2(-u0s * syr) * cxl;
+            m.uy = F2(u0s * cyr) * sxl;
+            interface_flux<F2>(ph, K, m.jx, m.jy);
+        } else {
+            const F2 jgx = ((g[1] - g[3]) + (g[5] - g[6])) - (g[7] - g[8]);
+            const F2 jgy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
+            node_macro<F2, LANGMUIR>(ph, ps, jgx, jgy, xf, F2(float(y)), K, m);
+            if constexpr (SRT) collide_fluid_srt<F2>(g, ps.c, m);
+            else collide_fluid<F2>(g, ps.c, m);
+        }
         if constexpr (SRT) collide_ace_srt<F2>(f, ph.c, m, omega_phi);
         else collide_ace<F2>(f, ph.c, m, omega_phi);
 
@@ -767,14 +798,14 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
             float gq[9], fq[9];
 #pragma unroll
             for (int a = 0; a < 9; ++a) {
-                gq[a] = b ? g[a].v.y : g[a].v.x;
+                gq[a] = SHEAR ? 0.0f : (b ? g[a].v.y : g[a].v.x);
                 fq[a] = b ? f[a].v.y : f[a].v.x;
             }
             if constexpr (NARROW)
                 push_node_z<S, float>(gq, fq, half_win(ps, b), half_win(ph, b), rS, rC, rN, cw,
                                       cc, ce, zc, bxw, bxe, bys, byn, G.slip, fast, K);
             else
-                push_node<S, float, false>(gq, fq, rS, rC, rN, cw, cc, ce, bxw, bxe, bys, byn,
+                push_node<S, float, SHEAR>(gq, fq, rS, rC, rN, cw, cc, ce, bxw, bxe, bys, byn,
                                            G.slip, fast, K);
         };
         if (actA) push(false, cwA, ccA, ceA, zcA, bxwA, bxeA);
@@ -790,11 +821,10 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
     }
 }
 
-// The coupled step variants with FP32 arithmetic run paired (two tiles per warp); FP64 and the
-// interface-only variants one tile per warp.
+// Every step with FP32 arithmetic runs paired (two tiles per warp); FP64 one tile per warp.
 template <typename R, typename S, int V>
 struct Paired {
-    static constexpr bool value = std::is_same<R, float>::value && (V & kVarShear) == 0;
+    static constexpr bool value = std::is_same<R, float>::value;
 };
 template <typename R, typename S, int V>
 __host__ __device__ constexpr int tiles_per_warp() { return Paired<R, S, V>::value ? 2 : 1; }
@@ -810,7 +840,7 @@ step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R
     const int strip = warp % wstrips;
     const int seg = warp / wstrips;
     if (seg >= L.nseg) return;                       // warp-uniform
-    if constexpr (NT == 2) march2<S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err);
+    if constexpr (NT == 2) march2<S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign);
     else march<R, S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign);
 }
 
@@ -833,7 +863,7 @@ batch_step_kernel(S* __restrict__ base, const BatchCase<R>* __restrict__ cases,
     const int seg = t.y / wstrips;
     const S* src = base + (parity ? c.off1 : c.off0);
     S* dst = base + (parity ? c.off0 : c.off1);
-    if constexpr (NT == 2) march2<S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err);
+    if constexpr (NT == 2) march2<S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1);
     else march<R, S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1);
 }
 
