@@ -144,6 +144,23 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device="cuda") -> float:
+    """The largest value of x over the ranks (the job time of independent replicas that
+    started together at a barrier); x itself on one rank."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(ws: int, nodes: int, steps: int, ms_max: float) -> float:
+    """Whole-job rate: node updates of all ranks over the slowest rank's time."""
+    return ws * nodes * steps / (ms_max * 1e-3) / 1e6
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -183,10 +200,7 @@ def run_ours(args):
         dist.barrier()
     ms_total = ev0.elapsed_time(ev1)
     ms_launch = ms_total / K         # every launch in the region is the step kernel
-    t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms_total, ws)
     diag = lbm.lbm_diagnostics(ctx)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -208,11 +222,7 @@ def run_ours(args):
         lbm.lbm_init_fields(ctx, *(host[k] for k in ("phi", "p", "ux", "uy")))
         lbm.lbm_step(ctx, Ke)
         lbm.lbm_get_fields(ctx, *(hout[k] for k in ("phi", "p", "ux", "uy", "rho")))
-        te = time.perf_counter() - t0
-        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
+        te = max_over_ranks(time.perf_counter() - t0, ws)
         e2e = {"value": round(ws * N * Ke / te / 1e6, 2), "unit": "MLUPS",
                "h2d_bytes_per_step": int(4 * 8 * N / Ke),
                "d2h_bytes_per_step": int(5 * 8 * N / Ke),
@@ -233,7 +243,7 @@ def run_ours(args):
     if key in NCU_TRAFFIC:
         traffic = NCU_TRAFFIC[key]
     seg, block = None, None
-    value = ws * N * K / (ms_max * 1e-3) / 1e6
+    value = job_mlups(ws, N, K, ms_max)
     line = {
         "metric": METRIC,
         "value": round(value, 2),
