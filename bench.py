@@ -30,6 +30,9 @@ sys.path.insert(0, ROOT)
 # bytes read + written once per node update: 18 populations (FP32 / FP64); 16-bit: 18 deviations
 # plus the two FP32 zeroth-moment planes
 BYTES_PER_LU = {"fp32": 144, "fp64": 288, "fp16": 88, "bf16": 88}
+STORAGE = {"fp32": "FP32 populations", "fp64": "FP64 populations",
+           "fp16": "FP16 deviations from each node's rest state + FP32 zeroth moments",
+           "bf16": "BF16 deviations from each node's rest state + FP32 zeroth moments"}
 HBM_FALLBACK_GBS = 6800.0
 L2_BYTES = 129e6
 METRIC = "MLUPS (million node updates of both lattices per second)"
@@ -81,8 +84,10 @@ def kernel_source_hash() -> str:
 # DRAM traffic per launch of the step kernel from an ncu capture (profiles/), keyed by the
 # hash of the kernel sources it was taken on; scaled by node count to the bench workload.
 NCU_TRAFFIC = {
-    # profiles/step_kernel_impact_2048x1024_fp32.md (read 152.09 MB + write 98.38 MB)
-    ("60e78babbd4d22ad", "impact", "fp32"): 250_467_584,
+    # profiles/step_kernel_impact_2048x1024_fp32.md (read 152.05 MB + write 98.49 MB)
+    ("e305d2e748331700", "impact", "fp32"): 250_543_872,
+    # profiles/step_kernel_impact_2048x1024_fp16.md (read 92.43 MB + write 40.90 MB)
+    ("e305d2e748331700", "impact", "fp16"): 133_327_872,
 }
 
 
@@ -255,11 +260,12 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else "f64",
+        "dtype": "f64" if args.precision == "fp64" else "f32",
         "data": "synthetic (seeded initial fields of the paper's setup; no dataset)",
         "config": {
             "workload": f"{args.workload} {case['nx']}x{case['ny']} {args.precision} "
                         f"populations",
+            "storage": STORAGE[args.precision],
             **describe(case),
             "nodes": N,
             "l2": f"inputs larger than L2 (no flush): state {N * bpl / 1e6:.0f} MB "
@@ -510,7 +516,7 @@ def run_ensemble_line(args):
         "metric": METRIC, "value": r["batched_mlups"], "unit": "MLUPS", "n_gpus": 1,
         "steps": args.steps, "warmup": 8, "ms_per_step": r["batched_ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else "f64",
+        "dtype": "f64" if args.precision == "fp64" else "f32",
         "data": "synthetic (seeded ensemble of drop cases; no dataset)",
         "config": {"workload": f"ensemble of {r['cases']} drop cases, {r['nodes']} nodes, "
                                f"{args.precision} populations", "nodes": r["nodes"]},
@@ -530,7 +536,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="impact")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
