@@ -83,12 +83,14 @@ def test_fp32_parity_200_steps(nx, ny, wx, wy):
         assert rel_l2(fl[k], ref[k]) <= 2e-5, k
 
 
-def test_launch_shape_does_not_change_results():
-    """Segments of different heights (and both marching directions) give identical bits."""
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+def test_launch_shape_does_not_change_results(prec):
+    """Segments of different heights (and both marching directions) and block sizes give
+    identical bits, for one column per lane (FP64) and the paired forms (FP32, 16-bit)."""
     case = W.random_drop(75, 61, seed=4, wall_y=True, rho_ratio=100.0)
     outs = []
     for seg, block in ((0, 0), (1, 32), (3, 64), (7, 256), (61, 128)):
-        with lbm.Simulation(case, precision="fp64") as sim:
+        with lbm.Simulation(case, precision=prec) as sim:
             sim.init_case()
             lbm.lbm_set_launch(sim.ctx, seg, block)
             sim.step(9)
