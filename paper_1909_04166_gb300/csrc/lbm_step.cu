@@ -9,7 +9,9 @@
 // Step kernel (one launch = one time step of both lattices over the whole grid):
 //   * Each warp owns one strip of 32 columns and one segment of rows and marches along the rows
 //     (segments alternate direction so that neighbours read a shared boundary row at about the
-//     same time and the re-read hits L2).  Lane l owns column x0 + l.
+//     same time and the re-read hits L2; every segment also reverses its direction from one
+//     step to the next, so that a step starts on the rows the previous one wrote last, many of
+//     which are still in L2).  Lane l owns column x0 + l.
 //   * Tiles are staged in shared memory by bulk asynchronous copies (cp.async.bulk, one 2304-byte
 //     copy per warp-row, completion on an mbarrier), S stages deep: while row i is collided,
 //     rows i+2 .. i+S-1 are in flight.
@@ -38,6 +40,7 @@ struct StepLaunch {
     int nseg;      // ceil(ny / seg_h)
     int* err;      // device error word (0 = ok)
     int flow_sign; // imposed flow: +1, or -1 once reversed
+    int flip;      // 0 / 1 on alternate steps: reverses the march direction of every segment
 };
 
 // Step variants: bit 0 single relaxation time (Sec. 7) instead of the cascaded rates; bit 1 the
@@ -342,7 +345,7 @@ __device__ __forceinline__ void push_node_z(const R g[9], const R f[9], const Wi
 template <typename R, typename S, int V>
 __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__ dst,
                                       const Geometry& G, const Consts<R>& K, int strip, int seg,
-                                      int seg_h, int* err, int flow_sign)
+                                      int seg_h, int* err, int flow_sign, int flip)
 {
     constexpr int NS = Stages<S>::value;
     constexpr bool SRT = (V & kVarSRT) != 0;
@@ -376,7 +379,7 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     const int ys = seg * seg_h;
     const int ye = min(ys + seg_h, G.ny);
     const int nrows = ye - ys;
-    const bool up = (seg & 1) == 0;
+    const bool up = ((seg + flip) & 1) == 0;
     // row visited at step k (k = -1 .. nrows): behind/current/ahead rows of the march
     auto row_of = [&](int k) { return map_row(up ? ys + k : ye - 1 - k, G); };
 
@@ -595,7 +598,7 @@ __device__ __forceinline__ Win<float> half_win(const Win<F2>& w, bool b)
 template <typename S, int V>
 __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict__ dst,
                                        const Geometry& G, const Consts<float>& K, int wstrip,
-                                       int seg, int seg_h, int* err, int flow_sign)
+                                       int seg, int seg_h, int* err, int flow_sign, int flip)
 {
     constexpr int NS = Stages<S>::value;
     constexpr bool SRT = (V & kVarSRT) != 0;
@@ -633,7 +636,7 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
     const int ys = seg * seg_h;
     const int ye = min(ys + seg_h, G.ny);
     const int nrows = ye - ys;
-    const bool up = (seg & 1) == 0;
+    const bool up = ((seg + flip) & 1) == 0;
     auto row_of = [&](int k) { return map_row(up ? ys + k : ye - 1 - k, G); };
 
     // halo: lanes 0..8 load g-bar plane q, lanes 16..24 f plane q, at columns xl and xr; in
@@ -840,8 +843,10 @@ step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R
     const int strip = warp % wstrips;
     const int seg = warp / wstrips;
     if (seg >= L.nseg) return;                       // warp-uniform
-    if constexpr (NT == 2) march2<S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign);
-    else march<R, S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign);
+    if constexpr (NT == 2)
+        march2<S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign, L.flip);
+    else
+        march<R, S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign, L.flip);
 }
 
 // One time step of many independent grids in one launch: warp w takes task w = (case, local
@@ -863,8 +868,8 @@ batch_step_kernel(S* __restrict__ base, const BatchCase<R>* __restrict__ cases,
     const int seg = t.y / wstrips;
     const S* src = base + (parity ? c.off1 : c.off0);
     S* dst = base + (parity ? c.off0 : c.off1);
-    if constexpr (NT == 2) march2<S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1);
-    else march<R, S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1);
+    if constexpr (NT == 2) march2<S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1, parity);
+    else march<R, S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1, parity);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1060,15 +1065,23 @@ int step_blocks_per_sm(int block)
     return nb > 0 ? nb : 1;
 }
 
+// March direction parity of a step: the two state buffers alternate as source, so consecutive
+// steps march in opposite directions.
+inline int flip_of(const void* src, const void* dst)
+{
+    return reinterpret_cast<uintptr_t>(src) > reinterpret_cast<uintptr_t>(dst) ? 1 : 0;
+}
+
 template <typename R, typename S, int V>
 cudaError_t launch_step(const void* src, void* dst, const Geometry& G, const Consts<R>& K,
                         int seg_h, int block, int* err, int flow_sign, cudaStream_t st)
 {
-    StepLaunch L;
+    StepLaunch L = {};
     L.seg_h = seg_h;
     L.nseg = (G.ny + seg_h - 1) / seg_h;
     L.err = err;
     L.flow_sign = flow_sign;
+    L.flip = flip_of(src, dst);
     const long long warps = (long long)step_warp_strips<R, S, V>(G.nstrips) * L.nseg;
     const int wpb = block / 32;
     const long long grid = (warps + wpb - 1) / wpb;
@@ -1084,7 +1097,7 @@ cudaError_t build_step_graph(const void* a, const void* b, const Geometry& G, co
                              int seg_h, int block, int* err, int flow_sign, int chunk,
                              cudaGraphExec_t* out)
 {
-    StepLaunch L;
+    StepLaunch L = {};
     L.seg_h = seg_h;
     L.nseg = (G.ny + seg_h - 1) / seg_h;
     L.err = err;
@@ -1101,6 +1114,7 @@ cudaError_t build_step_graph(const void* a, const void* b, const Geometry& G, co
     for (int s = 0; s < chunk && e == cudaSuccess; ++s) {
         const S* src = static_cast<const S*>((s & 1) ? b : a);
         S* dst = const_cast<S*>(static_cast<const S*>((s & 1) ? a : b));
+        L.flip = flip_of(src, dst);
         void* args[] = {(void*)&src, (void*)&dst, (void*)&g, (void*)&k, (void*)&L};
         cudaKernelNodeParams p = {};
         p.func = (void*)step_kernel<R, S, V>;
