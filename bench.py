@@ -82,12 +82,14 @@ def kernel_source_hash() -> str:
 
 
 # DRAM traffic per launch of the step kernel from an ncu capture (profiles/), keyed by the
-# hash of the kernel sources it was taken on; scaled by node count to the bench workload.
+# hash of the kernel sources it was taken on; scaled by node count to the bench workload.  The
+# figures are steady-state launches (caches not flushed between launches, as in the timed run;
+# mean of three consecutive launches).
 NCU_TRAFFIC = {
-    # profiles/step_kernel_impact_2048x1024_fp32.md (read 152.05 MB + write 98.49 MB)
-    ("e305d2e748331700", "impact", "fp32"): 250_543_872,
-    # profiles/step_kernel_impact_2048x1024_fp16.md (read 92.43 MB + write 40.90 MB)
-    ("e305d2e748331700", "impact", "fp16"): 133_327_872,
+    # profiles/step_kernel_impact_2048x1024_fp32.md (read 105.80 MB + write 150.10 MB)
+    ("fa5ca9717bea708e", "impact", "fp32"): 255_901_611,
+    # profiles/step_kernel_impact_2048x1024_fp16.md (read 44.26 MB + write 92.29 MB)
+    ("fa5ca9717bea708e", "impact", "fp16"): 136_555_264,
 }
 
 
