@@ -250,6 +250,43 @@ def test_fluid_collision_moment_changes_with_forces(trial):
     assert (d * EY).sum() == pytest.approx(C2 * Fty, rel=1e-9, abs=1e-17)
 
 
+@pytest.mark.parametrize("trial", range(24))
+def test_fluid_collision_with_forces_relaxes_the_force_corrected_moments(trial):
+    """Sec. 4 with F_t, F_p != 0 (reading R13: h-hat as printed).  The stored g-bar carry
+    sum g-bar = p* and sum g-bar e = rho c_s^2 u - c_s^2 F_t / 2 (Eq. hydrodynamicfields).  Take
+    the moment set whose zeroth and first raw moments are the corrected p = p* + F_p . u / 2 and
+    rho c_s^2 u, and whose higher raw moments are those of g-bar; relaxing its central moments
+    about u (orders >= 2, arbitrary rates) towards the equilibria of the force-free test changes
+    the populations by exactly sum_{j >= 3} K_j h-hat_j.  So the printed h-hat_3..h-hat_8 are
+    the cascaded relaxation of the half-force-corrected moments: a dropped or mis-signed force
+    term in them fails here.  (h-hat_0..h-hat_2 and delta g^s are pinned by the moment-change
+    and projection tests.)"""
+    ux, uy = RNG.uniform(-0.15, 0.15, 2)
+    rho = float(np.exp(RNG.uniform(np.log(1e-3), 0.0)))
+    Ftx, Fty, Fpx, Fpy = RNG.uniform(-1e-3, 1e-3, 4)
+    om = RNG.uniform(0.3, 1.95, 9)
+    pstar = RNG.uniform(-1e-2, 1e-2)
+    r = raw_moments(O.geq(pstar, ux, uy, rho))
+    r[3:] += RNG.uniform(-1e-3, 1e-3, 6)
+    r[0], r[1], r[2] = pstar, rho * C2 * ux - 0.5 * C2 * Ftx, rho * C2 * uy - 0.5 * C2 * Fty
+    g = pops_from_raw(r)
+    p = pstar + 0.5 * (Fpx * ux + Fpy * uy)
+    _, h = O.fluid_collide(g, p, ux, uy, rho, Ftx, Fty, Fpx, Fpy, om)
+    rc = r.copy()
+    rc[0], rc[1], rc[2] = p, rho * C2 * ux, rho * C2 * uy
+    gc = pops_from_raw(rc)
+    psi = p - rho * C2
+    eq = np.array([p, -psi * ux, -psi * uy, p * C2 + psi * ux ** 2, p * C2 + psi * uy ** 2,
+                   psi * ux * uy, -psi * (C2 + ux ** 2) * uy, -psi * (C2 + uy ** 2) * ux,
+                   C2 ** 3 * rho + psi * (ux ** 2 + C2) * (uy ** 2 + C2)])
+    change = relax_central(gc, ux, uy, eq, om) - gc
+    assert np.allclose(change, basis_K()[:, 3:] @ h[3:], rtol=0, atol=1e-15)
+    # the corrected set is already at its first-order equilibrium: relaxation alone moves no
+    # zeroth or first moment, so every such change comes from h-hat_0..2 and delta g^s
+    assert abs(change.sum()) < 1e-16
+    assert abs((change * EX).sum()) < 1e-16 and abs((change * EY).sum()) < 1e-16
+
+
 # ---------------------------------------------------------------------------------------------
 # Stencils
 # ---------------------------------------------------------------------------------------------
