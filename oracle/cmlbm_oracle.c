@@ -53,12 +53,13 @@
  *       field at node positions (x, y) = (i, j) with L0 = nx along x and ny along y, reversed for
  *       time levels t >= reverse_step; the fluid populations are carried unchanged.
  *
- * Parity unpinned: the -grad p* part of F_p (R7, p* of the same time level standing in for the
- * corrected p) rests on the paper's text and that reading alone; no closed form or invariant
- * checks it (a flipped sign changes a translating drop or a decaying vortex by less than their
- * discretisation error).  The c_s^2 (rho_A - rho_B) grad phi part of F_p is pinned by the
- * translating-drop test, the F != 0 terms of the fluid collision (R13) by the test that
- * relaxes the half-force-corrected moments (tests/test_oracle_physics.py, test_oracle_pins.py).
+ * Pins of the force coupling (tests/test_oracle_pins.py, tests/test_oracle_physics.py): the
+ * F != 0 terms of the fluid collision (R13) equal relaxation of the half-force-corrected
+ * moments; the c_s^2 (rho_A - rho_B) grad phi part of F_p keeps a drop in a uniform stream
+ * moving at the stream's speed; the -grad p* part advects p, so a pressure wave in a uniform
+ * stream follows the linear modes of the paper's macroscopic equations.  Not separable by any
+ * test: p* in place of the corrected p inside that gradient (R7); the two differ by
+ * F_p . u / 2, second order in the flow.
  *
  * Layout: a population field is 9 planes [alpha][y][x], plane size nx*ny, row-major in x.
  * Node coordinates are (x, y) = (i, j), i in [0, nx), j in [0, ny).
