@@ -2,7 +2,8 @@
 
 One bench step = one time step of both D2Q9 lattices over the whole grid (one fused kernel
 launch).  Default workload: drop impact on a thin film at density ratio 1000 on a 2048 x 1024
-grid, FP32 populations (the bandwidth headline).  Prints one JSON line.
+grid (the paper's Sec. 6.6 parameters at Re = 100, We = 8000), FP32 populations (the bandwidth
+headline).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload impact|rt|marangoni|laplace] [--precision fp32|fp64]
@@ -57,6 +58,8 @@ def describe(case) -> dict:
     d = {k: case[k] for k in keys}
     d["bc"] = ("wall" if case["wall_x"] else "periodic") + "_x/" + (
         "wall" if case["wall_y"] else "periodic") + "_y"
+    if "name" in case:
+        d["case"] = case["name"]
     return d
 
 

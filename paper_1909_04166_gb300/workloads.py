@@ -132,16 +132,18 @@ def marangoni(nx=512, ny=256, radius=32.0, rho_ratio=10.0, nu_a=0.05, sigma0=1e-
 
 
 def impact(nx=2048, ny=1024, diameter=200.0, film_frac=0.1, gap=0.0, velocity=0.05,
-           reynolds=20.0, weber=8000.0, rho_ratio=1000.0, mu_ratio=10.0, width=5.0,
-           mobility=0.02) -> Case:
+           reynolds=100.0, weber=8000.0, rho_ratio=1000.0, mu_ratio=10.0, width=5.0,
+           mobility=0.1) -> Case:
     """Drop of diameter D moving down at speed U, initially touching a film of thickness
     film_frac D on the bottom wall (periodic x, walls y): mu_A = rho_A U D / Re,
     sigma = rho_A U^2 D / We, mu_B = mu_A / mu_ratio.
 
     The defaults take the paper's own drop-impact parameters (Sec. 6.6: density ratio 1000,
-    viscosity ratio 10, We = 8000, U = 0.05, Re = 2 rho_A U R / mu_A = 20, W = 5) on a
-    2048 x 1024 grid with D = 200 and a film of 0.1 D.  At Re >= 100 with this thin film the
-    run diverges within a few hundred steps (air squeezed out at |u| > 0.3)."""
+    viscosity ratio 10, We = 8000, U = 0.05, W = 5, and the higher of its two Reynolds numbers,
+    Re = 2 rho_A U R / mu_A = 100, the case that forms an ejecta sheet) on a 2048 x 1024 grid
+    with D = 200 and a film of 0.1 D.  The paper gives no mobility for this case: M_phi = 0.1
+    runs stably (0.05 - 0.2 do; 0.02 diverges within 1000 steps at Re = 100).  Re >= 150
+    diverges within 500 steps for every mobility in 0.02 - 0.5 and width 5 - 8."""
     rho_a, rho_b = 1.0, 1.0 / rho_ratio
     mu_a = rho_a * velocity * diameter / reynolds
     sigma = rho_a * velocity ** 2 * diameter / weber
