@@ -89,10 +89,10 @@ def kernel_source_hash() -> str:
 # figures are steady-state launches (caches not flushed between launches, as in the timed run;
 # mean of three consecutive launches).
 NCU_TRAFFIC = {
-    # profiles/step_kernel_impact_2048x1024_fp32.md (read 105.80 MB + write 150.10 MB)
-    ("fa5ca9717bea708e", "impact", "fp32"): 255_901_611,
-    # profiles/step_kernel_impact_2048x1024_fp16.md (read 44.26 MB + write 92.29 MB)
-    ("fa5ca9717bea708e", "impact", "fp16"): 136_555_264,
+    # profiles/step_kernel_impact_2048x1024_fp32.md (read 105.90 MB + write 150.05 MB)
+    ("458350935cd05687", "impact", "fp32"): 255_949_739,
+    # profiles/step_kernel_impact_2048x1024_fp16.md (read 46.05 MB + write 92.33 MB)
+    ("458350935cd05687", "impact", "fp16"): 138_385_835,
 }
 
 
@@ -282,7 +282,8 @@ def run_ours(args):
             "frac": round(achieved / peak, 4), "traffic": traffic,
             "peak_source": f"{peak_kind} HBM copy bandwidth",
             "bytes_per_lu": bpl, "ms_per_launch": round(ms_launch, 5),
-            "kernel": "cmlbm::step_kernel", "kernel_hash": hsh,
+            "kernel": ("cmlbm::step_kernel_narrow" if args.precision in ("fp16", "bf16")
+                       else "cmlbm::step_kernel"), "kernel_hash": hsh,
         },
         "clocks": clk.summary(),
         "e2e": e2e,

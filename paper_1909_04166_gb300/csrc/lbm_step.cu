@@ -340,6 +340,67 @@ __device__ __forceinline__ void push_node_z(const R g[9], const R f[9], const Wi
     }
 }
 
+// Stored values of population a for a lane's two nodes at once (the packed form of encode):
+// d = (v - w_a z) s for both halves with FFMA2 / FMUL2, rounded to 16 bits by one paired
+// conversion.  Same roundings as encode, element by element.
+template <typename S>
+__device__ __forceinline__ void encode_pair(F2 v, F2 z, float w, float scale, S& lo, S& hi)
+{
+    const F2 d = fmad(F2(-w), z, v) * F2(scale);
+    if constexpr (std::is_same<S, __half>::value) {
+        const __half2 h = __float22half2_rn(d.v);
+        lo = __low2half(h);
+        hi = __high2half(h);
+    } else {
+        const __nv_bfloat162 h = __float22bfloat162_rn(d.v);
+        lo = __low2bfloat16(h);
+        hi = __high2bfloat16(h);
+    }
+}
+
+// push_node_z for both nodes of a lane when no node of the warp row touches a wall (the fast
+// path): encodes each population pair once, then stores node A's value if A is active and
+// node B's if B is.  c*A / c*B: column offsets of x - 1, x, x + 1 for the two nodes.
+template <typename S>
+__device__ __forceinline__ void push_pair_z(const F2 g[9], const F2 f[9], const Win<F2>& ps,
+                                            const Win<F2>& ph, S* rS, S* rC, S* rN, int cwA,
+                                            int ccA, int ceA, int cwB, int ccB, int ceB,
+                                            int zcA, int zcB, bool actA, bool actB,
+                                            const Consts<float>& K)
+{
+    if (actA) {
+        float* z = reinterpret_cast<float*>(rC + zcA);
+        z[0] = ps.c.v.x;
+        z[32] = ph.c.v.x;
+    }
+    if (actB) {
+        float* z = reinterpret_cast<float*>(rC + zcB);
+        z[0] = ps.c.v.y;
+        z[32] = ph.c.v.y;
+    }
+    S* pA[9] = {rC + ccA, rC + ceA, rN + ccA, rC + cwA, rS + ccA, rN + ceA, rN + cwA, rS + cwA,
+                rS + ceA};
+    S* pB[9] = {rC + ccB, rC + ceB, rN + ccB, rC + cwB, rS + ccB, rN + ceB, rN + cwB, rS + cwB,
+                rS + ceB};
+    constexpr int EXc[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    constexpr int EYc[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const float w = float(d2q9_w(a));
+        S gA, gB, fA, fB;
+        encode_pair<S>(g[a], win_at(ps, EXc[a], EYc[a]), w, K.st_scale[0], gA, gB);
+        encode_pair<S>(f[a], win_at(ph, EXc[a], EYc[a]), w, K.st_scale[1], fA, fB);
+        if (actA) {
+            pA[a][a * 32] = gA;
+            pA[a][(9 + a) * 32] = fA;
+        }
+        if (actB) {
+            pB[a][a * 32] = gB;
+            pB[a][(9 + a) * 32] = fB;
+        }
+    }
+}
+
 // The march of one warp over one strip x segment of one grid: everything the step does for
 // those nodes.  Used by the single-grid kernel and by the batched kernel.
 template <typename R, typename S, int V>
@@ -811,8 +872,13 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
                 push_node<S, float, SHEAR>(gq, fq, rS, rC, rN, cw, cc, ce, bxw, bxe, bys, byn,
                                            G.slip, fast, K);
         };
-        if (actA) push(false, cwA, ccA, ceA, zcA, bxwA, bxeA);
-        if (actB) push(true, cwB, ccB, ceB, zcB, bxwB, bxeB);
+        if (NARROW && fast) {
+            push_pair_z<S>(g, f, ps, ph, rS, rC, rN, cwA, ccA, ceA, cwB, ccB, ceB, zcA, zcB,
+                           actA, actB, K);
+        } else {
+            if (actA) push(false, cwA, ccA, ceA, zcA, bxwA, bxeA);
+            if (actB) push(true, cwB, ccB, ceB, zcB, bxwB, bxeB);
+        }
         issue(i + NS, st);
         rb = rc;
         rc = rn;
@@ -833,9 +899,9 @@ template <typename R, typename S, int V>
 __host__ __device__ constexpr int tiles_per_warp() { return Paired<R, S, V>::value ? 2 : 1; }
 
 template <typename R, typename S, int V>
-__global__ void __launch_bounds__(256)
-step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R> K,
-            StepLaunch L)
+__device__ __forceinline__ void step_body(const S* __restrict__ src, S* __restrict__ dst,
+                                          const Geometry& G, const Consts<R>& K,
+                                          const StepLaunch& L)
 {
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     constexpr int NT = tiles_per_warp<R, S, V>();
@@ -847,6 +913,40 @@ step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R
         march2<S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign, L.flip);
     else
         march<R, S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign, L.flip);
+}
+
+template <typename R, typename S, int V>
+__global__ void __launch_bounds__(256)
+step_kernel(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R> K,
+            StepLaunch L)
+{
+    step_body<R, S, V>(src, dst, G, K, L);
+}
+
+// The 16-bit forms: at most 256 threads per block, like step_kernel, and at most 168 registers
+// per thread, so that three 128-thread blocks (12 warps, the residency the shared memory allows
+// the FP32 form) fit in the register file.  (Without the cap they take 172 and only 8 warps fit;
+// a cap through __launch_bounds__(128, 3) instead gives slower code, 56.6 against 54.9 us per
+// step on the 2048 x 1024 impact.)
+template <typename S>
+struct NarrowRegs {
+    static constexpr int value = 168;
+};
+
+template <typename R, typename S, int V>
+__global__ void __launch_bounds__(256) __maxnreg__(NarrowRegs<S>::value)
+step_kernel_narrow(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R> K,
+                   StepLaunch L)
+{
+    step_body<R, S, V>(src, dst, G, K, L);
+}
+
+// The step kernel of a form.
+template <typename R, typename S, int V>
+constexpr auto step_kernel_of()
+{
+    if constexpr (Narrow<S>::value) return step_kernel_narrow<R, S, V>;
+    else return step_kernel<R, S, V>;
 }
 
 // One time step of many independent grids in one launch: warp w takes task w = (case, local
@@ -1044,11 +1144,11 @@ int step_warp_strips(int nstrips)
 template <typename R, typename S, int V>
 cudaError_t configure_step(int block)
 {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<R, S, V>,
+    cudaError_t e = cudaFuncSetAttribute(step_kernel_of<R, S, V>(),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)step_smem_bytes<R, S, V>(block));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(step_kernel<R, S, V>,
+    return cudaFuncSetAttribute(step_kernel_of<R, S, V>(),
                                 cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
 }
@@ -1058,7 +1158,7 @@ template <typename R, typename S, int V>
 int step_blocks_per_sm(int block)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<R, S, V>, block,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel_of<R, S, V>(), block,
                                                       step_smem_bytes<R, S, V>(block)) !=
         cudaSuccess)
         return 1;
@@ -1085,7 +1185,7 @@ cudaError_t launch_step(const void* src, void* dst, const Geometry& G, const Con
     const long long warps = (long long)step_warp_strips<R, S, V>(G.nstrips) * L.nseg;
     const int wpb = block / 32;
     const long long grid = (warps + wpb - 1) / wpb;
-    step_kernel<R, S, V><<<(unsigned)grid, block, step_smem_bytes<R, S, V>(block), st>>>(
+    step_kernel_of<R, S, V>()<<<(unsigned)grid, block, step_smem_bytes<R, S, V>(block), st>>>(
         static_cast<const S*>(src), static_cast<S*>(dst), G, K, L);
     return cudaGetLastError();
 }
@@ -1117,7 +1217,7 @@ cudaError_t build_step_graph(const void* a, const void* b, const Geometry& G, co
         L.flip = flip_of(src, dst);
         void* args[] = {(void*)&src, (void*)&dst, (void*)&g, (void*)&k, (void*)&L};
         cudaKernelNodeParams p = {};
-        p.func = (void*)step_kernel<R, S, V>;
+        p.func = (void*)step_kernel_of<R, S, V>();
         p.gridDim = dim3(grid);
         p.blockDim = dim3(block);
         p.sharedMemBytes = (unsigned)step_smem_bytes<R, S, V>(block);
