@@ -953,9 +953,10 @@ constexpr auto step_kernel_of()
 // warp index) from a flattened task list; every case has its own geometry, constants and pair
 // of buffers inside one allocation.  All cases share the buffer parity (they step together).
 template <typename R, typename S>
-__global__ void __launch_bounds__(256)
-batch_step_kernel(S* __restrict__ base, const BatchCase<R>* __restrict__ cases,
-                  const int2* __restrict__ tasks, int ntasks, int parity, int* err)
+__device__ __forceinline__ void batch_body(S* __restrict__ base,
+                                           const BatchCase<R>* __restrict__ cases,
+                                           const int2* __restrict__ tasks, int ntasks,
+                                           int parity, int* err)
 {
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (warp >= ntasks) return;                      // warp-uniform
@@ -970,6 +971,32 @@ batch_step_kernel(S* __restrict__ base, const BatchCase<R>* __restrict__ cases,
     S* dst = base + (parity ? c.off0 : c.off1);
     if constexpr (NT == 2) march2<S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1, parity);
     else march<R, S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1, parity);
+}
+
+template <typename R, typename S>
+__global__ void __launch_bounds__(256)
+batch_step_kernel(S* __restrict__ base, const BatchCase<R>* __restrict__ cases,
+                  const int2* __restrict__ tasks, int ntasks, int parity, int* err)
+{
+    batch_body<R, S>(base, cases, tasks, ntasks, parity, err);
+}
+
+// The batched step of the 16-bit forms, held to 168 registers per thread like
+// step_kernel_narrow (200 without the cap, which leaves 8 warps per SM).
+template <typename R, typename S>
+__global__ void __launch_bounds__(256) __maxnreg__(NarrowRegs<S>::value)
+batch_step_kernel_narrow(S* __restrict__ base, const BatchCase<R>* __restrict__ cases,
+                         const int2* __restrict__ tasks, int ntasks, int parity, int* err)
+{
+    batch_body<R, S>(base, cases, tasks, ntasks, parity, err);
+}
+
+// The batched step kernel of a storage form.
+template <typename R, typename S>
+constexpr auto batch_kernel_of()
+{
+    if constexpr (Narrow<S>::value) return batch_step_kernel_narrow<R, S>;
+    else return batch_step_kernel<R, S>;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1234,11 +1261,11 @@ cudaError_t build_step_graph(const void* a, const void* b, const Geometry& G, co
 template <typename R, typename S>
 cudaError_t configure_batch(int block)
 {
-    cudaError_t e = cudaFuncSetAttribute(batch_step_kernel<R, S>,
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel_of<R, S>(),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)step_smem_bytes<R, S, 0>(block));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(batch_step_kernel<R, S>,
+    return cudaFuncSetAttribute(batch_kernel_of<R, S>(),
                                 cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
 }
@@ -1249,7 +1276,7 @@ cudaError_t launch_batch_step(void* base, const BatchCase<R>* cases, const int2*
 {
     const int wpb = block / 32;
     const unsigned grid = (unsigned)((ntasks + wpb - 1) / wpb);
-    batch_step_kernel<R, S><<<grid, block, step_smem_bytes<R, S, 0>(block), st>>>(
+    batch_kernel_of<R, S>()<<<grid, block, step_smem_bytes<R, S, 0>(block), st>>>(
         static_cast<S*>(base), cases, tasks, ntasks, parity, err);
     return cudaGetLastError();
 }
@@ -1273,7 +1300,7 @@ cudaError_t build_batch_graph(void* base, const BatchCase<R>* cases, const int2*
         void* args[] = {(void*)&b, (void*)&cases, (void*)&tasks, (void*)&n, (void*)&parity,
                         (void*)&err};
         cudaKernelNodeParams p = {};
-        p.func = (void*)batch_step_kernel<R, S>;
+        p.func = (void*)batch_kernel_of<R, S>();
         p.gridDim = dim3(grid);
         p.blockDim = dim3(block);
         p.sharedMemBytes = (unsigned)step_smem_bytes<R, S, 0>(block);
