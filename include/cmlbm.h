@@ -69,6 +69,9 @@ extern "C" {
 #define LBM_ERR_TIMEOUT (-8)    /* a bounded wait inside the step kernel gave up; the state of
                                    that step is invalid (reported by the next synchronising
                                    call or lbm_check) */
+#define LBM_ERR_INDEX (-9)      /* the bounds-checked step kernel (lbm_set_checked) met a load,
+                                   store or copy outside the state buffers and skipped it; the
+                                   state is invalid (reported as LBM_ERR_TIMEOUT is) */
 
 /* Storage / compute precision of a context. */
 typedef enum {
@@ -203,6 +206,16 @@ int lbm_step(lbm_ctx* ctx, int32_t nsteps);
 /* Enable (default) or disable the graph replays of lbm_step; results are identical. */
 int lbm_set_graphs(lbm_ctx* ctx, int32_t enable);
 
+/* Debugging aid standing in for a memory checker: run the following steps through a variant of
+ * the step kernel that checks every global load, store and bulk copy of a step against the
+ * bounds of the source and destination state buffers before doing it.  An access outside is
+ * skipped and recorded; lbm_check (or the next synchronising call) then returns LBM_ERR_INDEX.
+ * The arithmetic is the plain kernel's, so results are bitwise identical when nothing is out
+ * of range; steps run as single launches (no graph replays) and somewhat slower.  Shared-memory
+ * accesses are not checked.  Only the cascaded coupled step with the linear sigma(T) (no step
+ * variant): LBM_ERR_UNSUPPORTED otherwise.  enable = 0 returns to the plain kernel. */
+int lbm_set_checked(lbm_ctx* ctx, int32_t enable);
+
 /* Fields of the current state into host arrays ([ny][nx] doubles): phi, the corrected p, u and
  * rho as defined by Sec. 4 Eq. hydrodynamicfields.  Any pointer may be NULL.  Synchronises. */
 int lbm_get_fields(lbm_ctx* ctx, double* phi, double* p, double* ux, double* uy, double* rho);
@@ -232,7 +245,8 @@ int lbm_load_state(lbm_ctx* ctx, const void* host, size_t bytes, int64_t steps);
 int lbm_state_device(lbm_ctx* ctx, void** state, int32_t* nstrips, int64_t* elements);
 
 /* Synchronise the stream and report LBM_ERR_TIMEOUT if any step since creation gave up on a
- * bounded device wait; LBM_OK otherwise. */
+ * bounded device wait, LBM_ERR_INDEX if a checked step (lbm_set_checked) met an access outside
+ * the state buffers; LBM_OK otherwise. */
 int lbm_check(lbm_ctx* ctx);
 
 /* Diagnostics of the current state; see lbm_diag.  r_in < 0 skips dp_laplace.  Synchronises.

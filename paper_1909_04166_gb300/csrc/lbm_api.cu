@@ -36,6 +36,7 @@ struct lbm_ctx {
     int variant;           // step variant (lbm_host.h step_variant)
     cudaGraphExec_t graph[2][2];   // kGraphChunk steps from buffer 0 / 1, flow sign + / -
     int use_graph;
+    int checked;           // steps run through the bounds-checked kernel (lbm_set_checked)
     int nsm;
     int last_cuda;
 };
@@ -108,6 +109,13 @@ int flow_sign_at(const lbm_ctx* c, long long t)
 
 cudaError_t launch_one(lbm_ctx* c, const void* src, void* dst, int sign)
 {
+    if (c->checked) {
+        return with_variant(c->P.precision, 0, [&](auto r, auto s, auto) {
+            using R = decltype(r);
+            return launch_step_checked<R, decltype(s)>(src, dst, c->G, kref<R>(c), c->seg_h,
+                                                       c->block, c->err, c->st);
+        });
+    }
     return with_variant(c->P.precision, c->variant, [&](auto r, auto s, auto v) {
         using R = decltype(r);
         return launch_step<R, decltype(s), decltype(v)::value>(
@@ -136,6 +144,7 @@ int check_device_error(lbm_ctx* c)
     cudaError_t e = cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_fail(c, e);
+    if (h & 2) return LBM_ERR_INDEX;
     return h ? LBM_ERR_TIMEOUT : LBM_OK;
 }
 
@@ -410,7 +419,7 @@ int lbm_step(lbm_ctx* c, int32_t nsteps)
         if (sign > 0 && c->P.reverse_step > 0)
             run = std::min<long long>(run, c->P.reverse_step - c->steps);
         // whole chunks as replays of a prebuilt graph of kGraphChunk launches
-        while (c->use_graph && run >= kGraphChunk) {
+        while (c->use_graph && !c->checked && run >= kGraphChunk) {
             cudaError_t e = ensure_graph(c, c->cur, sign);
             if (e == cudaSuccess) e = cudaGraphLaunch(c->graph[c->cur][sign < 0 ? 1 : 0], c->st);
             if (e != cudaSuccess) return cuda_fail(c, e);
@@ -434,6 +443,21 @@ int lbm_set_graphs(lbm_ctx* c, int32_t enable)
 {
     if (!c) return LBM_ERR_ARG;
     c->use_graph = enable ? 1 : 0;
+    return LBM_OK;
+}
+
+int lbm_set_checked(lbm_ctx* c, int32_t enable)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (enable && c->variant != 0) return LBM_ERR_UNSUPPORTED;
+    if (enable) {
+        cudaSetDevice(c->P.device);
+        cudaError_t e = with_variant(c->P.precision, 0, [&](auto r, auto s, auto) {
+            return configure_step_checked<decltype(r), decltype(s)>(c->block);
+        });
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    c->checked = enable ? 1 : 0;
     return LBM_OK;
 }
 
@@ -592,6 +616,10 @@ int lbm_set_launch(lbm_ctx* c, int32_t seg_rows, int32_t block_threads)
         c->block = block_threads;
         cudaSetDevice(c->P.device);
         cudaError_t e = configure(c);
+        if (e == cudaSuccess && c->checked)
+            e = with_variant(c->P.precision, 0, [&](auto r, auto s, auto) {
+                return configure_step_checked<decltype(r), decltype(s)>(c->block);
+            });
         if (e != cudaSuccess) return cuda_fail(c, e);
     }
     return LBM_OK;
@@ -632,6 +660,7 @@ const char* lbm_strerror(int s)
     case LBM_ERR_NONFINITE: return "non-finite values in the fields";
     case LBM_ERR_UNSUPPORTED: return "unsupported precision mode";
     case LBM_ERR_TIMEOUT: return "a bounded device wait timed out (state invalid)";
+    case LBM_ERR_INDEX: return "the checked step kernel found an access outside the state buffers";
     default: return "unknown status";
     }
 }

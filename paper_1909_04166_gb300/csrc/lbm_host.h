@@ -27,6 +27,14 @@ int step_warp_strips(int nstrips);
 template <typename R, typename S, int V>
 cudaError_t build_step_graph(const void*, const void*, const Geometry&, const Consts<R>&, int,
                              int, int*, int, int, cudaGraphExec_t*);
+// The bounds-checked step (cascaded coupled form only): every global load, store and bulk copy
+// of a step is range-checked against the two state buffers; an access outside is skipped and
+// the error word gets bit 1 (LBM_ERR_INDEX).
+template <typename R, typename S>
+cudaError_t configure_step_checked(int block);
+template <typename R, typename S>
+cudaError_t launch_step_checked(const void*, void*, const Geometry&, const Consts<R>&, int, int,
+                                int*, cudaStream_t);
 template <typename R, typename S>
 cudaError_t launch_init(const double*, const double*, const double*, const double*, void*,
                         const Geometry&, const Consts<R>&, cudaStream_t);

@@ -219,6 +219,56 @@ __device__ __forceinline__ void ld_pops_t(const S* tile, int lane, const Consts<
     }
 }
 
+// Range checks of a step's global accesses, for the bounds-checked step kernel: halo loads and
+// bulk copies must lie inside the source state buffer, stores inside the destination buffer.
+// An access outside is skipped and bit 1 of the error word is set.  The plain kernels use
+// Bounds<false>, whose checks are constant true and compile to nothing.
+template <bool ON>
+struct Bounds {
+    __device__ __forceinline__ bool rd(const void*, unsigned) const { return true; }
+    __device__ __forceinline__ bool wr(const void*, unsigned) const { return true; }
+};
+template <>
+struct Bounds<true> {
+    uintptr_t src_lo, src_hi, dst_lo, dst_hi;
+    int* err;
+    __device__ __forceinline__ bool in(const void* p, unsigned n, uintptr_t lo,
+                                       uintptr_t hi) const
+    {
+        const uintptr_t q = reinterpret_cast<uintptr_t>(p);
+        if (q >= lo && q <= hi && n <= hi - q) return true;
+        atomicOr(err, 2);
+        return false;
+    }
+    __device__ __forceinline__ bool rd(const void* p, unsigned n) const
+    {
+        return in(p, n, src_lo, src_hi);
+    }
+    __device__ __forceinline__ bool wr(const void* p, unsigned n) const
+    {
+        return in(p, n, dst_lo, dst_hi);
+    }
+};
+template <bool CK, typename S>
+__device__ __forceinline__ Bounds<CK> make_bounds(const S* src, const S* dst, long long elems,
+                                                  int* err)
+{
+    if constexpr (CK) {
+        return Bounds<true>{reinterpret_cast<uintptr_t>(src),
+                            reinterpret_cast<uintptr_t>(src + elems),
+                            reinterpret_cast<uintptr_t>(dst),
+                            reinterpret_cast<uintptr_t>(dst + elems), err};
+    } else {
+        return Bounds<false>{};
+    }
+}
+// Store through a bounds check.
+template <class BND, typename T>
+__device__ __forceinline__ void st_chk(const BND& B, T* p, T v)
+{
+    if (B.wr(p, sizeof(T))) *p = v;
+}
+
 // Value of a window at offset (dx, dy) in {-1, 0, 1}^2.
 template <typename R>
 __device__ __forceinline__ R win_at(const Win<R>& w, int dx, int dy)
@@ -235,18 +285,19 @@ __device__ __forceinline__ R win_at(const Win<R>& w, int dx, int dy)
 // a no-slip wall returns to this node reversed (half-way bounce-back); one crossing only free-slip
 // walls has its normal components reversed and stays on this side of them (specular reflection).
 // bxw / bxe / bys / byn: the node lies next to the west / east / south / north wall.
-template <typename S, typename R, bool F_ONLY>
+template <typename S, typename R, bool F_ONLY, class BND = Bounds<false>>
 __device__ __forceinline__ void push_node(const R g[9], const R f[9], S* rS, S* rC, S* rN, int cw,
                                           int cc, int ce, bool bxw, bool bxe, bool bys,
-                                          bool byn, int slip, bool fast, const Consts<R>& K)
+                                          bool byn, int slip, bool fast, const Consts<R>& K,
+                                          const BND& B = BND())
 {
     S* pc = rC + cc;
     S* p[9] = {pc, rC + ce, rN + cc, rC + cw, rS + cc, rN + ce, rN + cw, rS + cw, rS + ce};
     if (fast) {
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            if (!F_ONLY) p[a][a * 32] = static_cast<S>(g[a]);
-            p[a][(9 + a) * 32] = static_cast<S>(f[a]);
+            if (!F_ONLY) st_chk(B, &p[a][a * 32], static_cast<S>(g[a]));
+            st_chk(B, &p[a][(9 + a) * 32], static_cast<S>(f[a]));
         }
         return;
     }
@@ -272,24 +323,24 @@ __device__ __forceinline__ void push_node(const R g[9], const R f[9], S* rS, S* 
             S* row = cy ? rC : (ey > 0 ? rN : (ey < 0 ? rS : rC));
             q = row + (cx ? cc : (ex > 0 ? ce : (ex < 0 ? cw : cc)));
         }
-        if (!F_ONLY) q[plane * 32] = static_cast<S>(g[a]);
-        q[(9 + plane) * 32] = static_cast<S>(f[a]);
+        if (!F_ONLY) st_chk(B, &q[plane * 32], static_cast<S>(g[a]));
+        st_chk(B, &q[(9 + plane) * 32], static_cast<S>(f[a]));
     }
 }
 
 // As push_node for the 16-bit forms: every population is stored as its deviation from the rest
 // state of the node it lands on, whose zeroth moments are the window values ps (p*) and ph (phi)
 // at the landing offset; the node's own zeroth moments go to its Z planes (element offset zc).
-template <typename S, typename R>
+template <typename S, typename R, class BND = Bounds<false>>
 __device__ __forceinline__ void push_node_z(const R g[9], const R f[9], const Win<R>& ps,
                                             const Win<R>& ph, S* rS, S* rC, S* rN, int cw,
                                             int cc, int ce, int zc, bool bxw, bool bxe,
                                             bool bys, bool byn, int slip, bool fast,
-                                            const Consts<R>& K)
+                                            const Consts<R>& K, const BND& B = BND())
 {
     float* zp = reinterpret_cast<float*>(rC + zc);
-    zp[0] = float(ps.c);
-    zp[32] = float(ph.c);
+    st_chk(B, &zp[0], float(ps.c));
+    st_chk(B, &zp[32], float(ph.c));
     S* pc = rC + cc;
     S* p[9] = {pc, rC + ce, rN + cc, rC + cw, rS + cc, rN + ce, rN + cw, rS + cw, rS + ce};
     constexpr int EXc[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -297,8 +348,9 @@ __device__ __forceinline__ void push_node_z(const R g[9], const R f[9], const Wi
     if (fast) {
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            p[a][a * 32] = encode<S, R>(g[a], win_at(ps, EXc[a], EYc[a]), 0, a, K);
-            p[a][(9 + a) * 32] = encode<S, R>(f[a], win_at(ph, EXc[a], EYc[a]), 1, a, K);
+            st_chk(B, &p[a][a * 32], encode<S, R>(g[a], win_at(ps, EXc[a], EYc[a]), 0, a, K));
+            st_chk(B, &p[a][(9 + a) * 32],
+                   encode<S, R>(f[a], win_at(ph, EXc[a], EYc[a]), 1, a, K));
         }
         return;
     }
@@ -335,8 +387,8 @@ __device__ __forceinline__ void push_node_z(const R g[9], const R f[9], const Wi
             zg = win_at(ps, ex, 0);
             zf = win_at(ph, ex, 0);
         }
-        q[plane * 32] = encode<S, R>(g[a], zg, 0, a, K);
-        q[(9 + plane) * 32] = encode<S, R>(f[a], zf, 1, a, K);
+        st_chk(B, &q[plane * 32], encode<S, R>(g[a], zg, 0, a, K));
+        st_chk(B, &q[(9 + plane) * 32], encode<S, R>(f[a], zf, 1, a, K));
     }
 }
 
@@ -361,22 +413,22 @@ __device__ __forceinline__ void encode_pair(F2 v, F2 z, float w, float scale, S&
 // push_node_z for both nodes of a lane when no node of the warp row touches a wall (the fast
 // path): encodes each population pair once, then stores node A's value if A is active and
 // node B's if B is.  c*A / c*B: column offsets of x - 1, x, x + 1 for the two nodes.
-template <typename S>
+template <typename S, class BND = Bounds<false>>
 __device__ __forceinline__ void push_pair_z(const F2 g[9], const F2 f[9], const Win<F2>& ps,
                                             const Win<F2>& ph, S* rS, S* rC, S* rN, int cwA,
                                             int ccA, int ceA, int cwB, int ccB, int ceB,
                                             int zcA, int zcB, bool actA, bool actB,
-                                            const Consts<float>& K)
+                                            const Consts<float>& K, const BND& B = BND())
 {
     if (actA) {
         float* z = reinterpret_cast<float*>(rC + zcA);
-        z[0] = ps.c.v.x;
-        z[32] = ph.c.v.x;
+        st_chk(B, &z[0], ps.c.v.x);
+        st_chk(B, &z[32], ph.c.v.x);
     }
     if (actB) {
         float* z = reinterpret_cast<float*>(rC + zcB);
-        z[0] = ps.c.v.y;
-        z[32] = ph.c.v.y;
+        st_chk(B, &z[0], ps.c.v.y);
+        st_chk(B, &z[32], ph.c.v.y);
     }
     S* pA[9] = {rC + ccA, rC + ceA, rN + ccA, rC + cwA, rS + ccA, rN + ceA, rN + cwA, rS + cwA,
                 rS + ceA};
@@ -391,19 +443,19 @@ __device__ __forceinline__ void push_pair_z(const F2 g[9], const F2 f[9], const 
         encode_pair<S>(g[a], win_at(ps, EXc[a], EYc[a]), w, K.st_scale[0], gA, gB);
         encode_pair<S>(f[a], win_at(ph, EXc[a], EYc[a]), w, K.st_scale[1], fA, fB);
         if (actA) {
-            pA[a][a * 32] = gA;
-            pA[a][(9 + a) * 32] = fA;
+            st_chk(B, &pA[a][a * 32], gA);
+            st_chk(B, &pA[a][(9 + a) * 32], fA);
         }
         if (actB) {
-            pB[a][a * 32] = gB;
-            pB[a][(9 + a) * 32] = fB;
+            st_chk(B, &pB[a][a * 32], gB);
+            st_chk(B, &pB[a][(9 + a) * 32], fB);
         }
     }
 }
 
 // The march of one warp over one strip x segment of one grid: everything the step does for
 // those nodes.  Used by the single-grid kernel and by the batched kernel.
-template <typename R, typename S, int V>
+template <typename R, typename S, int V, bool CK = false>
 __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__ dst,
                                       const Geometry& G, const Consts<R>& K, int strip, int seg,
                                       int seg_h, int* err, int flow_sign, int flip)
@@ -414,6 +466,7 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     constexpr bool LANGMUIR = (V & kVarLangmuir) != 0;
     constexpr bool NARROW = Narrow<S>::value;
     constexpr int TE = Tile<S>::ELEMS;               // elements per tile
+    const auto B = make_bounds<CK>(src, dst, (long long)G.ny * G.nstrips * TE, err);
     // the interface lattice alone copies only the f half of every tile (planes 9..17)
     constexpr int COPY_OFF = SHEAR ? Tile<S>::P0 + 9 * 32 : 0;
     constexpr uint32_t COPY_BYTES = SHEAR ? 9 * 32 * sizeof(S) : Tile<S>::BYTES;
@@ -459,15 +512,17 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
         const S* rb = row_ptr(src, row_of(k));
         if (hlane) {
             if constexpr (NARROW) {
-                hl = R(narrow_to_f(__ldg(rb + hoffl))) * hinv;
-                hr = R(narrow_to_f(__ldg(rb + hoffr))) * hinv;
+                if (B.rd(rb + hoffl, sizeof(S))) hl = R(narrow_to_f(__ldg(rb + hoffl))) * hinv;
+                if (B.rd(rb + hoffr, sizeof(S))) hr = R(narrow_to_f(__ldg(rb + hoffr))) * hinv;
             } else {
-                hl = R(__ldg(rb + hoffl));
-                hr = R(__ldg(rb + hoffr));
+                if (B.rd(rb + hoffl, sizeof(S))) hl = R(__ldg(rb + hoffl));
+                if (B.rd(rb + hoffr, sizeof(S))) hr = R(__ldg(rb + hoffr));
             }
         } else if (zlane) {
-            hl = R(__ldg(reinterpret_cast<const float*>(rb + hoffl)));
-            hr = R(__ldg(reinterpret_cast<const float*>(rb + hoffr)));
+            const float* zl = reinterpret_cast<const float*>(rb + hoffl);
+            const float* zr = reinterpret_cast<const float*>(rb + hoffr);
+            if (B.rd(zl, sizeof(float))) hl = R(__ldg(zl));
+            if (B.rd(zr, sizeof(float))) hr = R(__ldg(zr));
         }
     };
 
@@ -480,9 +535,10 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
         if (lane == 0) {
             fence_proxy_async();
             const uint32_t bar = bar0 + 8 * st;
-            mbar_expect_tx(bar, COPY_BYTES);
-            bulk_g2s(smem_u32(tiles + st * TE + COPY_OFF),
-                     row_ptr(src, row_of(k)) + strip * TE + COPY_OFF, COPY_BYTES, bar);
+            const S* from = row_ptr(src, row_of(k)) + strip * TE + COPY_OFF;
+            const bool okc = B.rd(from, COPY_BYTES);   // a refused copy only arrives
+            mbar_expect_tx(bar, okc ? COPY_BYTES : 0u);
+            if (okc) bulk_g2s(smem_u32(tiles + st * TE + COPY_OFF), from, COPY_BYTES, bar);
         }
         issued = k;
     };
@@ -564,10 +620,10 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
             const bool fast = !(bys || byn) && !xwall_warp;
             if constexpr (NARROW)
                 push_node_z<S, R>(g, f, ps, ph, rS, rC, rN, cw, cc, ce, zc, bxw, bxe, bys, byn,
-                                  G.slip, fast, K);
+                                  G.slip, fast, K, B);
             else
                 push_node<S, R, SHEAR>(g, f, rS, rC, rN, cw, cc, ce, bxw, bxe, bys, byn,
-                                       G.slip, fast, K);
+                                       G.slip, fast, K, B);
         }
         issue(i + NS, st);      // the tile of row i is consumed: refill its stage
         rb = rc;
@@ -656,7 +712,7 @@ __device__ __forceinline__ Win<float> half_win(const Win<F2>& w, bool b)
     return Win<float>{h(w.sw), h(w.s), h(w.se), h(w.w), h(w.c), h(w.e), h(w.nw), h(w.n), h(w.ne)};
 }
 
-template <typename S, int V>
+template <typename S, int V, bool CK = false>
 __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict__ dst,
                                        const Geometry& G, const Consts<float>& K, int wstrip,
                                        int seg, int seg_h, int* err, int flow_sign, int flip)
@@ -668,6 +724,7 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
     static_assert(!(SHEAR && Narrow<S>::value), "the imposed flow runs in FP32 storage");
     constexpr bool NARROW = Narrow<S>::value;
     constexpr int TE = Tile<S>::ELEMS;               // elements per tile
+    const auto B = make_bounds<CK>(src, dst, (long long)G.ny * G.nstrips * TE, err);
     constexpr int STAGE = 2 * TE;                    // elements per stage (two tiles)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -714,11 +771,13 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
         hr = 0.0f;
         const S* rb = row_ptr(src, row_of(k));
         if (hlane) {
-            hl = narrow_to_f_or_self(__ldg(rb + hoffl)) * hinv;
-            hr = narrow_to_f_or_self(__ldg(rb + hoffr)) * hinv;
+            if (B.rd(rb + hoffl, sizeof(S))) hl = narrow_to_f_or_self(__ldg(rb + hoffl)) * hinv;
+            if (B.rd(rb + hoffr, sizeof(S))) hr = narrow_to_f_or_self(__ldg(rb + hoffr)) * hinv;
         } else if (zlane) {
-            hl = __ldg(reinterpret_cast<const float*>(rb + hoffl));
-            hr = __ldg(reinterpret_cast<const float*>(rb + hoffr));
+            const float* zl = reinterpret_cast<const float*>(rb + hoffl);
+            const float* zr = reinterpret_cast<const float*>(rb + hoffr);
+            if (B.rd(zl, sizeof(float))) hl = __ldg(zl);
+            if (B.rd(zr, sizeof(float))) hr = __ldg(zr);
         }
     };
 
@@ -732,16 +791,20 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
         if (lane == 0) {
             fence_proxy_async();
             const uint32_t bar = bar0 + 8 * st;
-            mbar_expect_tx(bar, copy_bytes);
             const S* rowk = row_ptr(src, row_of(k)) + t0 * TE;
             if constexpr (SHEAR) {
                 constexpr int FOFF = 9 * 32;
                 constexpr uint32_t FB = 9 * 32 * sizeof(S);
-                bulk_g2s(smem_u32(tiles + st * STAGE + FOFF), rowk + FOFF, FB, bar);
-                if (nt == 2)
+                const bool ok0 = B.rd(rowk + FOFF, FB);   // a refused copy only arrives
+                const bool ok1 = nt == 2 && B.rd(rowk + TE + FOFF, FB);
+                mbar_expect_tx(bar, (ok0 ? FB : 0u) + (ok1 ? FB : 0u));
+                if (ok0) bulk_g2s(smem_u32(tiles + st * STAGE + FOFF), rowk + FOFF, FB, bar);
+                if (ok1)
                     bulk_g2s(smem_u32(tiles + st * STAGE + TE + FOFF), rowk + TE + FOFF, FB, bar);
             } else {
-                bulk_g2s(smem_u32(tiles + st * STAGE), rowk, copy_bytes, bar);
+                const bool okc = B.rd(rowk, copy_bytes);
+                mbar_expect_tx(bar, okc ? copy_bytes : 0u);
+                if (okc) bulk_g2s(smem_u32(tiles + st * STAGE), rowk, copy_bytes, bar);
             }
         }
         issued = k;
@@ -867,14 +930,14 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
             }
             if constexpr (NARROW)
                 push_node_z<S, float>(gq, fq, half_win(ps, b), half_win(ph, b), rS, rC, rN, cw,
-                                      cc, ce, zc, bxw, bxe, bys, byn, G.slip, fast, K);
+                                      cc, ce, zc, bxw, bxe, bys, byn, G.slip, fast, K, B);
             else
                 push_node<S, float, SHEAR>(gq, fq, rS, rC, rN, cw, cc, ce, bxw, bxe, bys, byn,
-                                           G.slip, fast, K);
+                                           G.slip, fast, K, B);
         };
         if (NARROW && fast) {
             push_pair_z<S>(g, f, ps, ph, rS, rC, rN, cwA, ccA, ceA, cwB, ccB, ceB, zcA, zcB,
-                           actA, actB, K);
+                           actA, actB, K, B);
         } else {
             if (actA) push(false, cwA, ccA, ceA, zcA, bxwA, bxeA);
             if (actB) push(true, cwB, ccB, ceB, zcB, bxwB, bxeB);
@@ -898,7 +961,7 @@ struct Paired {
 template <typename R, typename S, int V>
 __host__ __device__ constexpr int tiles_per_warp() { return Paired<R, S, V>::value ? 2 : 1; }
 
-template <typename R, typename S, int V>
+template <typename R, typename S, int V, bool CK = false>
 __device__ __forceinline__ void step_body(const S* __restrict__ src, S* __restrict__ dst,
                                           const Geometry& G, const Consts<R>& K,
                                           const StepLaunch& L)
@@ -910,9 +973,9 @@ __device__ __forceinline__ void step_body(const S* __restrict__ src, S* __restri
     const int seg = warp / wstrips;
     if (seg >= L.nseg) return;                       // warp-uniform
     if constexpr (NT == 2)
-        march2<S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign, L.flip);
+        march2<S, V, CK>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign, L.flip);
     else
-        march<R, S, V>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign, L.flip);
+        march<R, S, V, CK>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign, L.flip);
 }
 
 template <typename R, typename S, int V>
@@ -939,6 +1002,15 @@ step_kernel_narrow(const S* __restrict__ src, S* __restrict__ dst, Geometry G, C
                    StepLaunch L)
 {
     step_body<R, S, V>(src, dst, G, K, L);
+}
+
+// The bounds-checked step (a debugging aid: see Bounds); same arithmetic, same results.
+template <typename R, typename S, int V>
+__global__ void __launch_bounds__(256)
+step_kernel_checked(const S* __restrict__ src, S* __restrict__ dst, Geometry G, Consts<R> K,
+                    StepLaunch L)
+{
+    step_body<R, S, V, true>(src, dst, G, K, L);
 }
 
 // The step kernel of a form.
@@ -1217,6 +1289,35 @@ cudaError_t launch_step(const void* src, void* dst, const Geometry& G, const Con
     return cudaGetLastError();
 }
 
+// The bounds-checked step of the coupled cascaded form (variant 0): configuration and launch,
+// as configure_step / launch_step.
+template <typename R, typename S>
+cudaError_t configure_step_checked(int block)
+{
+    return cudaFuncSetAttribute(step_kernel_checked<R, S, 0>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)step_smem_bytes<R, S, 0>(block));
+}
+
+template <typename R, typename S>
+cudaError_t launch_step_checked(const void* src, void* dst, const Geometry& G,
+                                const Consts<R>& K, int seg_h, int block, int* err,
+                                cudaStream_t st)
+{
+    StepLaunch L = {};
+    L.seg_h = seg_h;
+    L.nseg = (G.ny + seg_h - 1) / seg_h;
+    L.err = err;
+    L.flow_sign = 1;
+    L.flip = flip_of(src, dst);
+    const long long warps = (long long)step_warp_strips<R, S, 0>(G.nstrips) * L.nseg;
+    const int wpb = block / 32;
+    const long long grid = (warps + wpb - 1) / wpb;
+    step_kernel_checked<R, S, 0><<<(unsigned)grid, block, step_smem_bytes<R, S, 0>(block), st>>>(
+        static_cast<const S*>(src), static_cast<S*>(dst), G, K, L);
+    return cudaGetLastError();
+}
+
 // A graph of `chunk` (even) consecutive steps starting from buffer `a` (a -> b -> a -> ...),
 // replayed by lbm_step to cut the per-launch gaps between steps.
 template <typename R, typename S, int V>
@@ -1367,6 +1468,10 @@ cudaError_t launch_unpack(const double* in, void* state, const Geometry& G, cons
                                               cudaStream_t);
 
 #define CMLBM_INSTANTIATE(R, S)                                                                   \
+    template cudaError_t configure_step_checked<R, S>(int);                                     \
+    template cudaError_t launch_step_checked<R, S>(const void*, void*, const Geometry&,         \
+                                                   const Consts<R>&, int, int, int*,            \
+                                                   cudaStream_t);                               \
     template cudaError_t configure_batch<R, S>(int);                                            \
     template cudaError_t build_batch_graph<R, S>(void*, const BatchCase<R>*, const int2*, int,  \
                                                  int, int, int*, int, cudaGraphExec_t*);        \

@@ -24,6 +24,7 @@ LBM_ERR_STATE = -5
 LBM_ERR_NONFINITE = -6
 LBM_ERR_UNSUPPORTED = -7
 LBM_ERR_TIMEOUT = -8
+LBM_ERR_INDEX = -9
 
 LBM_FP64 = 0
 LBM_FP32 = 1
@@ -47,7 +48,7 @@ EXPORTS = [
     "lbm_set_populations", "lbm_save_state", "lbm_load_state", "lbm_state_device",
     "lbm_diagnostics", "lbm_set_launch",
     "lbm_get_launch", "lbm_steps_done", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error",
-    "lbm_check", "lbm_set_graphs", "lbm_diagnostics_noalloc",
+    "lbm_check", "lbm_set_graphs", "lbm_set_checked", "lbm_diagnostics_noalloc",
     "lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_get_fields",
     "lbm_batch_get_populations", "lbm_batch_set_launch", "lbm_batch_get_launch",
     "lbm_batch_tune", "lbm_batch_nodes", "lbm_batch_check", "lbm_batch_destroy",
@@ -133,6 +134,7 @@ def lib(build_if_missing: bool = True):
     L.lbm_last_cuda_error.argtypes = [vp]
     L.lbm_check.argtypes = [vp]
     L.lbm_set_graphs.argtypes = [vp, i32]
+    L.lbm_set_checked.argtypes = [vp, i32]
     dd = ctypes.c_double
     L.lbm_diagnostics_noalloc.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, dd, dd, dd, dd,
                                           vp, vp]
@@ -278,6 +280,10 @@ def lbm_diagnostics_noalloc(phi_ptr: int, p_ptr: int, ux_ptr: int, uy_ptr: int, 
 
 def lbm_set_graphs(ctx, enable: bool) -> None:
     _check(lib().lbm_set_graphs(ctx, int(bool(enable))), "lbm_set_graphs")
+
+
+def lbm_set_checked(ctx, enable: bool) -> None:
+    _check(lib().lbm_set_checked(ctx, int(bool(enable))), "lbm_set_checked")
 
 
 def lbm_check(ctx) -> None:
