@@ -4,16 +4,19 @@
 // State layout ("tiled SoA"): for every row y and every strip of 32 columns, the 18 planes
 // (9 fluid g-bar, then 9 interface f) of those 32 nodes are contiguous: element (a, x, y) sits
 // at ((y * nstrips + x / 32) * 18 + a) * 32 + x % 32.  One warp-row tile is 18 * 32 elements
-// (2304 bytes in FP32), a single contiguous block.
+// (2304 bytes in FP32), a single contiguous block.  The 16-bit forms prefix each tile with two
+// FP32 planes of zeroth moments (see lbm_device.cuh).
 //
 // Step kernel (one launch = one time step of both lattices over the whole grid):
-//   * Each warp owns one strip of 32 columns and one segment of rows and marches along the rows
-//     (segments alternate direction so that neighbours read a shared boundary row at about the
-//     same time and the re-read hits L2; every segment also reverses its direction from one
-//     step to the next, so that a step starts on the rows the previous one wrote last, many of
-//     which are still in L2).  Lane l owns column x0 + l.
-//   * Tiles are staged in shared memory by bulk asynchronous copies (cp.async.bulk, one 2304-byte
-//     copy per warp-row, completion on an mbarrier), S stages deep: while row i is collided,
+//   * Each warp owns a strip of columns and a segment of rows and marches along the rows.  With
+//     FP32 arithmetic (march2) the strip is two adjacent tiles and lane l owns columns x0 + l
+//     and x0 + 32 + l, updated together on the packed FP32x2 instructions; in FP64 (march) the
+//     strip is one tile and lane l owns column x0 + l.  Segments alternate direction so that
+//     neighbours read a shared boundary row at about the same time and the re-read hits L2;
+//     every segment also reverses its direction from one step to the next, so that a step
+//     starts on the rows the previous one wrote last, many of which are still in L2.
+//   * The tiles of a row are staged in shared memory by bulk asynchronous copies
+//     (cp.async.bulk, completion on an mbarrier), S stages deep: while row i is collided,
 //     rows i+2 .. i+S-1 are in flight.
 //   * phi = sum f and p* = sum g-bar form a rolling 3x3 window in registers: east/west
 //     neighbours by warp shuffles; the two halo columns of the strip by one load per lane
@@ -21,10 +24,14 @@
 //     prefetched one row ahead.
 //   * Row y is updated once its upper and lower rows' (phi, p*) are known: stencils, forces,
 //     corrected p and u, both cascaded collisions in registers, then the 18 post-collision
-//     populations are pushed to x + e_a in the other buffer (half-way bounce-back at walls).
-//     The state therefore always holds streamed (pre-collision) populations.
+//     populations are pushed to x + e_a in the other buffer (half-way bounce-back or specular
+//     reflection at walls).  The state therefore always holds streamed (pre-collision)
+//     populations.
 //   * Every mbarrier wait is bounded; on timeout the warp records an error code, waits (again
 //     bounded) for its copies in flight and returns.
+//   * Kernels: step_kernel (FP32 / FP64 storage), step_kernel_narrow (16-bit storage, held to
+//     168 registers), step_kernel_checked (every global access range-checked, for debugging),
+//     batch_step_kernel / batch_step_kernel_narrow (many grids per launch).
 #include "lbm_device.cuh"
 
 #include <type_traits>
