@@ -89,10 +89,10 @@ def kernel_source_hash() -> str:
 # figures are steady-state launches (caches not flushed between launches, as in the timed run;
 # mean of three consecutive launches).
 NCU_TRAFFIC = {
-    # profiles/step_kernel_impact_2048x1024_fp32.md (read 105.78 MB + write 149.93 MB)
-    ("0004eff92e0622a7", "impact", "fp32"): 255_716_352,
-    # profiles/step_kernel_impact_2048x1024_fp16.md (read 46.07 MB + write 92.40 MB)
-    ("0004eff92e0622a7", "impact", "fp16"): 138_463_488,
+    # profiles/step_kernel_impact_2048x1024_fp32.md (read 106.09 MB + write 149.77 MB)
+    ("3969cb5ef703aa49", "impact", "fp32"): 255_855_616,
+    # profiles/step_kernel_impact_2048x1024_fp16.md (read 46.23 MB + write 92.29 MB)
+    ("3969cb5ef703aa49", "impact", "fp16"): 138_528_853,
 }
 
 
