@@ -200,3 +200,25 @@ def test_pressure_wave_in_a_uniform_stream_follows_the_linear_modes(U):
         pred = a_plus * np.exp(-1j * w_plus * t) + a_minus * np.exp(-1j * w_minus * t)
         assert abs(np.angle(a / pred)) < 0.05, (t, np.angle(a / pred))
         assert 0.85 < abs(a) / abs(pred) <= 1.0   # viscous and bulk damping only
+
+
+@pytest.mark.parametrize("rho_ref", [0.0, 0.25])
+def test_uniform_body_force_accelerates_at_the_closed_form(rho_ref):
+    """One phase in a periodic box under F = (rho - rho_ref) g (Sec. 3): nothing varies in
+    space, so every node's momentum grows by F per step and the corrected velocity of Sec. 4
+    Eq. hydrodynamicfields, (sum g-bar e + c_s^2 F / 2) / (rho c_s^2), is (n + 1/2) F / rho
+    after n steps, with the pressure uniform; a uniform stream with no force stays as it is."""
+    n, nx, ny, g = 60, 12, 10, 2e-5
+    oc = O.OracleCase(nx=nx, ny=ny, rho_a=1.0, rho_b=0.1, mu_a=0.05, mu_b=0.005,
+                      sigma0=1e-3, gx=0.3 * g, gy=-g, rho_ref=rho_ref)
+    ones, zeros = np.ones((ny, nx)), np.zeros((ny, nx))
+    g0, f0 = O.init(oc, ones, zeros, zeros, zeros)
+    fl = O.fields(oc, *O.run(oc, g0, f0, n))
+    F = (1.0 - rho_ref) * np.array([0.3 * g, -g])
+    assert np.allclose(fl["ux"], (n + 0.5) * F[0], rtol=1e-12, atol=0)
+    assert np.allclose(fl["uy"], (n + 0.5) * F[1], rtol=1e-12, atol=0)
+    assert np.ptp(fl["p"]) <= 1e-15 and np.abs(fl["phi"] - 1.0).max() <= 1e-14
+    oc2 = O.OracleCase(nx=nx, ny=ny, rho_a=1.0, rho_b=0.1, mu_a=0.05, mu_b=0.005)
+    g1, f1 = O.init(oc2, ones, zeros, np.full((ny, nx), 0.07), np.full((ny, nx), -0.02))
+    g2, f2 = O.run(oc2, g1, f1, n)
+    assert np.allclose(g2, g1, rtol=0, atol=1e-16) and np.allclose(f2, f1, rtol=0, atol=1e-16)
