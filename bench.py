@@ -358,8 +358,49 @@ def measure_ensemble(steps, per_case_steps, precision="fp32", device=0, stream=0
                     "per_case_steps": per_case_steps,
                     "per_case_launches_per_step": len(cases)})
         out["batched_over_per_case"] = round(out["batched_mlups"] / out["per_case_mlups"], 2)
+    out["rel_l2_vs_fp64"] = ensemble_accuracy(cases, precision, device, stream)
     return out
 
+
+def ensemble_accuracy(cases, precision, device=0, stream=0, nsteps=20, nsample=8):
+    """Largest relative L2 (phi, p, u) over 8 sampled cases of the batch after nsteps batched
+    steps, against each case run alone in the FP64 mode (itself pinned to the oracle in the
+    tests), next to the same cases' conditioning floor: the largest deviation of an FP64 run
+    whose initial populations carry relative noise of nsteps unit roundoffs of the storage
+    precision.  Some drops (small boxes, large sigma, density ratios up to 1000, a random
+    velocity field) amplify any rounding difference a thousandfold within 20 steps, so the
+    deviation means something only next to that floor."""
+    from paper_1909_04166_gb300 import lbm
+    unit = {"fp32": 2.0 ** -24, "fp16": 2.0 ** -11, "bf16": 2.0 ** -8, "fp64": 2.0 ** -53}
+    idx = [int(i) for i in np.linspace(0, len(cases) - 1, nsample)]
+    with lbm.Batch(cases, precision=precision, device=device, stream=stream) as b:
+        b.init_all()
+        b.step(nsteps)
+        got = {i: b.fields(i) for i in idx}
+    keys = ("phi", "p", "ux", "uy")
+    dev = dict.fromkeys(keys, 0.0)
+    floor = dict.fromkeys(keys, 0.0)
+    rng = np.random.default_rng(5)
+
+    def rel(a, b):
+        nb = np.linalg.norm(b)
+        return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+    for i in idx:
+        with lbm.Simulation(cases[i], precision="fp64", device=device, stream=stream) as s:
+            s.init_case()
+            g0, f0 = s.populations()
+            ref = s.step(nsteps).fields()
+            eps = nsteps * unit[precision]
+            s.set_populations(g0 * (1 + eps * rng.standard_normal(g0.shape)),
+                              f0 * (1 + eps * rng.standard_normal(f0.shape)))
+            pert = s.step(nsteps).fields()
+        for k in keys:
+            dev[k] = max(dev[k], rel(got[i][k], ref[k]))
+            floor[k] = max(floor[k], rel(pert[k], ref[k]))
+    return {"cases": idx, "steps": nsteps,
+            "max_rel_l2": {k: float(f"{v:.3g}") for k, v in dev.items()},
+            "fp64_perturbed_floor": {k: float(f"{v:.3g}") for k, v in floor.items()}}
 
 def measure_storage(case, steps, device=0, stream=0):
     """FP32 and 16-bit storage forms of the same workload: MLUPS, and relative L2 of the fields
