@@ -2,6 +2,12 @@
 
 * ``e1``  circular interface in the imposed reversing shear flow (Sec. 6.1): shape error when it
   returns at 2 T_f, and the phase-mass drift.
+* ``e4``  drop falling under gravity (Sec. 6.4, density ratio 5, Eo = 43): the drop's extent
+  (width and height of phi > 1/2) and centroid at the paper's three Ohnesorge numbers; the
+  paper finds less deformation at larger Oh and a bag with side tails at Oh = 0.3.
+* ``e5``  bubble rising at density ratio 1000 and viscosity ratio 100 (Sec. 6.5, Re = 35): the
+  bubble's extent and centroid at Eo = 10, 50, 125; the paper finds a flattened cap at low Eo
+  and an elongating skirt with tails as Eo grows.
 * ``e6``  drop impact on a thin film at density ratio 1000 (Sec. 6.6): the outcome at the
   paper's two Reynolds numbers, deposition at Re = 20 and an ejecta sheet at Re = 100, read
   off the height that liquid (phi > 1/2) reaches above the film outside the drop's footprint.
@@ -14,7 +20,7 @@
   stably, for the cascaded and the single-relaxation-time operators at density ratios 500, 600,
   800 and 900, on a grid of quarter decades in nu.
 
-``python -m paper_1909_04166_gb300.experiments [e1|e6|e7|e8|all]`` prints one JSON line each.
+``python -m paper_1909_04166_gb300.experiments [e1|e4|e5|e6|e7|e8|all]`` prints one JSON line each.
 """
 from __future__ import annotations
 
@@ -86,6 +92,51 @@ def e7(sens=(0.0048, 0.0146, 0.0244), steps=100000, sample=1000, precision="fp32
             "v_centroid_second_half": float((ys[-1] - ys[len(ys) // 2]) /
                                             (sample * (len(ys) - 1 - len(ys) // 2))),
         })
+    return out
+
+
+def _extent(phi):
+    """Width and height of the region phi > 1/2, and its phi-weighted centroid height."""
+    inside = phi > 0.5
+    if not inside.any():
+        return {"width": 0, "height": 0, "yc": float("nan")}
+    rows, cols = np.nonzero(inside)
+    y = np.arange(phi.shape[0], dtype=float)[:, None]
+    return {"width": int(cols.max() - cols.min() + 1), "height": int(rows.max() - rows.min() + 1),
+            "yc": round(float((phi * y).sum() / phi.sum()), 2)}
+
+
+def _shape_history(case, steps, sample, precision, of_phase_b=False):
+    rows = []
+    with lbm.Simulation(case, precision=precision) as sim:
+        sim.init_case()
+        for k in range(steps // sample):
+            sim.step(sample)
+            phi = sim.fields()["phi"]
+            rows.append({"t": (k + 1) * sample, **_extent(1.0 - phi if of_phase_b else phi)})
+    return rows
+
+
+def e4(ohnesorge=(0.3, 0.7, 1.0), steps=8000, sample=2000, precision="fp32") -> dict:
+    """151 x 451, D = 30 at (75, 300), free-slip top and bottom, periodic sides, sigma = 1e-3
+    (sets the scale; the time unit sqrt(D/g) is 709 steps)."""
+    out = {"experiment": "e4 falling drop (Sec. 6.4)", "steps": steps, "precision": precision,
+           "time_unit_steps": 709, "cases": []}
+    for oh in ohnesorge:
+        out["cases"].append({"Oh": oh, "history": _shape_history(W.falling_drop(ohnesorge=oh),
+                                                                 steps, sample, precision)})
+    return out
+
+
+def e5(eotvos=(10.0, 50.0, 125.0), steps=9600, sample=1600, precision="fp32") -> dict:
+    """161 x 481, D = 64, density ratio 1000, viscosity ratio 100, Re = 35, W = 5, U_g = 0.02
+    (the time unit D / U_g is 3200 steps, so 9600 steps are t* = 3)."""
+    out = {"experiment": "e5 rising bubble (Sec. 6.5)", "steps": steps, "precision": precision,
+           "time_unit_steps": 3200, "cases": []}
+    for eo in eotvos:
+        case = W.rising_bubble(rho_ratio=1000.0, mu_ratio=100.0, eotvos=eo, width=5.0)
+        out["cases"].append({"Eo": eo, "history": _shape_history(case, steps, sample, precision,
+                                                                 of_phase_b=True)})
     return out
 
 
@@ -175,7 +226,7 @@ def e8(ratios=(500.0, 600.0, 800.0, 900.0), steps=50000, check=2000, umax=0.1, n
 
 def main(argv=None):
     which = (argv or sys.argv[1:] or ["all"])[0]
-    for name, fn in (("e1", e1), ("e6", e6), ("e7", e7), ("e8", e8)):
+    for name, fn in (("e1", e1), ("e4", e4), ("e5", e5), ("e6", e6), ("e7", e7), ("e8", e8)):
         if which in (name, "all"):
             print(json.dumps(fn()), flush=True)
 
