@@ -2,6 +2,8 @@
 
 * ``e1``  circular interface in the imposed reversing shear flow (Sec. 6.1): shape error when it
   returns at 2 T_f, and the phase-mass drift.
+* ``e3``  Rayleigh-Taylor instability (Sec. 6.3, Atwood 0.5, Re = 3000, 256 x 1024): positions
+  of the bubble front and the spike tip against time.
 * ``e4``  drop falling under gravity (Sec. 6.4, density ratio 5, Eo = 43): the drop's extent
   (width and height of phi > 1/2) and centroid at the paper's three Ohnesorge numbers; the
   paper finds less deformation at larger Oh and a bag with side tails at Oh = 0.3.
@@ -20,7 +22,7 @@
   stably, for the cascaded and the single-relaxation-time operators at density ratios 500, 600,
   800 and 900, on a grid of quarter decades in nu.
 
-``python -m paper_1909_04166_gb300.experiments [e1|e4|e5|e6|e7|e8|all]`` prints one JSON line each.
+``python -m paper_1909_04166_gb300.experiments [e1|e3|e4|e5|e6|e7|e8|all]`` prints one JSON line each.
 """
 from __future__ import annotations
 
@@ -115,6 +117,28 @@ def _shape_history(case, steps, sample, precision, of_phase_b=False):
             phi = sim.fields()["phi"]
             rows.append({"t": (k + 1) * sample, **_extent(1.0 - phi if of_phase_b else phi)})
     return rows
+
+
+def e3(steps=20000, sample=1600, precision="fp32") -> dict:
+    """Heavy fluid over light, interface ny/2 + 0.1 nx cos(2 pi x / nx): the light fluid rises
+    as a bubble at x = 0 and the heavy one falls as a spike at x = nx/2.  Positions relative to
+    the initial mean interface in units of nx, time t* = t sqrt(g / nx) (6400 steps)."""
+    case = W.rt()
+    nx, ny = case["nx"], case["ny"]
+    rows = []
+    with lbm.Simulation(case, precision=precision) as sim:
+        sim.init_case()
+        for k in range(steps // sample):
+            sim.step(sample)
+            phi = sim.fields()["phi"]
+            light_at_0 = np.nonzero(phi[:, 0] < 0.5)[0]
+            heavy_at_mid = np.nonzero(phi[:, nx // 2] > 0.5)[0]
+            t = (k + 1) * sample
+            rows.append({"t": t, "t_star": round(t / 6400.0, 3),
+                         "bubble": round((light_at_0.max() - ny / 2) / nx, 3),
+                         "spike": round((heavy_at_mid.min() - ny / 2) / nx, 3)})
+    return {"experiment": "e3 Rayleigh-Taylor instability (Sec. 6.3)", "steps": steps,
+            "precision": precision, "history": rows}
 
 
 def e4(ohnesorge=(0.3, 0.7, 1.0), steps=8000, sample=2000, precision="fp32") -> dict:
@@ -226,7 +250,8 @@ def e8(ratios=(500.0, 600.0, 800.0, 900.0), steps=50000, check=2000, umax=0.1, n
 
 def main(argv=None):
     which = (argv or sys.argv[1:] or ["all"])[0]
-    for name, fn in (("e1", e1), ("e4", e4), ("e5", e5), ("e6", e6), ("e7", e7), ("e8", e8)):
+    for name, fn in (("e1", e1), ("e3", e3), ("e4", e4), ("e5", e5), ("e6", e6), ("e7", e7),
+                     ("e8", e8)):
         if which in (name, "all"):
             print(json.dumps(fn()), flush=True)
 
