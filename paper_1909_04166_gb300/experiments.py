@@ -1,4 +1,5 @@
-"""The paper's experiments for the step's further forms, run on the GPU through the C ABI.
+"""The paper's experiments (Secs. 6.1 and 6.3 - 7), run on the GPU through the C ABI.  (The
+Laplace law of Sec. 6.2 is checked on the FP64 oracle in the tests.)
 
 * ``e1``  circular interface in the imposed reversing shear flow (Sec. 6.1): shape error when it
   returns at 2 T_f, and the phase-mass drift.
@@ -22,7 +23,8 @@
   stably, for the cascaded and the single-relaxation-time operators at density ratios 500, 600,
   800 and 900, on a grid of quarter decades in nu.
 
-``python -m paper_1909_04166_gb300.experiments [e1|e3|e4|e5|e6|e7|e8|all]`` prints one JSON line each.
+``python -m paper_1909_04166_gb300.experiments [e1|e3|e4|e5|e6|e7|e8|all]`` prints one JSON
+line each.
 """
 from __future__ import annotations
 
