@@ -214,7 +214,10 @@ int lbm_set_graphs(lbm_ctx* ctx, int32_t enable);
  * of range; steps run as single launches (no graph replays), about a third slower (78 against
  * 59 us per step on the 2048 x 1024 drop impact, FP32).  Shared-memory
  * accesses are not checked.  Only the cascaded coupled step with the linear sigma(T) (no step
- * variant): LBM_ERR_UNSUPPORTED otherwise.  enable = 0 returns to the plain kernel. */
+ * variant): LBM_ERR_UNSUPPORTED otherwise.  enable = 0 returns to the plain kernel.
+ * enable = 2 is a self-test of the checker: the declared bounds of both buffers leave out
+ * their last row (memory that is allocated, so nothing stray happens), every access there is
+ * reported, and the step's results are invalid.  Other values: LBM_ERR_ARG. */
 int lbm_set_checked(lbm_ctx* ctx, int32_t enable);
 
 /* Fields of the current state into host arrays ([ny][nx] doubles): phi, the corrected p, u and

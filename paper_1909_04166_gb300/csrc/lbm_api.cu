@@ -113,7 +113,8 @@ cudaError_t launch_one(lbm_ctx* c, const void* src, void* dst, int sign)
         return with_variant(c->P.precision, 0, [&](auto r, auto s, auto) {
             using R = decltype(r);
             return launch_step_checked<R, decltype(s)>(src, dst, c->G, kref<R>(c), c->seg_h,
-                                                       c->block, c->err, c->st);
+                                                       c->block, c->err,
+                                                       c->checked == 2 ? 1 : 0, c->st);
         });
     }
     return with_variant(c->P.precision, c->variant, [&](auto r, auto s, auto v) {
@@ -448,7 +449,7 @@ int lbm_set_graphs(lbm_ctx* c, int32_t enable)
 
 int lbm_set_checked(lbm_ctx* c, int32_t enable)
 {
-    if (!c) return LBM_ERR_ARG;
+    if (!c || enable < 0 || enable > 2) return LBM_ERR_ARG;
     if (enable && c->variant != 0) return LBM_ERR_UNSUPPORTED;
     if (enable) {
         cudaSetDevice(c->P.device);
@@ -457,7 +458,7 @@ int lbm_set_checked(lbm_ctx* c, int32_t enable)
         });
         if (e != cudaSuccess) return cuda_fail(c, e);
     }
-    c->checked = enable ? 1 : 0;
+    c->checked = enable;
     return LBM_OK;
 }
 

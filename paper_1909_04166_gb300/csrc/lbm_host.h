@@ -34,7 +34,7 @@ template <typename R, typename S>
 cudaError_t configure_step_checked(int block);
 template <typename R, typename S>
 cudaError_t launch_step_checked(const void*, void*, const Geometry&, const Consts<R>&, int, int,
-                                int*, cudaStream_t);
+                                int*, int shrink_rows, cudaStream_t);
 template <typename R, typename S>
 cudaError_t launch_init(const double*, const double*, const double*, const double*, void*,
                         const Geometry&, const Consts<R>&, cudaStream_t);

@@ -48,6 +48,7 @@ struct StepLaunch {
     int* err;      // device error word (0 = ok)
     int flow_sign; // imposed flow: +1, or -1 once reversed
     int flip;      // 0 / 1 on alternate steps: reverses the march direction of every segment
+    long long chk_shrink;   // checked kernel only: elements left out of the declared buffer ends
 };
 
 // Step variants: bit 0 single relaxation time (Sec. 7) instead of the cascaded rates; bit 1 the
@@ -465,7 +466,8 @@ __device__ __forceinline__ void push_pair_z(const F2 g[9], const F2 f[9], const 
 template <typename R, typename S, int V, bool CK = false>
 __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__ dst,
                                       const Geometry& G, const Consts<R>& K, int strip, int seg,
-                                      int seg_h, int* err, int flow_sign, int flip)
+                                      int seg_h, int* err, int flow_sign, int flip,
+                                      long long chk_shrink = 0)
 {
     constexpr int NS = Stages<S>::value;
     constexpr bool SRT = (V & kVarSRT) != 0;
@@ -473,7 +475,8 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     constexpr bool LANGMUIR = (V & kVarLangmuir) != 0;
     constexpr bool NARROW = Narrow<S>::value;
     constexpr int TE = Tile<S>::ELEMS;               // elements per tile
-    const auto B = make_bounds<CK>(src, dst, (long long)G.ny * G.nstrips * TE, err);
+    const auto B =
+        make_bounds<CK>(src, dst, (long long)G.ny * G.nstrips * TE - chk_shrink, err);
     // the interface lattice alone copies only the f half of every tile (planes 9..17)
     constexpr int COPY_OFF = SHEAR ? Tile<S>::P0 + 9 * 32 : 0;
     constexpr uint32_t COPY_BYTES = SHEAR ? 9 * 32 * sizeof(S) : Tile<S>::BYTES;
@@ -722,7 +725,8 @@ __device__ __forceinline__ Win<float> half_win(const Win<F2>& w, bool b)
 template <typename S, int V, bool CK = false>
 __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict__ dst,
                                        const Geometry& G, const Consts<float>& K, int wstrip,
-                                       int seg, int seg_h, int* err, int flow_sign, int flip)
+                                       int seg, int seg_h, int* err, int flow_sign, int flip,
+                                       long long chk_shrink = 0)
 {
     constexpr int NS = Stages<S>::value;
     constexpr bool SRT = (V & kVarSRT) != 0;
@@ -731,7 +735,8 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
     static_assert(!(SHEAR && Narrow<S>::value), "the imposed flow runs in FP32 storage");
     constexpr bool NARROW = Narrow<S>::value;
     constexpr int TE = Tile<S>::ELEMS;               // elements per tile
-    const auto B = make_bounds<CK>(src, dst, (long long)G.ny * G.nstrips * TE, err);
+    const auto B =
+        make_bounds<CK>(src, dst, (long long)G.ny * G.nstrips * TE - chk_shrink, err);
     constexpr int STAGE = 2 * TE;                    // elements per stage (two tiles)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -980,9 +985,11 @@ __device__ __forceinline__ void step_body(const S* __restrict__ src, S* __restri
     const int seg = warp / wstrips;
     if (seg >= L.nseg) return;                       // warp-uniform
     if constexpr (NT == 2)
-        march2<S, V, CK>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign, L.flip);
+        march2<S, V, CK>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign, L.flip,
+                         L.chk_shrink);
     else
-        march<R, S, V, CK>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign, L.flip);
+        march<R, S, V, CK>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign, L.flip,
+                           L.chk_shrink);
 }
 
 template <typename R, typename S, int V>
@@ -1309,9 +1316,10 @@ cudaError_t configure_step_checked(int block)
 template <typename R, typename S>
 cudaError_t launch_step_checked(const void* src, void* dst, const Geometry& G,
                                 const Consts<R>& K, int seg_h, int block, int* err,
-                                cudaStream_t st)
+                                int shrink_rows, cudaStream_t st)
 {
     StepLaunch L = {};
+    L.chk_shrink = (long long)shrink_rows * G.nstrips * Tile<S>::ELEMS;
     L.seg_h = seg_h;
     L.nseg = (G.ny + seg_h - 1) / seg_h;
     L.err = err;
@@ -1477,7 +1485,7 @@ cudaError_t launch_unpack(const double* in, void* state, const Geometry& G, cons
 #define CMLBM_INSTANTIATE(R, S)                                                                   \
     template cudaError_t configure_step_checked<R, S>(int);                                     \
     template cudaError_t launch_step_checked<R, S>(const void*, void*, const Geometry&,         \
-                                                   const Consts<R>&, int, int, int*,            \
+                                                   const Consts<R>&, int, int, int*, int,       \
                                                    cudaStream_t);                               \
     template cudaError_t configure_batch<R, S>(int);                                            \
     template cudaError_t build_batch_graph<R, S>(void*, const BatchCase<R>*, const int2*, int,  \

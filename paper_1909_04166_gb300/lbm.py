@@ -282,8 +282,9 @@ def lbm_set_graphs(ctx, enable: bool) -> None:
     _check(lib().lbm_set_graphs(ctx, int(bool(enable))), "lbm_set_graphs")
 
 
-def lbm_set_checked(ctx, enable: bool) -> None:
-    _check(lib().lbm_set_checked(ctx, int(bool(enable))), "lbm_set_checked")
+def lbm_set_checked(ctx, enable) -> None:
+    """enable: 0 / False plain kernel, 1 / True checked kernel, 2 the checker's self-test."""
+    _check(lib().lbm_set_checked(ctx, int(enable)), "lbm_set_checked")
 
 
 def lbm_check(ctx) -> None:

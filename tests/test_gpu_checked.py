@@ -68,3 +68,26 @@ def test_checked_mode_is_refused_for_step_variants():
         with pytest.raises(lbm.LbmError) as e:
             lbm.lbm_set_checked(sim.ctx, True)
         assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
+def test_checker_reports_accesses_outside_its_declared_bounds(precision):
+    """Self-test of the checker (mode 2): the declared bounds leave out the last row of both
+    buffers (allocated memory, so nothing stray is touched); the steps' loads, copies and stores
+    of that row are refused and reported as LBM_ERR_INDEX by every later synchronising call of
+    that context, while the device stays usable for others."""
+    case = W.random_drop(45, 20, seed=9, wall_y=1, rho_ratio=10.0)
+    with lbm.Simulation(case, precision=precision) as sim:
+        sim.init_case()
+        lbm.lbm_set_checked(sim.ctx, 2)
+        sim.step(3)
+        assert lbm.lib().lbm_check(sim.ctx) == lbm.LBM_ERR_INDEX
+        with pytest.raises(lbm.LbmError) as e:
+            sim.fields()
+        assert e.value.status == lbm.LBM_ERR_INDEX
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_set_checked(sim.ctx, 3)
+        assert e.value.status == lbm.LBM_ERR_ARG
+    with lbm.Simulation(case, precision=precision) as other:
+        other.init_case().step(3)
+        assert lbm.lib().lbm_check(other.ctx) == lbm.LBM_OK
