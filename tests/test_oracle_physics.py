@@ -4,7 +4,8 @@ reproduce.  Laplace law for a static drop (Sec. 6.2), the tanh equilibrium inter
 interpolation, Eq. fluidviscosity, body force, walls), diffusion at the mobility M_phi (Sec. 5),
 the integrated Marangoni traction of a flat interface (Sec. 6.7), Galilean translation of a
 drop and the linear modes of a pressure wave in a uniform stream (the two parts of the net
-gradient pressure force F_p, Sec. 3).
+gradient pressure force F_p, Sec. 3), and the symmetry of the whole step under the diagonal
+reflection x <-> y (the D2Q9 lattice and the moment bases of Secs. 3 and 5).
 """
 import numpy as np
 import pytest
@@ -222,3 +223,46 @@ def test_uniform_body_force_accelerates_at_the_closed_form(rho_ref):
     g1, f1 = O.init(oc2, ones, zeros, np.full((ny, nx), 0.07), np.full((ny, nx), -0.02))
     g2, f2 = O.run(oc2, g1, f1, n)
     assert np.allclose(g2, g1, rtol=0, atol=1e-16) and np.allclose(f2, f1, rtol=0, atol=1e-16)
+
+
+DIAGONAL = [0, 2, 1, 4, 3, 5, 8, 7, 6]   # population index under the reflection x <-> y
+
+
+def _reflected(case):
+    """The same problem seen across the diagonal: every x quantity becomes the y one."""
+    d = dict(case.params)
+    for a, b in (("nx", "ny"), ("wall_x", "wall_y"), ("wall_x_hi", "wall_y_hi"),
+                 ("gradT_x", "gradT_y"), ("gx", "gy"), ("gradpsi_x", "gradpsi_y")):
+        d[a], d[b] = case.get(b), case.get(a)
+    d = {k: v for k, v in d.items() if v is not None}
+    fl = case["fields"]
+    return d, (fl["phi"].T, fl["p"].T, fl["uy"].T, fl["ux"].T)
+
+
+@pytest.mark.parametrize("extra", [
+    dict(wall_x=1, wall_x_hi=2, wall_y=0, gravity=1e-6, marangoni=-2e-5, rho_ratio=100.0),
+    dict(wall_x=2, wall_y=1, wall_y_hi=2, gravity=2e-6, rho_ratio=10.0, collision=1),
+    dict(wall_x=0, wall_y=1, rho_ratio=30.0, sigma_model=1, beta=0.5, psi0=0.2,
+         gradpsi_x=8e-4, gradpsi_y=-3e-4),
+])
+def test_step_is_equivariant_under_the_diagonal_reflection(extra):
+    """The D2Q9 lattice, its isotropic stencils and the moment bases of Secs. 3 and 5 are
+    symmetric under the reflection x <-> y (directions 1 <-> 2, 3 <-> 4, 6 <-> 8; the
+    relaxation rates of each pair of swapped moments are equal), so stepping the reflected
+    problem must give the reflected populations up to rounding.  A term with a wrong index or
+    sign in only one of the two axes breaks this."""
+    kw = dict(extra)
+    gravity, marangoni, ratio = kw.pop("gravity", 0.0), kw.pop("marangoni", 0.0), kw.pop("rho_ratio")
+    wx, wy = kw.pop("wall_x"), kw.pop("wall_y")
+    case = W.random_drop(23, 37, seed=11, wall_x=wx, wall_y=wy, rho_ratio=ratio, gravity=gravity,
+                         marangoni=marangoni, **kw)
+    case["gx"] = 0.4 * case["gy"]                  # a force along both axes
+    _, g, f, _ = run_case(case, 20)
+    d, fields = _reflected(case)
+    oc = O.OracleCase.from_dict(d)
+    gr, fr = O.run(oc, *O.init(oc, *fields), 20)
+    g_back = gr[DIAGONAL].transpose(0, 2, 1)
+    f_back = fr[DIAGONAL].transpose(0, 2, 1)
+    assert np.linalg.norm(g_back - g) <= 1e-12 * np.linalg.norm(g)
+    assert np.linalg.norm(f_back - f) <= 1e-12 * np.linalg.norm(f)
+    assert np.linalg.norm(g - g[:, :, ::-1]) > 1e-3 * np.linalg.norm(g)   # not trivially symmetric
