@@ -319,6 +319,7 @@ def measure_ensemble(steps, per_case_steps, precision="fp32", device=0, stream=0
     total = sum(c.nodes for c in cases)
     out = {"cases": len(cases), "nodes": total}
     with lbm.Batch(cases, precision=precision, device=device, stream=stream) as b:
+        out["transposed_cases"] = sum(b.transposed(i) for i in range(len(cases)))
         b.init_all()
         seg, block = lbm.lbm_batch_tune(b.b, 4)
         b.step(8)

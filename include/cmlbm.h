@@ -305,15 +305,37 @@ int lbm_diagnostics_noalloc(const double* phi, const double* p, const double* ux
  * advanced together.  Every lbm_batch_step advances all cases by one time step with ONE launch
  * of the batched step kernel (each warp takes one strip x segment task of one case from a
  * flattened task list); runs of 32 steps are replays of a CUDA graph.  The per-node arithmetic
- * is the one of lbm_step, so each case evolves exactly as it would in its own context.
+ * is the one of lbm_step.  A warp owns strips of 64 columns (32 in FP64), so a case whose width
+ * is not a multiple of that leaves lanes idle; lbm_batch_create therefore stores each case in
+ * the orientation whose padded strips cover fewer nodes (LBM_BATCH_FEWEST_COLUMNS): a case
+ * stored transposed is stepped as its problem reflected across the diagonal (grid, boundary
+ * kinds, gradients and body force with x and y exchanged), whose solution the D2Q9 scheme of
+ * Secs. 3 and 5 maps onto the reflected one.  All fields and populations are passed in the
+ * case's own orientation; the transposes run on the host in those calls.  A case stored as
+ * given evolves bitwise as in its own context; a transposed one agrees with it up to the
+ * rounding of the reflected evaluation order.
  * ------------------------------------------------------------------------------------------- */
 typedef struct lbm_batch lbm_batch;
+
+/* Orientation policy of lbm_batch_create_ex. */
+typedef enum {
+    LBM_BATCH_AS_GIVEN = 0,        /* every case as given: bitwise as in its own context */
+    LBM_BATCH_FEWEST_COLUMNS = 1   /* per case, the orientation with fewer padded columns */
+} lbm_batch_layout;
 
 /* params: array of ncases (>= 1) cases; precision, device and stream must be equal in all of
  * them.  One device allocation holds every case's two state buffers (zeroed).  Cases may mix
  * boundary kinds; every case must take the cascaded coupled step with the linear sigma(T)
  * (LBM_CASCADED, LBM_FLOW_COUPLED, LBM_SIGMA_LINEAR_T), else LBM_ERR_UNSUPPORTED. */
 int lbm_batch_create(const lbm_params* params, int32_t ncases, lbm_batch** out);
+
+/* As lbm_batch_create with the orientation policy `layout` (lbm_batch_layout; lbm_batch_create
+ * takes LBM_BATCH_FEWEST_COLUMNS); other values: LBM_ERR_ARG.  Ties keep the case as given. */
+int lbm_batch_create_ex(const lbm_params* params, int32_t ncases, int32_t layout,
+                        lbm_batch** out);
+
+/* 1 if case c is stored transposed, 0 if as given; LBM_ERR_ARG for a bad batch or index. */
+int lbm_batch_case_transposed(const lbm_batch* b, int32_t c);
 
 /* Equilibrium initialisation of case c from host fields ([ny][nx] doubles of that case), as
  * lbm_init_fields.  Synchronises. */

@@ -1,6 +1,15 @@
 // Batched C ABI (declared in include/cmlbm.h): many independent cases of uneven grid sizes
 // advanced together, one launch of the batched step kernel per time step (replayed from a CUDA
 // graph), with an autotuner that picks the segment height and block size on the live batch.
+//
+// Orientation.  A warp owns whole strips of 32 (FP64) or 64 (FP32 arithmetic) columns, so a
+// case whose width is not a multiple of that leaves lanes idle in its last strip.  Under the
+// fewest-columns layout each case is stored in the orientation whose padded strips cover fewer
+// nodes: a case whose transpose wins is stepped as the problem reflected across the diagonal
+// (x <-> y for the grid, the boundary kinds, the temperature and surfactant gradients and the
+// body force; populations 1 <-> 2, 3 <-> 4, 6 <-> 8), which the D2Q9 scheme of Secs. 3 and 5
+// maps onto the reflected solution.  Fields and populations cross the boundary in the case's
+// own orientation; the transposes run on the host.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,13 +28,37 @@ namespace {
 constexpr int kBatchGraphChunk = 32;
 
 struct HostCase {
-    lbm_params P;
+    lbm_params P;           // as stored: the reflected problem when tr
+    bool tr;                // stored transposed
     Geometry G;
     Consts<double> Kd;
     Consts<float> Kf;
     long long off0, off1;   // element offsets of the two buffers
     long long nodes;
 };
+
+// Population index under the reflection x <-> y (e_a -> (e_y, e_x)).
+constexpr int kDiagonal[9] = {0, 2, 1, 4, 3, 5, 8, 7, 6};
+
+// The problem reflected across the diagonal: every x quantity becomes the y one.
+lbm_params reflected(const lbm_params& p)
+{
+    lbm_params q = p;
+    std::swap(q.nx, q.ny);
+    std::swap(q.bc_x, q.bc_y);
+    std::swap(q.bc_x_hi, q.bc_y_hi);
+    std::swap(q.gradT_x, q.gradT_y);
+    std::swap(q.gx, q.gy);
+    std::swap(q.gradpsi_x, q.gradpsi_y);
+    return q;
+}
+
+// t = the transpose of a, a row-major [ny][nx] host array (t is [nx][ny]).
+void transpose(const double* a, int nx, int ny, double* t)
+{
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) t[(size_t)x * ny + y] = a[(size_t)y * nx + x];
+}
 
 }  // namespace
 
@@ -163,9 +196,16 @@ extern "C" {
 
 int lbm_batch_create(const lbm_params* params, int32_t ncases, lbm_batch** out)
 {
+    return lbm_batch_create_ex(params, ncases, LBM_BATCH_FEWEST_COLUMNS, out);
+}
+
+int lbm_batch_create_ex(const lbm_params* params, int32_t ncases, int32_t layout,
+                        lbm_batch** out)
+{
     if (!out) return LBM_ERR_ARG;
     *out = nullptr;
     if (!params || ncases < 1) return LBM_ERR_ARG;
+    if (layout != LBM_BATCH_AS_GIVEN && layout != LBM_BATCH_FEWEST_COLUMNS) return LBM_ERR_ARG;
     for (int c = 0; c < ncases; ++c) {
         int s = validate_params(&params[c]);
         if (s) return s;
@@ -186,9 +226,21 @@ int lbm_batch_create(const lbm_params* params, int32_t ncases, lbm_batch** out)
     for (int c = 0; c < ncases; ++c) {
         HostCase hc;
         hc.P = params[c];
-        hc.G = make_geometry(params[c]);
-        hc.Kd = make_consts<double>(params[c]);
-        hc.Kf = make_consts<float>(params[c]);
+        hc.tr = false;
+        if (layout == LBM_BATCH_FEWEST_COLUMNS) {
+            // nodes covered by the padded strips of either orientation
+            const auto covered = [&](int w, int h) {
+                const int wstrips = with_types(b->precision, [&](auto r, auto s) {
+                    return step_warp_strips<decltype(r), decltype(s), 0>((w + 31) / 32);
+                });
+                return (long long)wstrips * h;
+            };
+            hc.tr = covered(hc.P.ny, hc.P.nx) < covered(hc.P.nx, hc.P.ny);
+            if (hc.tr) hc.P = reflected(hc.P);
+        }
+        hc.G = make_geometry(hc.P);
+        hc.Kd = make_consts<double>(hc.P);
+        hc.Kf = make_consts<float>(hc.P);
         const long long elems = (long long)buffer_elems(hc.G.nx, hc.G.ny, b->precision);
         hc.off0 = off;
         hc.off1 = off + elems;
@@ -226,6 +278,16 @@ int lbm_batch_init_fields(lbm_batch* b, int32_t c, const double* phi, const doub
     const HostCase& hc = b->cases[c];
     const size_t N = (size_t)hc.nodes, B = N * sizeof(double);
     const double* src[4] = {phi, p, ux, uy};
+    std::vector<double> t;
+    if (hc.tr) {   // the reflected fields: phi, p and the swapped velocity components
+        const int nx = hc.P.ny, ny = hc.P.nx;   // the case's own grid
+        t.resize(4 * N);
+        const double* own[4] = {phi, p, uy, ux};
+        for (int k = 0; k < 4; ++k) {
+            transpose(own[k], nx, ny, t.data() + k * N);
+            src[k] = t.data() + k * N;
+        }
+    }
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 4 && e == cudaSuccess; ++k)
         e = cudaMemcpyAsync(b->scratch + k * N, src[k], B, cudaMemcpyHostToDevice, b->st);
@@ -273,10 +335,20 @@ int lbm_batch_get_fields(lbm_batch* b, int32_t c, double* phi, double* p, double
                                              d + 2 * N, d + 3 * N, d + 4 * N, b->st);
     });
     double* h[5] = {phi, p, ux, uy, rho};
+    std::vector<double> t;
+    if (hc.tr) {   // fetch the stored fields, then transpose each into the case's orientation
+        t.resize(5 * N);
+        for (int k = 0; k < 5; ++k) h[k] = h[k] ? t.data() + k * N : nullptr;
+    }
     for (int k = 0; k < 5 && e == cudaSuccess; ++k)
         if (h[k]) e = cudaMemcpyAsync(h[k], d + k * N, B, cudaMemcpyDeviceToHost, b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) return fail_cuda(b, e);
+    if (hc.tr) {
+        double* own[5] = {phi, p, uy, ux, rho};   // stored u_x is the case's u_y
+        for (int k = 0; k < 5; ++k)
+            if (own[k]) transpose(t.data() + k * N, hc.P.nx, hc.P.ny, own[k]);
+    }
     return check_err(b);
 }
 
@@ -292,14 +364,22 @@ int lbm_batch_get_populations(lbm_batch* b, int32_t c, double* g, double* f)
         e = with_types(b->precision, [&](auto r, auto s) {
             return launch_pack<double, decltype(s)>(case_state(b, c), tmp, hc.G, hc.Kd, b->st);
         });
+    std::vector<double> t(hc.tr ? 18 * N : 0);
+    double* hg = hc.tr ? t.data() : g;
+    double* hf = hc.tr ? t.data() + 9 * N : f;
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(g, tmp, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, b->st);
+        e = cudaMemcpyAsync(hg, tmp, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, b->st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(f, tmp + 9 * N, 9 * N * sizeof(double), cudaMemcpyDeviceToHost,
+        e = cudaMemcpyAsync(hf, tmp + 9 * N, 9 * N * sizeof(double), cudaMemcpyDeviceToHost,
                             b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) return fail_cuda(b, e);
+    if (hc.tr)   // population a of the case is the stored population kDiagonal[a], transposed
+        for (int a = 0; a < 9; ++a) {
+            transpose(hg + kDiagonal[a] * N, hc.P.nx, hc.P.ny, g + a * N);
+            transpose(hf + kDiagonal[a] * N, hc.P.nx, hc.P.ny, f + a * N);
+        }
     return check_err(b);
 }
 
@@ -391,6 +471,12 @@ int lbm_batch_tune(lbm_batch* b, int32_t trial_steps, int32_t* seg_rows, int32_t
 }
 
 int64_t lbm_batch_nodes(const lbm_batch* b) { return b ? b->total_nodes : -1; }
+
+int lbm_batch_case_transposed(const lbm_batch* b, int32_t c)
+{
+    if (!b || c < 0 || c >= (int)b->cases.size()) return LBM_ERR_ARG;
+    return b->cases[c].tr ? 1 : 0;
+}
 
 int lbm_batch_check(lbm_batch* b)
 {

@@ -41,6 +41,8 @@ LBM_SIGMA_LINEAR_T = 0
 LBM_SIGMA_LANGMUIR = 1
 LBM_FLOW_COUPLED = 0
 LBM_FLOW_SHEAR = 1
+LBM_BATCH_AS_GIVEN = 0
+LBM_BATCH_FEWEST_COLUMNS = 1
 
 EXPORTS = [
     "lbm_state_bytes", "lbm_create", "lbm_create_with_buffer", "lbm_init_fields",
@@ -52,6 +54,7 @@ EXPORTS = [
     "lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_get_fields",
     "lbm_batch_get_populations", "lbm_batch_set_launch", "lbm_batch_get_launch",
     "lbm_batch_tune", "lbm_batch_nodes", "lbm_batch_check", "lbm_batch_destroy",
+    "lbm_batch_create_ex", "lbm_batch_case_transposed",
 ]
 
 
@@ -139,6 +142,8 @@ def lib(build_if_missing: bool = True):
     L.lbm_diagnostics_noalloc.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, dd, dd, dd, dd,
                                           vp, vp]
     L.lbm_batch_create.argtypes = [P(lbm_params), i32, P(vp)]
+    L.lbm_batch_create_ex.argtypes = [P(lbm_params), i32, i32, P(vp)]
+    L.lbm_batch_case_transposed.argtypes = [vp, i32]
     L.lbm_batch_init_fields.argtypes = [vp, i32, dp, dp, dp, dp]
     L.lbm_batch_step.argtypes = [vp, i32]
     L.lbm_batch_get_fields.argtypes = [vp, i32, dp, dp, dp, dp, dp]
@@ -331,6 +336,20 @@ def lbm_batch_create(params_list) -> ctypes.c_void_p:
     return b
 
 
+def lbm_batch_create_ex(params_list, layout: int) -> ctypes.c_void_p:
+    arr = (lbm_params * len(params_list))(*params_list)
+    b = ctypes.c_void_p()
+    _check(lib().lbm_batch_create_ex(arr, len(params_list), int(layout), ctypes.byref(b)),
+           "lbm_batch_create_ex")
+    return b
+
+
+def lbm_batch_case_transposed(b, c: int) -> bool:
+    s = int(lib().lbm_batch_case_transposed(b, int(c)))
+    _check(min(s, 0), "lbm_batch_case_transposed")
+    return bool(s)
+
+
 def lbm_batch_init_fields(b, c, phi, p, ux, uy) -> None:
     _check(lib().lbm_batch_init_fields(b, int(c), _dptr(phi), _dptr(p), _dptr(ux), _dptr(uy)),
            "lbm_batch_init_fields")
@@ -387,10 +406,14 @@ def lbm_batch_destroy(b) -> None:
 class Batch:
     """Owns one batch of independent cases (dictionaries from ``workloads``)."""
 
-    def __init__(self, cases, precision="fp32", device=0, stream=0):
+    def __init__(self, cases, precision="fp32", device=0, stream=0,
+                 layout=LBM_BATCH_FEWEST_COLUMNS):
         self.cases = list(cases)
         self.params = [make_params(c, precision, device, stream) for c in self.cases]
-        self.b = lbm_batch_create(self.params)
+        self.b = lbm_batch_create_ex(self.params, layout)
+
+    def transposed(self, i) -> bool:
+        return lbm_batch_case_transposed(self.b, i)
 
     def init_case(self, i, fields=None):
         c = self.cases[i]

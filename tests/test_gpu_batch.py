@@ -1,10 +1,10 @@
 """Batched stepping (lbm_batch_*): one launch per step over many independent cases.
 
-Each case must evolve as in its own context (the batched kernel runs the same per-node
-arithmetic one node per lane, while the single-grid FP32 step updates two columns per lane on
-the packed FP32x2 instructions, so the two round differently: the comparison allows FP32
-rounding-level differences after 37 steps), match the FP64 oracle, and survive the autotuner
-bit for bit (within one kernel the launch shape does not change any result)."""
+Each case must evolve as in its own context: bitwise when stored as given (the batched kernel
+runs the per-node arithmetic of the single-grid step), to rounding when stored transposed (the
+reflected problem evaluates its sums in the reflected order); match the FP64 oracle, with its
+fields and populations returned in its own orientation; and survive the autotuner bit for bit
+(within one kernel the launch shape does not change any result)."""
 import numpy as np
 import pytest
 
@@ -26,22 +26,54 @@ def mixed_cases():
     ]
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp64", 1e-14), ("fp16", 1e-4)])
+# cases stored transposed under the fewest-columns layout: strips of 64 columns with FP32
+# arithmetic, 32 in FP64
+TRANSPOSED = {"fp32": [1, 2, 3], "fp16": [1, 2, 3], "fp64": [1, 2, 3, 5]}
+
+
+# Bound on a transposed case against its own context after 37 steps: rounding level in FP32 /
+# FP64; in FP16 storage a last-bit difference before encoding flips a 16-bit rounding, so the
+# two runs differ by up to about the FP16 unit roundoff 2^-11 = 4.9e-4 (2.7e-4 measured)
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp64", 1e-14), ("fp16", 1e-3)])
 def test_batch_cases_match_their_own_contexts(prec, tol):
     cases = mixed_cases()
-    with lbm.Batch(cases, precision=prec) as b:
-        b.init_all().step(37)
-        got = [b.populations(i) for i in range(len(cases))]
+    got = {}
+    for layout in (lbm.LBM_BATCH_AS_GIVEN, lbm.LBM_BATCH_FEWEST_COLUMNS):
+        with lbm.Batch(cases, precision=prec, layout=layout) as b:
+            tr = [i for i in range(len(cases)) if b.transposed(i)]
+            assert tr == ([] if layout == lbm.LBM_BATCH_AS_GIVEN else TRANSPOSED[prec])
+            b.init_all().step(37)
+            got[layout] = [(b.populations(i), b.fields(i)) for i in range(len(cases))]
     for i, c in enumerate(cases):
         with lbm.Simulation(c, precision=prec) as s:
-            g, f = s.init_case().step(37).populations()
-        assert np.linalg.norm(got[i][0] - g) <= tol * np.linalg.norm(g), i
-        assert np.linalg.norm(got[i][1] - f) <= tol * np.linalg.norm(f), i
+            s.init_case().step(37)
+            g, f = s.populations()
+            fl = s.fields()
+        (g0, f0), fl0 = got[lbm.LBM_BATCH_AS_GIVEN][i]
+        assert np.array_equal(g0, g) and np.array_equal(f0, f), i
+        (g1, f1), fl1 = got[lbm.LBM_BATCH_FEWEST_COLUMNS][i]
+        assert np.linalg.norm(g1 - g) <= tol * np.linalg.norm(g), i
+        assert np.linalg.norm(f1 - f) <= tol * np.linalg.norm(f), i
+        for k in ("phi", "p", "ux", "uy", "rho"):
+            assert np.linalg.norm(fl1[k] - fl[k]) <= 10 * tol * np.linalg.norm(fl[k]) + 1e-300, (i, k)
+
+
+def test_batch_layout_argument_is_checked():
+    p = [lbm.make_params(c, "fp32") for c in mixed_cases()[:2]]
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_batch_create_ex(p, 2)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    with lbm.Batch(mixed_cases()[:2]) as b:
+        with pytest.raises(lbm.LbmError) as e:
+            b.transposed(2)
+        assert e.value.status == lbm.LBM_ERR_ARG
 
 
 def test_batch_matches_oracle_fp64():
+    """Cases 1 and 2 are stored transposed, the others as given."""
     cases = mixed_cases()[:3] + W.ensemble(ncases=4)[1:3]
     with lbm.Batch(cases, precision="fp64") as b:
+        assert b.transposed(1) and b.transposed(2) and not b.transposed(0)
         b.init_all().step(6)
         for i, c in enumerate(cases):
             oc = O.OracleCase.from_dict(c.params)
