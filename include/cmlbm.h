@@ -325,8 +325,11 @@ typedef enum {
 
 /* params: array of ncases (>= 1) cases; precision, device and stream must be equal in all of
  * them.  One device allocation holds every case's two state buffers (zeroed).  Cases may mix
- * boundary kinds; every case must take the cascaded coupled step with the linear sigma(T)
- * (LBM_CASCADED, LBM_FLOW_COUPLED, LBM_SIGMA_LINEAR_T), else LBM_ERR_UNSUPPORTED. */
+ * grid sizes, boundary kinds and physical parameters; they must share the collision model
+ * (cascaded, Secs. 3-5, or single relaxation time, Sec. 7) and the sigma law (linear in T, or
+ * the Langmuir isotherm of Sec. 6.7): LBM_ERR_ARG otherwise.  The imposed flow
+ * (LBM_FLOW_SHEAR) is not batched: LBM_ERR_UNSUPPORTED.  The 16-bit storage modes take the
+ * cascaded step with the linear sigma(T) only, as in lbm_create. */
 int lbm_batch_create(const lbm_params* params, int32_t ncases, lbm_batch** out);
 
 /* As lbm_batch_create with the orientation policy `layout` (lbm_batch_layout; lbm_batch_create

@@ -75,6 +75,7 @@ struct lbm_batch {
     int* err;
     double* scratch;        // 5 * max nodes doubles (init / fields)
     long long max_nodes, total_nodes;
+    int variant;            // step variant shared by all cases (lbm_host.h step_variant)
     int cur;                // shared buffer parity
     int seg_h, block;
     cudaGraphExec_t graph[2];
@@ -141,33 +142,42 @@ int build_tasks(lbm_batch* b, int h)
     return LBM_OK;
 }
 
+// Call f(R{}, S{}, V{}) for the batch's precision and step variant (the imposed-flow variants
+// are refused at creation and never reach a kernel).
+template <class F>
+cudaError_t with_batch_kernel(const lbm_batch* b, F&& f)
+{
+    return with_variant(b->precision, b->variant, [&](auto r, auto s, auto v) -> cudaError_t {
+        if constexpr ((decltype(v)::value & 2) != 0) return cudaErrorInvalidValue;
+        else return f(r, s, v);
+    });
+}
+
 cudaError_t configure(lbm_batch* b)
 {
-    return with_types(b->precision, [&](auto r, auto s) {
-        return configure_batch<decltype(r), decltype(s)>(b->block);
+    return with_batch_kernel(b, [&](auto r, auto s, auto v) {
+        return configure_batch<decltype(r), decltype(s), decltype(v)::value>(b->block);
     });
 }
 
 cudaError_t launch_one(lbm_batch* b)
 {
-    return with_types(b->precision, [&](auto r, auto s) {
+    return with_batch_kernel(b, [&](auto r, auto s, auto v) {
         using R = decltype(r);
-        return launch_batch_step<R, decltype(s)>(b->base,
-                                                 static_cast<BatchCase<R>*>(b->dcases),
-                                                 b->dtasks, b->ntasks, b->cur, b->block, b->err,
-                                                 b->st);
+        return launch_batch_step<R, decltype(s), decltype(v)::value>(
+            b->base, static_cast<BatchCase<R>*>(b->dcases), b->dtasks, b->ntasks, b->cur,
+            b->block, b->err, b->st);
     });
 }
 
 cudaError_t ensure_graph(lbm_batch* b)
 {
     if (b->graph[b->cur]) return cudaSuccess;
-    return with_types(b->precision, [&](auto r, auto s) {
+    return with_batch_kernel(b, [&](auto r, auto s, auto v) {
         using R = decltype(r);
-        return build_batch_graph<R, decltype(s)>(b->base,
-                                                 static_cast<BatchCase<R>*>(b->dcases),
-                                                 b->dtasks, b->ntasks, b->cur, b->block, b->err,
-                                                 kBatchGraphChunk, &b->graph[b->cur]);
+        return build_batch_graph<R, decltype(s), decltype(v)::value>(
+            b->base, static_cast<BatchCase<R>*>(b->dcases), b->dtasks, b->ntasks, b->cur,
+            b->block, b->err, kBatchGraphChunk, &b->graph[b->cur]);
     });
 }
 
@@ -212,12 +222,14 @@ int lbm_batch_create_ex(const lbm_params* params, int32_t ncases, int32_t layout
         if (params[c].precision != params[0].precision || params[c].device != params[0].device ||
             params[c].stream != params[0].stream)
             return LBM_ERR_ARG;
-        if (step_variant(params[c]) != 0) return LBM_ERR_UNSUPPORTED;
+        if ((step_variant(params[c]) & 2) != 0) return LBM_ERR_UNSUPPORTED;   // imposed flow
+        if (step_variant(params[c]) != step_variant(params[0])) return LBM_ERR_ARG;
     }
     if (cudaSetDevice(params[0].device) != cudaSuccess) return LBM_ERR_CUDA;
     lbm_batch* b = new (std::nothrow) lbm_batch();
     if (!b) return LBM_ERR_NOMEM;
     b->precision = params[0].precision;
+    b->variant = step_variant(params[0]);
     b->device = params[0].device;
     b->elem = elem_bytes(b->precision);
     b->st = static_cast<cudaStream_t>(params[0].stream);

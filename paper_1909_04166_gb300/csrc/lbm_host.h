@@ -46,12 +46,14 @@ cudaError_t launch_pack(const void*, double*, const Geometry&, const Consts<R>&,
 template <typename R, typename S>
 cudaError_t launch_unpack(const double*, void*, const Geometry&, const Consts<R>&,
                           cudaStream_t);
-template <typename R, typename S>
+// The batched step of variant V (0 cascaded, 1 SRT, 4 Langmuir, 5 both; no imposed flow; the
+// 16-bit storage modes 0 only).
+template <typename R, typename S, int V>
 cudaError_t configure_batch(int block);
-template <typename R, typename S>
+template <typename R, typename S, int V>
 cudaError_t launch_batch_step(void*, const BatchCase<R>*, const int2*, int, int, int, int*,
                               cudaStream_t);
-template <typename R, typename S>
+template <typename R, typename S, int V>
 cudaError_t build_batch_graph(void*, const BatchCase<R>*, const int2*, int, int, int, int*, int,
                               cudaGraphExec_t*);
 

@@ -1037,52 +1037,54 @@ constexpr auto step_kernel_of()
 
 // One time step of many independent grids in one launch: warp w takes task w = (case, local
 // warp index) from a flattened task list; every case has its own geometry, constants and pair
-// of buffers inside one allocation.  All cases share the buffer parity (they step together).
-template <typename R, typename S>
+// of buffers inside one allocation.  All cases share the buffer parity (they step together) and
+// the step variant V (no imposed flow).
+template <typename R, typename S, int V>
 __device__ __forceinline__ void batch_body(S* __restrict__ base,
                                            const BatchCase<R>* __restrict__ cases,
                                            const int2* __restrict__ tasks, int ntasks,
                                            int parity, int* err)
 {
+    static_assert((V & kVarShear) == 0, "batches take the coupled lattices");
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (warp >= ntasks) return;                      // warp-uniform
     const int2 t = tasks[warp];
     const BatchCase<R>& c = cases[t.x];
     const Geometry G = c.G;
-    constexpr int NT = tiles_per_warp<R, S, 0>();
+    constexpr int NT = tiles_per_warp<R, S, V>();
     const int wstrips = (G.nstrips + NT - 1) / NT;
     const int strip = t.y % wstrips;
     const int seg = t.y / wstrips;
     const S* src = base + (parity ? c.off1 : c.off0);
     S* dst = base + (parity ? c.off0 : c.off1);
-    if constexpr (NT == 2) march2<S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1, parity);
-    else march<R, S, 0>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1, parity);
+    if constexpr (NT == 2) march2<S, V>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1, parity);
+    else march<R, S, V>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1, parity);
 }
 
-template <typename R, typename S>
+template <typename R, typename S, int V>
 __global__ void __launch_bounds__(256)
 batch_step_kernel(S* __restrict__ base, const BatchCase<R>* __restrict__ cases,
                   const int2* __restrict__ tasks, int ntasks, int parity, int* err)
 {
-    batch_body<R, S>(base, cases, tasks, ntasks, parity, err);
+    batch_body<R, S, V>(base, cases, tasks, ntasks, parity, err);
 }
 
 // The batched step of the 16-bit forms, held to 168 registers per thread like
 // step_kernel_narrow (200 without the cap, which leaves 8 warps per SM).
-template <typename R, typename S>
+template <typename R, typename S, int V>
 __global__ void __launch_bounds__(256) __maxnreg__(NarrowRegs<S>::value)
 batch_step_kernel_narrow(S* __restrict__ base, const BatchCase<R>* __restrict__ cases,
                          const int2* __restrict__ tasks, int ntasks, int parity, int* err)
 {
-    batch_body<R, S>(base, cases, tasks, ntasks, parity, err);
+    batch_body<R, S, V>(base, cases, tasks, ntasks, parity, err);
 }
 
-// The batched step kernel of a storage form.
-template <typename R, typename S>
+// The batched step kernel of a storage form and step variant.
+template <typename R, typename S, int V>
 constexpr auto batch_kernel_of()
 {
-    if constexpr (Narrow<S>::value) return batch_step_kernel_narrow<R, S>;
-    else return batch_step_kernel<R, S>;
+    if constexpr (Narrow<S>::value) return batch_step_kernel_narrow<R, S, V>;
+    else return batch_step_kernel<R, S, V>;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1374,31 +1376,31 @@ cudaError_t build_step_graph(const void* a, const void* b, const Geometry& G, co
     return e;
 }
 
-template <typename R, typename S>
+template <typename R, typename S, int V>
 cudaError_t configure_batch(int block)
 {
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel_of<R, S>(),
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel_of<R, S, V>(),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)step_smem_bytes<R, S, 0>(block));
+                                         (int)step_smem_bytes<R, S, V>(block));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(batch_kernel_of<R, S>(),
+    return cudaFuncSetAttribute(batch_kernel_of<R, S, V>(),
                                 cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
 }
 
-template <typename R, typename S>
+template <typename R, typename S, int V>
 cudaError_t launch_batch_step(void* base, const BatchCase<R>* cases, const int2* tasks,
                               int ntasks, int parity, int block, int* err, cudaStream_t st)
 {
     const int wpb = block / 32;
     const unsigned grid = (unsigned)((ntasks + wpb - 1) / wpb);
-    batch_kernel_of<R, S>()<<<grid, block, step_smem_bytes<R, S, 0>(block), st>>>(
+    batch_kernel_of<R, S, V>()<<<grid, block, step_smem_bytes<R, S, V>(block), st>>>(
         static_cast<S*>(base), cases, tasks, ntasks, parity, err);
     return cudaGetLastError();
 }
 
 // A graph of `chunk` (even) consecutive batched steps starting from buffer parity `parity0`.
-template <typename R, typename S>
+template <typename R, typename S, int V>
 cudaError_t build_batch_graph(void* base, const BatchCase<R>* cases, const int2* tasks,
                               int ntasks, int parity0, int block, int* err, int chunk,
                               cudaGraphExec_t* out)
@@ -1416,10 +1418,10 @@ cudaError_t build_batch_graph(void* base, const BatchCase<R>* cases, const int2*
         void* args[] = {(void*)&b, (void*)&cases, (void*)&tasks, (void*)&n, (void*)&parity,
                         (void*)&err};
         cudaKernelNodeParams p = {};
-        p.func = (void*)batch_kernel_of<R, S>();
+        p.func = (void*)batch_kernel_of<R, S, V>();
         p.gridDim = dim3(grid);
         p.blockDim = dim3(block);
-        p.sharedMemBytes = (unsigned)step_smem_bytes<R, S, 0>(block);
+        p.sharedMemBytes = (unsigned)step_smem_bytes<R, S, V>(block);
         p.kernelParams = args;
         cudaGraphNode_t node;
         e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &p);
@@ -1487,17 +1489,20 @@ cudaError_t launch_unpack(const double* in, void* state, const Geometry& G, cons
     template cudaError_t launch_step_checked<R, S>(const void*, void*, const Geometry&,         \
                                                    const Consts<R>&, int, int, int*, int,       \
                                                    cudaStream_t);                               \
-    template cudaError_t configure_batch<R, S>(int);                                            \
-    template cudaError_t build_batch_graph<R, S>(void*, const BatchCase<R>*, const int2*, int,  \
-                                                 int, int, int*, int, cudaGraphExec_t*);        \
-    template cudaError_t launch_batch_step<R, S>(void*, const BatchCase<R>*, const int2*, int,  \
-                                                 int, int, int*, cudaStream_t);                 \
     template cudaError_t launch_init<R, S>(const double*, const double*, const double*,         \
                                            const double*, void*, const Geometry&,               \
                                            const Consts<R>&, cudaStream_t);                     \
     template cudaError_t launch_fields<R, S>(const void*, const Geometry&, const Consts<R>&,    \
                                              int, double*, double*, double*, double*, double*,  \
                                              cudaStream_t);
+
+#define CMLBM_INSTANTIATE_BATCH(R, S, V)                                                          \
+    template cudaError_t configure_batch<R, S, V>(int);                                         \
+    template cudaError_t build_batch_graph<R, S, V>(void*, const BatchCase<R>*, const int2*,    \
+                                                    int, int, int, int*, int,                   \
+                                                    cudaGraphExec_t*);                          \
+    template cudaError_t launch_batch_step<R, S, V>(void*, const BatchCase<R>*, const int2*,    \
+                                                    int, int, int, int*, cudaStream_t);
 
 // Populations are copied in and out in double; the codec of the 16-bit formats is applied in
 // double there so that a value read out and written back is stored exactly as before.
@@ -1526,6 +1531,18 @@ CMLBM_INSTANTIATE_STEP(float, float, 4)
 CMLBM_INSTANTIATE_STEP(float, float, 5)
 CMLBM_INSTANTIATE_STEP(float, __half, 0)
 CMLBM_INSTANTIATE_STEP(float, __nv_bfloat16, 0)
+// batches: the coupled-lattice variants (cascaded / SRT, linear sigma / Langmuir) in FP64 and
+// FP32, the cascaded linear-sigma step in the 16-bit storage modes
+CMLBM_INSTANTIATE_BATCH(double, double, 0)
+CMLBM_INSTANTIATE_BATCH(double, double, 1)
+CMLBM_INSTANTIATE_BATCH(double, double, 4)
+CMLBM_INSTANTIATE_BATCH(double, double, 5)
+CMLBM_INSTANTIATE_BATCH(float, float, 0)
+CMLBM_INSTANTIATE_BATCH(float, float, 1)
+CMLBM_INSTANTIATE_BATCH(float, float, 4)
+CMLBM_INSTANTIATE_BATCH(float, float, 5)
+CMLBM_INSTANTIATE_BATCH(float, __half, 0)
+CMLBM_INSTANTIATE_BATCH(float, __nv_bfloat16, 0)
 CMLBM_INSTANTIATE_PACK(double)
 CMLBM_INSTANTIATE_PACK(float)
 CMLBM_INSTANTIATE_PACK(__half)
@@ -1533,5 +1550,6 @@ CMLBM_INSTANTIATE_PACK(__nv_bfloat16)
 #undef CMLBM_INSTANTIATE
 #undef CMLBM_INSTANTIATE_STEP
 #undef CMLBM_INSTANTIATE_PACK
+#undef CMLBM_INSTANTIATE_BATCH
 
 }  // namespace cmlbm

@@ -120,14 +120,17 @@ def test_new_forms_are_validated_without_a_device():
     assert status("fp16", wall_y=2) == lbm.LBM_OK
 
 
-def test_batch_rejects_other_step_forms_without_a_device():
-    """A batch takes the cascaded coupled step with the linear sigma(T) only; the check comes
-    before any device work."""
+def test_batch_rejects_mixed_step_forms_without_a_device():
+    """The cases of a batch share the collision model and the sigma law (else LBM_ERR_ARG); the
+    imposed flow is not batched (LBM_ERR_UNSUPPORTED); the checks come before any device
+    work."""
     from paper_1909_04166_gb300 import workloads as W
     base = lbm.make_params(W.random_drop(40, 30, seed=1), "fp32")
-    for bad in (dict(collision=1), dict(flow=1, u0=0.01), dict(sigma_model=1, beta=0.5)):
+    for bad, code in ((dict(collision=1), lbm.LBM_ERR_ARG),
+                      (dict(sigma_model=1, beta=0.5), lbm.LBM_ERR_ARG),
+                      (dict(flow=1, u0=0.01), lbm.LBM_ERR_UNSUPPORTED)):
         c = W.random_drop(40, 30, seed=2)
         c.update(bad)
         with pytest.raises(lbm.LbmError) as e:
             lbm.lbm_batch_create([base, lbm.make_params(c, "fp32")])
-        assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
+        assert e.value.status == code, bad

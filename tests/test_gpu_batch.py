@@ -130,3 +130,68 @@ def test_batch_rejects_mixed_precision():
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_batch_create(p)
     assert e.value.status == lbm.LBM_ERR_ARG
+
+
+def variant_cases(collision, sigma_model):
+    extra = dict(collision=collision, sigma_model=sigma_model)
+    if sigma_model == 1:
+        extra.update(beta=0.5, psi0=0.2, gradpsi_x=6e-4, gradpsi_y=-2e-4)
+    return [
+        W.random_drop(40, 33, seed=11, wall_y=True, rho_ratio=20.0, gravity=1e-6, **extra),
+        W.random_drop(97, 64, seed=12, wall_x=True, rho_ratio=10.0, marangoni=-2e-5, **extra),
+        W.random_drop(17, 70, seed=13, wall_x=2, wall_y=1, rho_ratio=50.0, **extra),
+        W.random_drop(65, 9, seed=14, rho_ratio=5.0, **extra),
+    ]
+
+
+@pytest.mark.parametrize("collision,sigma_model", [(1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp64", 1e-13)])
+def test_batch_of_step_variants_matches_their_own_contexts(collision, sigma_model, prec, tol):
+    """Batches of single-relaxation-time cases (Sec. 7) and of Langmuir-isotherm cases (Sec.
+    6.7): bitwise as their own contexts when stored as given, to rounding when transposed."""
+    cases = variant_cases(collision, sigma_model)
+    got = {}
+    for layout in (lbm.LBM_BATCH_AS_GIVEN, lbm.LBM_BATCH_FEWEST_COLUMNS):
+        with lbm.Batch(cases, precision=prec, layout=layout) as b:
+            if layout == lbm.LBM_BATCH_FEWEST_COLUMNS:
+                assert b.transposed(1) and b.transposed(2) and not b.transposed(0)
+            b.init_all().step(40)
+            lbm.lbm_batch_check(b.b)
+            got[layout] = [b.populations(i) for i in range(len(cases))]
+    for i, c in enumerate(cases):
+        with lbm.Simulation(c, precision=prec) as s:
+            g, f = s.init_case().step(40).populations()
+        g0, f0 = got[lbm.LBM_BATCH_AS_GIVEN][i]
+        assert np.array_equal(g0, g) and np.array_equal(f0, f), i
+        g1, f1 = got[lbm.LBM_BATCH_FEWEST_COLUMNS][i]
+        assert np.linalg.norm(g1 - g) <= tol * np.linalg.norm(g), i
+        assert np.linalg.norm(f1 - f) <= tol * np.linalg.norm(f), i
+
+
+def test_batch_of_step_variants_matches_oracle_fp64():
+    cases = variant_cases(1, 1)[:3]
+    with lbm.Batch(cases, precision="fp64") as b:
+        b.init_all().step(5)
+        for i, c in enumerate(cases):
+            oc = O.OracleCase.from_dict(c.params)
+            fl = c["fields"]
+            g_ref, f_ref = O.run(oc, *O.init(oc, fl["phi"], fl["p"], fl["ux"], fl["uy"]), 5)
+            g, f = b.populations(i)
+            assert np.linalg.norm(g - g_ref) <= 1e-12 * np.linalg.norm(g_ref), i
+            assert np.linalg.norm(f - f_ref) <= 1e-12 * np.linalg.norm(f_ref), i
+
+
+def test_batch_refuses_mixed_variants_and_the_imposed_flow():
+    a, b = variant_cases(0, 0)[:2]
+    b = dict(b)
+    b["collision"] = 1
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_batch_create([lbm.make_params(a, "fp32"), lbm.make_params(b, "fp32")])
+    assert e.value.status == lbm.LBM_ERR_ARG
+    shear = W.shear_circle(L0=64)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_batch_create([lbm.make_params(shear, "fp32")])
+    assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_batch_create([lbm.make_params(b, "fp16")])
+    assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
