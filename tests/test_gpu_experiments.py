@@ -63,3 +63,15 @@ def test_cascaded_operator_runs_where_single_relaxation_time_fails():
     ok_srt, _, _ = E._stable(W.oscillating_cylinder(rho_ratio=900.0, nu=1e-2, collision=1),
                              "fp32", 20000, 2000, 0.1)
     assert ok_cascaded and not ok_srt
+
+
+def test_batched_stability_check_agrees_with_single_runs():
+    """The E8 sweep advances all its viscosities in one batch; each case must reach the same
+    verdict, at the same checkpoint, as when it runs alone."""
+    cases = [W.oscillating_cylinder(rho_ratio=900.0, nu=nu, collision=1) for nu in (1e-2, 5e-2)]
+    batched = E._stable_batch(cases, "fp32", 6000, 2000, 0.1)
+    for c, (ok, done, peak) in zip(cases, batched):
+        ok1, done1, peak1 = E._stable(c, "fp32", 6000, 2000, 0.1)
+        assert (ok, done) == (ok1, done1)
+        assert abs(peak - peak1) <= 1e-12 * max(peak1, 1e-300)
+    assert not batched[0][0]          # SRT at nu = 0.01 fails (Sec. 7)
