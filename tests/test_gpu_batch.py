@@ -195,3 +195,17 @@ def test_batch_refuses_mixed_variants_and_the_imposed_flow():
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_batch_create([lbm.make_params(b, "fp16")])
     assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
+
+
+def test_transposed_case_fields_with_some_outputs_omitted():
+    """Any output pointer of lbm_batch_get_fields may be NULL, transposed or not."""
+    cases = mixed_cases()[1:3]
+    with lbm.Batch(cases) as b:
+        assert b.transposed(0) and b.transposed(1)
+        b.init_all().step(3)
+        for i, c in enumerate(cases):
+            full = b.fields(i)
+            shape = (int(c["ny"]), int(c["nx"]))
+            p, uy = np.empty(shape), np.empty(shape)
+            lbm.lbm_batch_get_fields(b.b, i, None, p, None, uy, None)
+            assert np.array_equal(p, full["p"]) and np.array_equal(uy, full["uy"])
