@@ -346,21 +346,22 @@ int lbm_batch_get_fields(lbm_batch* b, int32_t c, double* phi, double* p, double
         return launch_fields<R, decltype(s)>(case_state(b, c), hc.G, kref<R>(hc), 0, d, d + N,
                                              d + 2 * N, d + 3 * N, d + 4 * N, b->st);
     });
-    double* h[5] = {phi, p, ux, uy, rho};
+    // destination of stored field k (phi, p, u_x, u_y, rho of the stored grid): a transposed
+    // case's stored u_x is its own u_y
+    double* own[5] = {phi, p, hc.tr ? uy : ux, hc.tr ? ux : uy, rho};
+    double* h[5] = {own[0], own[1], own[2], own[3], own[4]};
     std::vector<double> t;
     if (hc.tr) {   // fetch the stored fields, then transpose each into the case's orientation
         t.resize(5 * N);
-        for (int k = 0; k < 5; ++k) h[k] = h[k] ? t.data() + k * N : nullptr;
+        for (int k = 0; k < 5; ++k) h[k] = own[k] ? t.data() + k * N : nullptr;
     }
     for (int k = 0; k < 5 && e == cudaSuccess; ++k)
         if (h[k]) e = cudaMemcpyAsync(h[k], d + k * N, B, cudaMemcpyDeviceToHost, b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) return fail_cuda(b, e);
-    if (hc.tr) {
-        double* own[5] = {phi, p, uy, ux, rho};   // stored u_x is the case's u_y
+    if (hc.tr)
         for (int k = 0; k < 5; ++k)
             if (own[k]) transpose(t.data() + k * N, hc.P.nx, hc.P.ny, own[k]);
-    }
     return check_err(b);
 }
 
