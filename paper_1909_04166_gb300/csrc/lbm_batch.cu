@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "../../include/cmlbm.h"
