@@ -89,10 +89,10 @@ def kernel_source_hash() -> str:
 # figures are steady-state launches (caches not flushed between launches, as in the timed run;
 # mean of three consecutive launches).
 NCU_TRAFFIC = {
-    # profiles/step_kernel_impact_2048x1024_fp32.md (read 105.88 MB + write 149.99 MB)
-    ("13b0c2c78c484f2b", "impact", "fp32"): 255_865_344,
-    # profiles/step_kernel_impact_2048x1024_fp16.md (read 46.10 MB + write 92.32 MB)
-    ("13b0c2c78c484f2b", "impact", "fp16"): 138_416_128,
+    # profiles/step_kernel_impact_2048x1024_fp32.md (read 106.52 MB + write 150.91 MB)
+    ("4b7abf78c1218550", "impact", "fp32"): 257_428_651,
+    # profiles/step_kernel_impact_2048x1024_fp16.md (read 46.10 MB + write 92.23 MB)
+    ("4b7abf78c1218550", "impact", "fp16"): 138_330_112,
 }
 
 

@@ -55,7 +55,10 @@ __host__ __device__ constexpr double d2q9_w(int a)
 // population knows the destination's Z (it is in the writer's stencil window), so the reference
 // costs no extra traffic, the pressure level and the phase fraction stay in FP32, and only the
 // (small) departures from rest are rounded to 16 bits, with the floating exponent keeping the
-// light phase's momentum significant.  sum_a q_a = Z + (sum_a d_a) / s_L.
+// light phase's momentum significant.  sum_a q_a = Z + (sum_a d_a) / s_L.  The step stores a
+// node's rest population last, with the rounding errors of its eight moving populations
+// subtracted, so the 16-bit rounding does not accumulate in the lattice sums (lbm_step.cu,
+// encode_err).
 // ---------------------------------------------------------------------------------------------
 template <typename S> struct Narrow { static constexpr bool value = sizeof(S) < 4; };
 

@@ -336,9 +336,30 @@ __device__ __forceinline__ void push_node(const R g[9], const R f[9], S* rS, S* 
     }
 }
 
+// Rounding compensation of the 16-bit forms.  Each node stores its eight moving populations
+// first and keeps the sum of their rounding errors (stored minus exact scaled deviation; the
+// difference of a value and its 16-bit rounding is exact in FP32); its rest population, which
+// lands on the node itself, is stored with that sum subtracted.  The stored populations a node
+// sends out then sum to what it computed up to one 16-bit rounding of the rest population's
+// deviation, which is small (the rest state carries no flux), so the lattice sums (the phase
+// mass of the interface lattice) no longer drift with the rounding of every population.
+//
+// Stored value of a population that lands on a node with zeroth moment z: its scaled deviation
+// (v - w z) s, less adj when ADJ; err receives the stored value's rounding error, scaled.
+template <typename S, bool ADJ, typename R>
+__device__ __forceinline__ S encode_err(R v, R z, R w, R scale, R adj, R& err)
+{
+    R d = fmad(-w, z, v) * scale;
+    if constexpr (ADJ) d = d - adj;
+    const S h = f_to_narrow<S>(float(d));
+    err = R(narrow_to_f(h)) - d;
+    return h;
+}
+
 // As push_node for the 16-bit forms: every population is stored as its deviation from the rest
 // state of the node it lands on, whose zeroth moments are the window values ps (p*) and ph (phi)
 // at the landing offset; the node's own zeroth moments go to its Z planes (element offset zc).
+// The rest population goes last and takes up the rounding of the others (see encode_err).
 template <typename S, typename R, class BND = Bounds<false>>
 __device__ __forceinline__ void push_node_z(const R g[9], const R f[9], const Win<R>& ps,
                                             const Win<R>& ph, S* rS, S* rC, S* rN, int cw,
@@ -353,20 +374,28 @@ __device__ __forceinline__ void push_node_z(const R g[9], const R f[9], const Wi
     S* p[9] = {pc, rC + ce, rN + cc, rC + cw, rS + cc, rN + ce, rN + cw, rS + cw, rS + ce};
     constexpr int EXc[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     constexpr int EYc[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const R sg = K.st_scale[0], sf = K.st_scale[1];
+    R eg = R(0), ef = R(0), e;
     if (fast) {
 #pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            st_chk(B, &p[a][a * 32], encode<S, R>(g[a], win_at(ps, EXc[a], EYc[a]), 0, a, K));
+        for (int a = 1; a < 9; ++a) {
+            const R w = R(d2q9_w(a));
+            st_chk(B, &p[a][a * 32],
+                   encode_err<S, false>(g[a], win_at(ps, EXc[a], EYc[a]), w, sg, R(0), e));
+            eg += e;
             st_chk(B, &p[a][(9 + a) * 32],
-                   encode<S, R>(f[a], win_at(ph, EXc[a], EYc[a]), 1, a, K));
+                   encode_err<S, false>(f[a], win_at(ph, EXc[a], EYc[a]), w, sf, R(0), e));
+            ef += e;
         }
+        st_chk(B, &pc[0], encode_err<S, true>(g[0], ps.c, R(d2q9_w(0)), sg, eg, e));
+        st_chk(B, &pc[9 * 32], encode_err<S, true>(f[0], ph.c, R(d2q9_w(0)), sf, ef, e));
         return;
     }
     constexpr int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
     constexpr int MX[9] = {0, 3, 2, 1, 4, 6, 5, 8, 7};
     constexpr int MY[9] = {0, 1, 4, 3, 2, 8, 7, 6, 5};
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
+    for (int a = 1; a < 9; ++a) {
         const int ex = EXc[a], ey = EYc[a];
         const bool cx = (ex < 0 && bxw) || (ex > 0 && bxe);
         const bool cy = (ey < 0 && bys) || (ey > 0 && byn);
@@ -395,27 +424,39 @@ __device__ __forceinline__ void push_node_z(const R g[9], const R f[9], const Wi
             zg = win_at(ps, ex, 0);
             zf = win_at(ph, ex, 0);
         }
-        st_chk(B, &q[plane * 32], encode<S, R>(g[a], zg, 0, a, K));
-        st_chk(B, &q[(9 + plane) * 32], encode<S, R>(f[a], zf, 1, a, K));
+        const R w = R(d2q9_w(a));
+        st_chk(B, &q[plane * 32], encode_err<S, false>(g[a], zg, w, sg, R(0), e));
+        eg += e;
+        st_chk(B, &q[(9 + plane) * 32], encode_err<S, false>(f[a], zf, w, sf, R(0), e));
+        ef += e;
     }
+    st_chk(B, &pc[0], encode_err<S, true>(g[0], ps.c, R(d2q9_w(0)), sg, eg, e));
+    st_chk(B, &pc[9 * 32], encode_err<S, true>(f[0], ph.c, R(d2q9_w(0)), sf, ef, e));
 }
 
-// Stored values of population a for a lane's two nodes at once (the packed form of encode):
-// d = (v - w_a z) s for both halves with FFMA2 / FMUL2, rounded to 16 bits by one paired
-// conversion.  Same roundings as encode, element by element.
-template <typename S>
-__device__ __forceinline__ void encode_pair(F2 v, F2 z, float w, float scale, S& lo, S& hi)
+// Stored values of population a for a lane's two nodes at once (the packed form of
+// encode_err): d = (v - w_a z) s (less adj when ADJ) for both halves with FFMA2 / FMUL2, rounded
+// to 16 bits by one paired conversion; returns the pair's scaled rounding errors.  Same
+// roundings as encode_err, element by element.
+template <typename S, bool ADJ>
+__device__ __forceinline__ F2 encode_pair(F2 v, F2 z, float w, float scale, F2 adj, S& lo,
+                                          S& hi)
 {
-    const F2 d = fmad(F2(-w), z, v) * F2(scale);
+    F2 d = fmad(F2(-w), z, v) * F2(scale);
+    if constexpr (ADJ) d = d - adj;
+    float2 back;
     if constexpr (std::is_same<S, __half>::value) {
         const __half2 h = __float22half2_rn(d.v);
         lo = __low2half(h);
         hi = __high2half(h);
+        back = __half22float2(h);
     } else {
         const __nv_bfloat162 h = __float22bfloat162_rn(d.v);
         lo = __low2bfloat16(h);
         hi = __high2bfloat16(h);
+        back = __bfloat1622float2(h);
     }
+    return F2(back) - d;
 }
 
 // push_node_z for both nodes of a lane when no node of the warp row touches a wall (the fast
@@ -444,12 +485,8 @@ __device__ __forceinline__ void push_pair_z(const F2 g[9], const F2 f[9], const 
                 rS + ceB};
     constexpr int EXc[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     constexpr int EYc[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        const float w = float(d2q9_w(a));
-        S gA, gB, fA, fB;
-        encode_pair<S>(g[a], win_at(ps, EXc[a], EYc[a]), w, K.st_scale[0], gA, gB);
-        encode_pair<S>(f[a], win_at(ph, EXc[a], EYc[a]), w, K.st_scale[1], fA, fB);
+    F2 eg(0.0f), ef(0.0f);   // rounding errors of the moving populations (see encode_err)
+    auto put = [&](int a, S gA, S gB, S fA, S fB) {
         if (actA) {
             st_chk(B, &pA[a][a * 32], gA);
             st_chk(B, &pA[a][(9 + a) * 32], fA);
@@ -458,7 +495,22 @@ __device__ __forceinline__ void push_pair_z(const F2 g[9], const F2 f[9], const 
             st_chk(B, &pB[a][a * 32], gB);
             st_chk(B, &pB[a][(9 + a) * 32], fB);
         }
+    };
+#pragma unroll
+    for (int a = 1; a < 9; ++a) {
+        const float w = float(d2q9_w(a));
+        S gA, gB, fA, fB;
+        eg += encode_pair<S, false>(g[a], win_at(ps, EXc[a], EYc[a]), w, K.st_scale[0],
+                                    F2(0.0f), gA, gB);
+        ef += encode_pair<S, false>(f[a], win_at(ph, EXc[a], EYc[a]), w, K.st_scale[1],
+                                    F2(0.0f), fA, fB);
+        put(a, gA, gB, fA, fB);
     }
+    S gA, gB, fA, fB;
+    const float w0 = float(d2q9_w(0));
+    encode_pair<S, true>(g[0], ps.c, w0, K.st_scale[0], eg, gA, gB);
+    encode_pair<S, true>(f[0], ph.c, w0, K.st_scale[1], ef, fA, fB);
+    put(0, gA, gB, fA, fB);
 }
 
 // The march of one warp over one strip x segment of one grid: everything the step does for
