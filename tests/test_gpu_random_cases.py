@@ -67,8 +67,9 @@ def test_random_case_parity(seed, precision):
 
 # 16-bit storage (the cascaded coupled step with the linear sigma(T), the forms it offers):
 # bounds about three times the largest error measured over these 16 cases after 12 steps
-# (FP16: g 5.1e-4, f 2.5e-5, phi 2.3e-5, p 6.2e-4, u 3.0e-3; BF16: g 3.4e-3, f 2.3e-4,
-# phi 1.6e-4, p 4.5e-3, u 1.4e-2), the policy of the other 16-bit tests.
+# before the rest population's rounding compensation, which only lowers the errors (FP16: g
+# 5.1e-4, f 2.5e-5, phi 2.3e-5, p 6.2e-4, u 3.0e-3; BF16: g 3.4e-3, f 2.3e-4, phi 1.6e-4, p
+# 4.5e-3, u 1.4e-2).
 BOUNDS16 = {
     "fp16": {"g": 1.5e-3, "f": 1e-4, "phi": 1e-4, "p": 2e-3, "ux": 1e-2, "uy": 1e-2},
     "bf16": {"g": 1e-2, "f": 7e-4, "phi": 5e-4, "p": 1.5e-2, "ux": 5e-2, "uy": 5e-2},
