@@ -67,7 +67,8 @@ def test_random_case_parity(seed, precision):
 
 # 16-bit storage (the cascaded coupled step with the linear sigma(T), the forms it offers):
 # bounds about three times the largest error measured over these 16 cases after 12 steps
-# before the rest population's rounding compensation, which only lowers the errors (FP16: g
+# before the rest population's rounding compensation (which lowered the errors on the drop
+# workloads; these cases pass with it under the same bounds) (FP16: g
 # 5.1e-4, f 2.5e-5, phi 2.3e-5, p 6.2e-4, u 3.0e-3; BF16: g 3.4e-3, f 2.3e-4, phi 1.6e-4, p
 # 4.5e-3, u 1.4e-2).
 BOUNDS16 = {
