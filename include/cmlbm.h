@@ -89,7 +89,11 @@ typedef enum {
  * floating exponent keeping the light phase's momentum significant.  scale_L =
  * params.store_scale_g / store_scale_f, or when those are 0 the defaults 2^14 / 2^12 for FP16
  * (deviations from ~1e-6 to ~4 in the normal range) and 1 / 1 for BF16.  Collisions, forces and
- * stencils stay in float. */
+ * stencils stay in float.  A step stores each node's rest population last, with the 16-bit
+ * rounding errors of its eight moving populations subtracted from its deviation, so the
+ * populations a node sends out sum to what it computed up to one rounding of that (small)
+ * deviation: the lattice sums, the phase mass among them, do not drift with the storage
+ * rounding of a nearly steady state. */
 
 /* Boundary kind of the sides of one axis. */
 typedef enum {
