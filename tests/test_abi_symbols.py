@@ -134,3 +134,16 @@ def test_batch_rejects_mixed_step_forms_without_a_device():
         with pytest.raises(lbm.LbmError) as e:
             lbm.lbm_batch_create([base, lbm.make_params(c, "fp32")])
         assert e.value.status == code, bad
+
+
+def test_batch_layout_is_checked_without_a_device():
+    """lbm_batch_create_ex takes LBM_BATCH_AS_GIVEN or LBM_BATCH_FEWEST_COLUMNS only, checked
+    before any device work; lbm_batch_case_transposed refuses a NULL batch."""
+    import ctypes
+    from paper_1909_04166_gb300 import workloads as W
+    p = [lbm.make_params(W.random_drop(40, 30, seed=1), "fp32")]
+    for layout in (-1, 2):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_batch_create_ex(p, layout)
+        assert e.value.status == lbm.LBM_ERR_ARG
+    assert lbm.lib().lbm_batch_case_transposed(ctypes.c_void_p(), 0) == lbm.LBM_ERR_ARG
