@@ -194,7 +194,10 @@ int lbm_create_with_buffer(const lbm_params* params, void* device_buffer, size_t
 /* Equilibrium initialisation from host nodal fields phi, p, ux, uy ([ny][nx] doubles): the
  * fluid populations take the central moments of the transformed Maxwellian (Sec. 3 Eq.
  * centralmomentsgeqcomponents), the interface populations those of Sec. 5 with the
- * M_phi theta n term zero.  Synchronises the stream.  Resets the step counter. */
+ * M_phi theta n term zero.  Synchronises the stream.  Resets the step counter and clears a
+ * device error recorded by earlier steps (LBM_ERR_TIMEOUT / LBM_ERR_INDEX), as do
+ * lbm_init_fields_device, lbm_set_populations and lbm_load_state: they replace the state that
+ * error made invalid. */
 int lbm_init_fields(lbm_ctx* ctx, const double* phi, const double* p, const double* ux,
                     const double* uy);
 
@@ -203,8 +206,12 @@ int lbm_init_fields_device(lbm_ctx* ctx, const double* phi, const double* p, con
                            const double* uy);
 
 /* Advance nsteps (>= 0) time steps: one fused kernel launch per step on params.stream,
- * asynchronous; launch errors are returned.  Runs of 32 steps are issued as replays of a CUDA
- * graph of 32 launches (built on first use; see lbm_set_graphs). */
+ * asynchronous; launch errors are returned.  A run of two or more steps is issued as replays of
+ * CUDA graphs of 32, 16, 8, 4 and 2 launches (largest first; built on first use, see
+ * lbm_set_graphs), a last odd step as a single launch.  Inside a graph each launch is chained to
+ * the previous one by a programmatic dependency: it may be scheduled while the previous step's
+ * last blocks still run and waits on the device, before touching the state, until that step has
+ * completed, so the launch latency between steps is hidden. */
 int lbm_step(lbm_ctx* ctx, int32_t nsteps);
 
 /* Enable (default) or disable the graph replays of lbm_step; results are identical. */
@@ -252,10 +259,22 @@ int lbm_load_state(lbm_ctx* ctx, const void* host, size_t bytes, int64_t steps);
  * count of one state buffer. */
 int lbm_state_device(lbm_ctx* ctx, void** state, int32_t* nstrips, int64_t* elements);
 
-/* Synchronise the stream and report LBM_ERR_TIMEOUT if any step since creation gave up on a
- * bounded device wait, LBM_ERR_INDEX if a checked step (lbm_set_checked) met an access outside
- * the state buffers; LBM_OK otherwise. */
+/* Synchronise the stream and report LBM_ERR_TIMEOUT if any step since the state was last set
+ * (creation, lbm_init_fields*, lbm_set_populations, lbm_load_state) gave up on a bounded device
+ * wait, LBM_ERR_INDEX if a checked step (lbm_set_checked) met an access outside the state
+ * buffers; LBM_OK otherwise. */
 int lbm_check(lbm_ctx* ctx);
+
+/* Fault injection for tests of the failure path (no counterpart in the paper).  While enabled
+ * (enable = 1), every step launch makes the first bounded shared-memory wait of each warp give
+ * up at once, as if its row copy had never arrived: the warp records LBM_ERR_TIMEOUT in the
+ * device error word, waits (with the normal bound) for the bulk copies it has in flight so that
+ * none outlives the block, and returns without updating its nodes.  Nothing faults or hangs;
+ * the state of those steps is invalid, lbm_check reports LBM_ERR_TIMEOUT, and re-initialising
+ * the state (lbm_init_fields*, lbm_set_populations, lbm_load_state) clears the error.  Steps run
+ * as single launches while enabled.  enable = 0 (default) returns to normal waits; other
+ * values: LBM_ERR_ARG. */
+int lbm_inject_timeout(lbm_ctx* ctx, int32_t enable);
 
 /* Diagnostics of the current state; see lbm_diag.  r_in < 0 skips dp_laplace.  Synchronises.
  * Returns LBM_ERR_NONFINITE (with *out filled) when any node is non-finite. */
@@ -296,9 +315,13 @@ int lbm_last_cuda_error(const lbm_ctx* ctx);
  * Limit: nx * ny <= 8,388,608 nodes (4096 partial blocks of 2048 nodes); larger grids return
  * LBM_ERR_ARG.  The first call on a device looks up the array's device address with the device
  * current (make that first call before any stream capture begins); the address is cached per
- * device ordinal (0..63).  Every call reuses the same array: calls that overlap on the GPU (on
- * different streams, or on other host threads) race and give wrong results; serialise them.
- * Each call writes every partial slot it reads, so nothing needs clearing between calls. */
+ * device ordinal (0..63) together with the identity of the device's current CUDA context, and
+ * looked up again when that context changes (for instance after cudaDeviceReset).  Every call
+ * reuses the same array: calls that overlap on the GPU (on different streams, or on other host
+ * threads) race and give wrong results; serialise them.  Each call writes every partial slot it
+ * reads, so nothing needs clearing between calls.  Errors: LBM_ERR_ARG as above, LBM_ERR_CUDA if
+ * the set-up or a launch fails; a CUDA error the caller left pending before the call is neither
+ * reported nor cleared by it. */
 int lbm_diagnostics_noalloc(const double* phi, const double* p, const double* ux,
                             const double* uy, int32_t nx, int32_t ny, int32_t bc_x, int32_t bc_y,
                             double xc, double yc, double r_in, double r_out, lbm_diag* out,
@@ -308,7 +331,8 @@ int lbm_diagnostics_noalloc(const double* phi, const double* p, const double* ux
  * Batches: many independent cases (any mix of grid sizes, boundaries and physical parameters)
  * advanced together.  Every lbm_batch_step advances all cases by one time step with ONE launch
  * of the batched step kernel (each warp takes one strip x segment task of one case from a
- * flattened task list); runs of 32 steps are replays of a CUDA graph.  The per-node arithmetic
+ * flattened task list); runs of two or more steps are replays of CUDA graphs of 32, 16, 8, 4 and
+ * 2 launches chained as in lbm_step.  The per-node arithmetic
  * is the one of lbm_step.  A warp owns strips of 64 columns (32 in FP64), so a case whose width
  * is not a multiple of that leaves lanes idle; lbm_batch_create therefore stores each case in
  * the orientation whose padded strips cover fewer nodes (LBM_BATCH_FEWEST_COLUMNS): a case

@@ -76,8 +76,9 @@ static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 /* c_s^2 = c_sphi^2 = 1/3, Sec. 5. */
 #define CS2 (1.0 / 3.0)
 
-/* Regularisation of the interface normal (reading R6). */
-#define NORMAL_EPS 1e-6
+/* Regularisation of the interface normal (reading R6).  The tests may set another value
+ * (orc_set_normal_eps) to check that the pins of R6 reject materially different ones. */
+static double NORMAL_EPS = 1e-6;
 
 /* Boundary kind of one side of the grid. */
 #define BC_PERIODIC 0
@@ -729,6 +730,36 @@ void orc_run(const orc_case* c, double* g, double* f, double* g_tmp, double* f_t
         memcpy(f, f_tmp, bytes);
     }
 }
+
+/* Round every population to the nearest IEEE binary32 value (round to nearest even). */
+static void round_to_float(double* a, size_t n)
+{
+    for (size_t i = 0; i < n; ++i) a[i] = (double)(float)a[i];
+}
+
+/* As orc_run, with the state rounded to binary32 on entry and after every step: what storing the
+ * populations in FP32 between steps does on its own, every operation of a step staying in FP64.
+ * (Not a reading of the paper: it separates storage rounding from arithmetic rounding when the
+ * tests weigh an FP32 implementation against this FP64 one.) */
+void orc_run_float_storage(const orc_case* c, double* g, double* f, double* g_tmp,
+                           double* f_tmp, int nsteps)
+{
+    const size_t n = (size_t)9 * c->nx * c->ny;
+    round_to_float(g, n);
+    round_to_float(f, n);
+    orc_case cs = *c;
+    for (int s = 0; s < nsteps; ++s) {
+        cs.t = c->t + s;
+        orc_step(&cs, g, f, g_tmp, f_tmp);
+        memcpy(g, g_tmp, n * sizeof(double));
+        memcpy(f, f_tmp, n * sizeof(double));
+        round_to_float(g, n);
+        round_to_float(f, n);
+    }
+}
+
+void orc_set_normal_eps(double eps) { NORMAL_EPS = eps; }
+double orc_get_normal_eps(void) { return NORMAL_EPS; }
 
 int orc_num_threads(void)
 {

@@ -22,6 +22,7 @@ _LIB_PATH = os.path.join(_HERE, "libcmlbm_oracle.so")
 __all__ = [
     "OracleCase", "build", "lib", "init", "step", "run", "step_rows", "fields", "node_info",
     "stencils", "fluid_collide", "fluid_source", "ace_collide", "geq", "feq", "num_threads",
+    "run_float_storage", "normal_eps", "set_normal_eps",
 ]
 
 
@@ -152,6 +153,10 @@ def lib():
         _lib.orc_step.argtypes = [cp, dp, dp, dp, dp]
         _lib.orc_step_rows.argtypes = [cp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int]
         _lib.orc_run.argtypes = [cp, dp, dp, dp, dp, ctypes.c_int]
+        _lib.orc_run_float_storage.argtypes = [cp, dp, dp, dp, dp, ctypes.c_int]
+        _lib.orc_set_normal_eps.argtypes = [d]
+        _lib.orc_set_normal_eps.restype = None
+        _lib.orc_get_normal_eps.restype = d
         _lib.orc_fields.argtypes = [cp, dp, dp, dp, dp, dp, dp, dp]
         _lib.orc_node_info.argtypes = [cp, dp, dp, ctypes.c_int, ctypes.c_int, P(_Node)]
         _lib.orc_stencils.argtypes = [cp, dp, dp, dp, dp, dp, dp, dp]
@@ -206,6 +211,25 @@ def run(case: OracleCase, g, f, nsteps: int):
     gt, ft = np.empty_like(g), np.empty_like(f)
     lib().orc_run(case.c(), _ptr(g), _ptr(f), _ptr(gt), _ptr(ft), int(nsteps))
     return g, f
+
+
+def run_float_storage(case: OracleCase, g, f, nsteps: int):
+    """As run, with the state rounded to float32 on entry and after every step (FP32 storage
+    with FP64 arithmetic); returns the new (g-bar, f)."""
+    g, f = _f64(g).copy(), _f64(f).copy()
+    gt, ft = np.empty_like(g), np.empty_like(f)
+    lib().orc_run_float_storage(case.c(), _ptr(g), _ptr(f), _ptr(gt), _ptr(ft), int(nsteps))
+    return g, f
+
+
+def normal_eps() -> float:
+    """The regularisation eps of the interface normal n = grad phi / (|grad phi| + eps)."""
+    return float(lib().orc_get_normal_eps())
+
+
+def set_normal_eps(eps: float) -> None:
+    """Set eps (tests of reading R6 only: they restore the default afterwards)."""
+    lib().orc_set_normal_eps(float(eps))
 
 
 def fields(case: OracleCase, g, f) -> dict:

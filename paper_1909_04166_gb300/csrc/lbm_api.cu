@@ -34,8 +34,10 @@ struct lbm_ctx {
     double* partials;      // reduction partials
     int* err;              // device error word of the step kernel (bounded waits)
     int variant;           // step variant (lbm_host.h step_variant)
-    cudaGraphExec_t graph[2][2];   // kGraphChunk steps from buffer 0 / 1, flow sign + / -
+    // graphs of 2^(k+1) steps (k < kGraphSizes) from buffer 0 / 1, flow sign + / -
+    cudaGraphExec_t graph[2][2][5];
     int use_graph;
+    int cut_first_wait;    // lbm_inject_timeout
     int checked;           // steps run through the bounds-checked kernel (lbm_set_checked)
     int nsm;
     int last_cuda;
@@ -44,7 +46,9 @@ struct lbm_ctx {
 namespace {
 
 constexpr int kReduceSlots = 8;
-constexpr int kGraphChunk = 32;   // steps per replayed graph (even: the buffer parity returns)
+// Runs of n >= 2 steps replay graphs of 32, 16, 8, 4 and 2 steps (even: the buffer parity
+// returns); a last odd step is a single launch.
+constexpr int kGraphSizes = 5;
 
 template <typename R> const Consts<R>& kref(const lbm_ctx* c);
 template <> const Consts<double>& kref<double>(const lbm_ctx* c) { return c->Kd; }
@@ -93,10 +97,11 @@ void drop_graphs(lbm_ctx* c)
 {
     for (int k = 0; k < 2; ++k)
         for (int d = 0; d < 2; ++d)
-            if (c->graph[k][d]) {
-                cudaGraphExecDestroy(c->graph[k][d]);
-                c->graph[k][d] = nullptr;
-            }
+            for (int n = 0; n < kGraphSizes; ++n)
+                if (c->graph[k][d][n]) {
+                    cudaGraphExecDestroy(c->graph[k][d][n]);
+                    c->graph[k][d][n] = nullptr;
+                }
 }
 
 // Sign of the imposed flow for the step from time level t (+1 before the reversal, -1 from it
@@ -120,22 +125,30 @@ cudaError_t launch_one(lbm_ctx* c, const void* src, void* dst, int sign)
     return with_variant(c->P.precision, c->variant, [&](auto r, auto s, auto v) {
         using R = decltype(r);
         return launch_step<R, decltype(s), decltype(v)::value>(
-            src, dst, c->G, kref<R>(c), c->seg_h, c->block, c->err, sign ? sign : 1, c->st);
+            src, dst, c->G, kref<R>(c), c->seg_h, c->block, c->err, sign ? sign : 1,
+            c->cut_first_wait, c->st);
     });
 }
 
-cudaError_t ensure_graph(lbm_ctx* c, int start, int sign)
+// The graph of 2^(lg+1) steps from buffer `start` with flow sign `sign`, built on first use.
+cudaError_t ensure_graph(lbm_ctx* c, int start, int sign, int lg)
 {
-    cudaGraphExec_t* slot = &c->graph[start][sign < 0 ? 1 : 0];
+    cudaGraphExec_t* slot = &c->graph[start][sign < 0 ? 1 : 0][lg];
     if (*slot) return cudaSuccess;
     const void* a = c->buf + (size_t)start * c->state_bytes;
     const void* b = c->buf + (size_t)(1 - start) * c->state_bytes;
     return with_variant(c->P.precision, c->variant, [&](auto r, auto s, auto v) {
         using R = decltype(r);
         return build_step_graph<R, decltype(s), decltype(v)::value>(
-            a, b, c->G, kref<R>(c), c->seg_h, c->block, c->err, sign ? sign : 1, kGraphChunk,
+            a, b, c->G, kref<R>(c), c->seg_h, c->block, c->err, sign ? sign : 1, 2 << lg,
             slot);
     });
+}
+
+// A new state replaces the one a recorded device error made invalid: clear the error word.
+cudaError_t clear_device_error(lbm_ctx* c)
+{
+    return cudaMemsetAsync(c->err, 0, sizeof(int), c->st);
 }
 
 // Read the step kernel's error word (synchronises the stream).
@@ -317,9 +330,43 @@ constexpr int kNoAllocThreads = 256;
 constexpr long long kNoAllocNodesPerBlock = 2048; // 8 nodes per thread
 static __device__ __align__(256) double g_noalloc_partials[(kNoAllocMaxBlocks + 1) * kReduceSlots];
 
-// Device address of g_noalloc_partials per device ordinal, looked up once per device.
+// Device address of g_noalloc_partials per device ordinal, looked up once per device and CUDA
+// context (a device reset unloads the library image and the array moves).  The context identity
+// comes from the driver's cuCtxGetCurrent / cuCtxGetId, reached through the runtime's entry-point
+// query so that the library keeps no link-time dependency on the driver library.
 std::mutex g_noalloc_mutex;
 double* g_noalloc_ptr[64] = {};
+unsigned long long g_noalloc_ctx[64] = {};
+
+using CtxGetCurrentFn = int (*)(void**);                    // CUresult (CUcontext*)
+using CtxGetIdFn = int (*)(void*, unsigned long long*);     // CUresult (CUcontext, id*)
+
+// Identity of the calling thread's current CUDA context; false if it cannot be determined.
+bool current_context_id(unsigned long long* id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {   // under g_noalloc_mutex
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound;
+        cudaDriverEntryPointQueryResult q2 = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault,
+                                             &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+                cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f2);
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return false;
+    void* ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
 
 __global__ void diag_store_kernel(const double* __restrict__ part, int nblocks, lbm_diag* out)
 {
@@ -376,11 +423,13 @@ int lbm_init_fields_device(lbm_ctx* c, const double* phi, const double* p, const
     if (!c || !phi || !p || !ux || !uy) return LBM_ERR_ARG;
     cudaSetDevice(c->P.device);
     c->cur = 0;
-    cudaError_t e = with_types(c->P.precision, [&](auto r, auto s) {
-        using R = decltype(r);
-        return launch_init<R, decltype(s)>(phi, p, ux, uy, cur_state(c), c->G, kref<R>(c),
-                                           c->st);
-    });
+    cudaError_t e = clear_device_error(c);
+    if (e == cudaSuccess)
+        e = with_types(c->P.precision, [&](auto r, auto s) {
+            using R = decltype(r);
+            return launch_init<R, decltype(s)>(phi, p, ux, uy, cur_state(c), c->G, kref<R>(c),
+                                               c->st);
+        });
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->initialised = true;
     c->steps = 0;
@@ -419,14 +468,18 @@ int lbm_step(lbm_ctx* c, int32_t nsteps)
         long long run = nsteps - k;
         if (sign > 0 && c->P.reverse_step > 0)
             run = std::min<long long>(run, c->P.reverse_step - c->steps);
-        // whole chunks as replays of a prebuilt graph of kGraphChunk launches
-        while (c->use_graph && !c->checked && run >= kGraphChunk) {
-            cudaError_t e = ensure_graph(c, c->cur, sign);
-            if (e == cudaSuccess) e = cudaGraphLaunch(c->graph[c->cur][sign < 0 ? 1 : 0], c->st);
+        // runs of two or more steps as replays of prebuilt graphs of 32, 16, ..., 2 launches
+        while (c->use_graph && !c->checked && !c->cut_first_wait && run >= 2) {
+            int lg = 0;   // chunk = 2^(lg+1) <= run
+            while (lg + 1 < kGraphSizes && (4LL << lg) <= run) ++lg;
+            const int chunk = 2 << lg;
+            cudaError_t e = ensure_graph(c, c->cur, sign, lg);
+            if (e == cudaSuccess)
+                e = cudaGraphLaunch(c->graph[c->cur][sign < 0 ? 1 : 0][lg], c->st);
             if (e != cudaSuccess) return cuda_fail(c, e);
-            k += kGraphChunk;
-            run -= kGraphChunk;
-            c->steps += kGraphChunk;   // even chunk: the current buffer is unchanged
+            k += chunk;
+            run -= chunk;
+            c->steps += chunk;   // even chunk: the current buffer is unchanged
         }
         for (; run > 0; --run, ++k) {
             void* src = cur_state(c);
@@ -444,6 +497,13 @@ int lbm_set_graphs(lbm_ctx* c, int32_t enable)
 {
     if (!c) return LBM_ERR_ARG;
     c->use_graph = enable ? 1 : 0;
+    return LBM_OK;
+}
+
+int lbm_inject_timeout(lbm_ctx* c, int32_t enable)
+{
+    if (!c || enable < 0 || enable > 1) return LBM_ERR_ARG;
+    c->cut_first_wait = enable;
     return LBM_OK;
 }
 
@@ -521,6 +581,7 @@ int lbm_set_populations(lbm_ctx* c, const double* g, const double* f)
         e = cudaMemcpyAsync(tmp + 9 * N, f, 9 * N * sizeof(double), cudaMemcpyHostToDevice,
                             c->st);
     c->cur = 0;
+    if (e == cudaSuccess) e = clear_device_error(c);
     if (e == cudaSuccess)
         e = with_types(c->P.precision, [&](auto r, auto s) {
             return launch_unpack<double, decltype(s)>(tmp, cur_state(c), c->G, c->Kd, c->st);
@@ -549,7 +610,9 @@ int lbm_load_state(lbm_ctx* c, const void* host, size_t bytes, int64_t steps)
     if (!c || !host || bytes != c->state_bytes || steps < 0) return LBM_ERR_ARG;
     cudaSetDevice(c->P.device);
     c->cur = 0;
-    cudaError_t e = cudaMemcpyAsync(cur_state(c), host, bytes, cudaMemcpyHostToDevice, c->st);
+    cudaError_t e = clear_device_error(c);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cur_state(c), host, bytes, cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->initialised = true;
@@ -681,21 +744,32 @@ int lbm_diagnostics_noalloc(const double* phi, const double* p, const double* ux
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LBM_ERR_CUDA;
     double* part = nullptr;
     {
+        // set-up, once per device and context, with that device current
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_ptr[dev]) {
+        unsigned long long ctx_id = 0;
+        const bool have_id = current_context_id(&ctx_id);
+        if (!g_noalloc_ptr[dev] || !have_id || ctx_id != g_noalloc_ctx[dev]) {
             void* addr = nullptr;
             if (cudaGetSymbolAddress(&addr, g_noalloc_partials) != cudaSuccess || !addr)
                 return LBM_ERR_CUDA;
             g_noalloc_ptr[dev] = static_cast<double*>(addr);
+            g_noalloc_ctx[dev] = have_id ? ctx_id : 0;
         }
         part = g_noalloc_ptr[dev];
     }
     const int nb = (int)((N + kNoAllocNodesPerBlock - 1) / kNoAllocNodesPerBlock);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     DiagArgs A{nx, ny, bc_x != LBM_PERIODIC, bc_y != LBM_PERIODIC, xc, yc, r_in, r_out};
-    diag_partial_kernel<<<nb, kNoAllocThreads, 0, st>>>(phi, p, ux, uy, A, part);
-    diag_store_kernel<<<1, 32, 0, st>>>(part, nb, out);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+    // launched through cudaLaunchKernel so that each launch's own status is checked: a CUDA
+    // error the caller left pending is not taken for ours, nor cleared
+    void* a1[] = {(void*)&phi, (void*)&p, (void*)&ux, (void*)&uy, (void*)&A, (void*)&part};
+    cudaError_t e = cudaLaunchKernel((const void*)diag_partial_kernel, dim3(nb),
+                                     dim3(kNoAllocThreads), a1, 0, st);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    int nblocks = nb;
+    void* a2[] = {(void*)&part, (void*)&nblocks, (void*)&out};
+    e = cudaLaunchKernel((const void*)diag_store_kernel, dim3(1), dim3(32), a2, 0, st);
+    return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -26,7 +26,8 @@ using namespace cmlbm;
 
 namespace {
 
-constexpr int kBatchGraphChunk = 32;
+// runs of n >= 2 steps replay graphs of 32, 16, 8, 4 and 2 steps (parity returns after each)
+constexpr int kBatchGraphSizes = 5;
 
 struct HostCase {
     lbm_params P;           // as stored: the reflected problem when tr
@@ -79,7 +80,7 @@ struct lbm_batch {
     int variant;            // step variant shared by all cases (lbm_host.h step_variant)
     int cur;                // shared buffer parity
     int seg_h, block;
-    cudaGraphExec_t graph[2];
+    cudaGraphExec_t graph[2][5];   // 2^(k+1) steps from parity 0 / 1
     int last_cuda;
 };
 
@@ -94,10 +95,11 @@ int fail_cuda(lbm_batch* b, cudaError_t e)
 void drop_batch_graphs(lbm_batch* b)
 {
     for (int k = 0; k < 2; ++k)
-        if (b->graph[k]) {
-            cudaGraphExecDestroy(b->graph[k]);
-            b->graph[k] = nullptr;
-        }
+        for (int n = 0; n < kBatchGraphSizes; ++n)
+            if (b->graph[k][n]) {
+                cudaGraphExecDestroy(b->graph[k][n]);
+                b->graph[k][n] = nullptr;
+            }
 }
 
 // (Re)build the per-case descriptors and the flattened warp-task list for segment height h.
@@ -171,14 +173,14 @@ cudaError_t launch_one(lbm_batch* b)
     });
 }
 
-cudaError_t ensure_graph(lbm_batch* b)
+cudaError_t ensure_graph(lbm_batch* b, int lg)
 {
-    if (b->graph[b->cur]) return cudaSuccess;
+    if (b->graph[b->cur][lg]) return cudaSuccess;
     return with_batch_kernel(b, [&](auto r, auto s, auto v) {
         using R = decltype(r);
         return build_batch_graph<R, decltype(s), decltype(v)::value>(
             b->base, static_cast<BatchCase<R>*>(b->dcases), b->dtasks, b->ntasks, b->cur,
-            b->block, b->err, kBatchGraphChunk, &b->graph[b->cur]);
+            b->block, b->err, 2 << lg, &b->graph[b->cur][lg]);
     });
 }
 
@@ -320,11 +322,13 @@ int lbm_batch_step(lbm_batch* b, int32_t nsteps)
     if (!b || nsteps < 0) return LBM_ERR_ARG;
     cudaSetDevice(b->device);
     int32_t k = 0;
-    while (nsteps - k >= kBatchGraphChunk) {
-        cudaError_t e = ensure_graph(b);
-        if (e == cudaSuccess) e = cudaGraphLaunch(b->graph[b->cur], b->st);
+    while (nsteps - k >= 2) {
+        int lg = 0;   // chunk = 2^(lg+1) <= steps left
+        while (lg + 1 < kBatchGraphSizes && (4LL << lg) <= nsteps - k) ++lg;
+        cudaError_t e = ensure_graph(b, lg);
+        if (e == cudaSuccess) e = cudaGraphLaunch(b->graph[b->cur][lg], b->st);
         if (e != cudaSuccess) return fail_cuda(b, e);
-        k += kBatchGraphChunk;             // even chunk: parity unchanged
+        k += 2 << lg;                      // even chunk: parity unchanged
     }
     for (; k < nsteps; ++k) {
         cudaError_t e = launch_one(b);

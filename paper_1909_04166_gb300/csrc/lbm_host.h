@@ -17,7 +17,7 @@ namespace cmlbm {
 // imposed flow).
 template <typename R, typename S, int V>
 cudaError_t launch_step(const void*, void*, const Geometry&, const Consts<R>&, int, int, int*,
-                        int, cudaStream_t);
+                        int flow_sign, int cut_first_wait, cudaStream_t);
 template <typename R, typename S, int V>
 cudaError_t configure_step(int block);
 template <typename R, typename S, int V>

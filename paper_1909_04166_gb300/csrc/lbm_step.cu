@@ -49,6 +49,8 @@ struct StepLaunch {
     int flow_sign; // imposed flow: +1, or -1 once reversed
     int flip;      // 0 / 1 on alternate steps: reverses the march direction of every segment
     long long chk_shrink;   // checked kernel only: elements left out of the declared buffer ends
+    int cut_first_wait;     // 1: the first mbarrier wait of every warp gives up at once (tests
+                            // of the timeout path); the drain of copies in flight keeps its limit
 };
 
 // Step variants: bit 0 single relaxation time (Sec. 7) instead of the cascaded rates; bit 1 the
@@ -118,6 +120,15 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity)
     for (unsigned it = 0; it < WAIT_LIMIT; ++it)
         if (__all_sync(FULL, mbar_try_wait(bar, parity))) return true;
     return false;
+}
+
+// Programmatic dependent launch: a step launched behind another step of the same graph may be
+// scheduled while its predecessor's last blocks still run; it waits here, before its first
+// access to either state buffer, until the predecessor has finished and its writes are visible.
+// (Without a programmatic predecessor this returns at once.)
+__device__ __forceinline__ void wait_for_previous_step()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 template <typename R>
@@ -519,7 +530,7 @@ template <typename R, typename S, int V, bool CK = false>
 __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__ dst,
                                       const Geometry& G, const Consts<R>& K, int strip, int seg,
                                       int seg_h, int* err, int flow_sign, int flip,
-                                      long long chk_shrink = 0)
+                                      long long chk_shrink = 0, bool cut_first = false)
 {
     constexpr int NS = Stages<S>::value;
     constexpr bool SRT = (V & kVarSRT) != 0;
@@ -618,7 +629,7 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     Row3<R> rb, rc, rn;   // rows behind, current, ahead (in marching order)
     R hl, hr, hl2, hr2;
     halo_load(-1, hl, hr);
-    if (!wait_k(-1, 0)) { fail(-1); return; }
+    if (cut_first || !wait_k(-1, 0)) { fail(-1); return; }
     window_row<R, S, SHEAR>(tiles, lane, wlast, hl, hr, K, rb);
     issue(NS - 1, 0);
     halo_load(0, hl, hr);
@@ -778,7 +789,7 @@ template <typename S, int V, bool CK = false>
 __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict__ dst,
                                        const Geometry& G, const Consts<float>& K, int wstrip,
                                        int seg, int seg_h, int* err, int flow_sign, int flip,
-                                       long long chk_shrink = 0)
+                                       long long chk_shrink = 0, bool cut_first = false)
 {
     constexpr int NS = Stages<S>::value;
     constexpr bool SRT = (V & kVarSRT) != 0;
@@ -886,7 +897,7 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
     Row3P rb, rc, rn;
     float hl, hr, hl2, hr2;
     halo_load(-1, hl, hr);
-    if (!wait_k(-1, 0)) { fail(-1); return; }
+    if (cut_first || !wait_k(-1, 0)) { fail(-1); return; }
     window_row2<S, SHEAR>(tiles, tiles + TB, lane, lastA, lastB, hl, hr, K, rb);
     issue(NS - 1, 0);
     halo_load(0, hl, hr);
@@ -1036,12 +1047,14 @@ __device__ __forceinline__ void step_body(const S* __restrict__ src, S* __restri
     const int strip = warp % wstrips;
     const int seg = warp / wstrips;
     if (seg >= L.nseg) return;                       // warp-uniform
+    wait_for_previous_step();
+    const bool cut = L.cut_first_wait != 0;
     if constexpr (NT == 2)
         march2<S, V, CK>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign, L.flip,
-                         L.chk_shrink);
+                         L.chk_shrink, cut);
     else
         march<R, S, V, CK>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign, L.flip,
-                           L.chk_shrink);
+                           L.chk_shrink, cut);
 }
 
 template <typename R, typename S, int V>
@@ -1109,6 +1122,7 @@ __device__ __forceinline__ void batch_body(S* __restrict__ base,
     const int seg = t.y / wstrips;
     const S* src = base + (parity ? c.off1 : c.off0);
     S* dst = base + (parity ? c.off0 : c.off1);
+    wait_for_previous_step();
     if constexpr (NT == 2) march2<S, V>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1, parity);
     else march<R, S, V>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1, parity);
 }
@@ -1341,7 +1355,8 @@ inline int flip_of(const void* src, const void* dst)
 
 template <typename R, typename S, int V>
 cudaError_t launch_step(const void* src, void* dst, const Geometry& G, const Consts<R>& K,
-                        int seg_h, int block, int* err, int flow_sign, cudaStream_t st)
+                        int seg_h, int block, int* err, int flow_sign, int cut_first_wait,
+                        cudaStream_t st)
 {
     StepLaunch L = {};
     L.seg_h = seg_h;
@@ -1349,6 +1364,7 @@ cudaError_t launch_step(const void* src, void* dst, const Geometry& G, const Con
     L.err = err;
     L.flow_sign = flow_sign;
     L.flip = flip_of(src, dst);
+    L.cut_first_wait = cut_first_wait;
     const long long warps = (long long)step_warp_strips<R, S, V>(G.nstrips) * L.nseg;
     const int wpb = block / 32;
     const long long grid = (warps + wpb - 1) / wpb;
@@ -1387,8 +1403,21 @@ cudaError_t launch_step_checked(const void* src, void* dst, const Geometry& G,
     return cudaGetLastError();
 }
 
-// A graph of `chunk` (even) consecutive steps starting from buffer `a` (a -> b -> a -> ...),
-// replayed by lbm_step to cut the per-launch gaps between steps.
+// Chain `node` behind `prev` in a graph with a programmatic edge: the step of `node` may be
+// scheduled once every block of `prev` has started, and waits in wait_for_previous_step for
+// `prev` to complete before it touches the state.  This hides the launch latency between
+// consecutive steps of a replay.
+inline cudaError_t chain_steps(cudaGraph_t graph, cudaGraphNode_t prev, cudaGraphNode_t node)
+{
+    cudaGraphEdgeData ed = {};
+    ed.from_port = cudaGraphKernelNodePortLaunchCompletion;
+    ed.to_port = 0;
+    ed.type = cudaGraphDependencyTypeProgrammatic;
+    return cudaGraphAddDependencies(graph, &prev, &node, &ed, 1);
+}
+
+// A graph of `chunk` consecutive steps starting from buffer `a` (a -> b -> a -> ...), replayed
+// by lbm_step to cut the per-launch gaps between steps.
 template <typename R, typename S, int V>
 cudaError_t build_step_graph(const void* a, const void* b, const Geometry& G, const Consts<R>& K,
                              int seg_h, int block, int* err, int flow_sign, int chunk,
@@ -1420,7 +1449,8 @@ cudaError_t build_step_graph(const void* a, const void* b, const Geometry& G, co
         p.sharedMemBytes = (unsigned)step_smem_bytes<R, S, V>(block);
         p.kernelParams = args;
         cudaGraphNode_t node;
-        e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &p);
+        e = cudaGraphAddKernelNode(&node, graph, nullptr, 0, &p);
+        if (e == cudaSuccess && prev) e = chain_steps(graph, prev, node);
         prev = node;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
@@ -1451,7 +1481,8 @@ cudaError_t launch_batch_step(void* base, const BatchCase<R>* cases, const int2*
     return cudaGetLastError();
 }
 
-// A graph of `chunk` (even) consecutive batched steps starting from buffer parity `parity0`.
+// A graph of `chunk` consecutive batched steps starting from buffer parity `parity0`, chained
+// like the steps of build_step_graph.
 template <typename R, typename S, int V>
 cudaError_t build_batch_graph(void* base, const BatchCase<R>* cases, const int2* tasks,
                               int ntasks, int parity0, int block, int* err, int chunk,
@@ -1476,7 +1507,8 @@ cudaError_t build_batch_graph(void* base, const BatchCase<R>* cases, const int2*
         p.sharedMemBytes = (unsigned)step_smem_bytes<R, S, V>(block);
         p.kernelParams = args;
         cudaGraphNode_t node;
-        e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &p);
+        e = cudaGraphAddKernelNode(&node, graph, nullptr, 0, &p);
+        if (e == cudaSuccess && prev) e = chain_steps(graph, prev, node);
         prev = node;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
@@ -1533,7 +1565,7 @@ cudaError_t launch_unpack(const double* in, void* state, const Geometry& G, cons
                                                    const Consts<R>&, int, int, int*, int, int,  \
                                                    cudaGraphExec_t*);                           \
     template cudaError_t launch_step<R, S, V>(const void*, void*, const Geometry&,              \
-                                              const Consts<R>&, int, int, int*, int,            \
+                                              const Consts<R>&, int, int, int*, int, int,       \
                                               cudaStream_t);
 
 #define CMLBM_INSTANTIATE(R, S)                                                                   \

@@ -51,6 +51,7 @@ EXPORTS = [
     "lbm_diagnostics", "lbm_set_launch",
     "lbm_get_launch", "lbm_steps_done", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error",
     "lbm_check", "lbm_set_graphs", "lbm_set_checked", "lbm_diagnostics_noalloc",
+    "lbm_inject_timeout",
     "lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_get_fields",
     "lbm_batch_get_populations", "lbm_batch_set_launch", "lbm_batch_get_launch",
     "lbm_batch_tune", "lbm_batch_nodes", "lbm_batch_check", "lbm_batch_destroy",
@@ -138,6 +139,7 @@ def lib(build_if_missing: bool = True):
     L.lbm_check.argtypes = [vp]
     L.lbm_set_graphs.argtypes = [vp, i32]
     L.lbm_set_checked.argtypes = [vp, i32]
+    L.lbm_inject_timeout.argtypes = [vp, i32]
     dd = ctypes.c_double
     L.lbm_diagnostics_noalloc.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, dd, dd, dd, dd,
                                           vp, vp]
@@ -294,6 +296,12 @@ def lbm_set_checked(ctx, enable) -> None:
 
 def lbm_check(ctx) -> None:
     _check(lib().lbm_check(ctx), "lbm_check")
+
+
+def lbm_inject_timeout(ctx, enable: bool) -> None:
+    """Test hook of the failure path: while enabled the first bounded wait of every warp of a
+    step gives up at once (the step reports LBM_ERR_TIMEOUT; nothing faults or hangs)."""
+    _check(lib().lbm_inject_timeout(ctx, int(bool(enable))), "lbm_inject_timeout")
 
 
 def lbm_diagnostics(ctx, xc=0.0, yc=0.0, r_in=-1.0, r_out=0.0, allow_nonfinite=True) -> dict:

@@ -99,14 +99,19 @@ def test_launch_shape_does_not_change_results(prec):
         assert np.array_equal(g, outs[0][0]) and np.array_equal(f, outs[0][1])
 
 
-def test_graph_replays_match_single_launches():
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
+def test_graph_replays_match_single_launches(precision):
+    """Runs of every length (graphs of 32, 16, 8, 4 and 2 chained launches, a last odd step
+    alone) give the same state, bit for bit, as one launch per step."""
     case = W.random_drop(64, 48, seed=12, wall_y=True, rho_ratio=100.0)
     outs = []
     for graphs in (False, True):
-        with lbm.Simulation(case, precision="fp32") as sim:
+        with lbm.Simulation(case, precision=precision) as sim:
             sim.init_case()
             lbm.lbm_set_graphs(sim.ctx, graphs)
-            sim.step(70).step(33)
+            for n in (70, 33, 20, 3, 2, 1, 17, 31):
+                sim.step(n)
+            assert lbm.lbm_steps_done(sim.ctx) == 177
             outs.append(sim.populations())
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
 

@@ -266,3 +266,59 @@ def test_step_is_equivariant_under_the_diagonal_reflection(extra):
     assert np.linalg.norm(g_back - g) <= 1e-12 * np.linalg.norm(g)
     assert np.linalg.norm(f_back - f) <= 1e-12 * np.linalg.norm(f)
     assert np.linalg.norm(g - g[:, :, ::-1]) > 1e-3 * np.linalg.norm(g)   # not trivially symmetric
+
+
+# ---------------------------------------------------------------------------------------------
+# Reading R6: the regularised interface normal n = grad phi / (|grad phi| + eps), eps = 1e-6.
+# Sec. 2 defines n = grad phi / |grad phi| and leaves it undefined where grad phi vanishes.  Two
+# pins bracket eps: inside a bulk phase the conservative Allen-Cahn equation has no interface to
+# sharpen (theta = 4 phi (1 - phi)/W ~ 0) and reduces to the diffusion equation
+# d phi/dt = M_phi lap phi, which must hold for rounding-sized departures of phi from 0 or 1
+# (rejects eps below ~4e-7: the sharpening flux M theta n then acts on the noise at a fixed
+# magnitude and amplifies it); and the flat tanh profile of Sec. 2 must stay the interface's
+# equilibrium (rejects eps above ~1e-4: |n| < 1 in the profile's tails shifts the balance).
+# ---------------------------------------------------------------------------------------------
+def bulk_mode_decay(phi0, nsteps=500, n=32, amp=1e-10):
+    """Amplitude ratio after nsteps of a sine mode of phi (wavelength n) riding on a uniform
+    bulk value phi0, and the largest departure from a pure sine relative to amp."""
+    x = np.arange(n)
+    mode = np.sin(2.0 * np.pi * x / n)
+    phi = np.tile(phi0 + amp * mode, (4, 1))
+    oc = O.OracleCase(nx=n, ny=4, rho_a=1.0, rho_b=0.001, mu_a=0.1, mu_b=1e-4, sigma0=1e-3,
+                      mobility=0.02, width=4.0)
+    g, f = O.run(oc, *O.init(oc, phi, 0.0, 0.0, 0.0), nsteps)
+    row = O.fields(oc, g, f)["phi"][0]
+    d = row - row.mean()
+    a = 2.0 * float(np.dot(d, mode)) / n
+    return a / amp, float(np.abs(d - a * mode).max()) / amp
+
+
+@pytest.mark.parametrize("phi0", [1.0 - 5e-8, 5e-8])
+def test_bulk_phase_noise_diffuses_at_the_mobility(phi0):
+    """R6 pin (lower side): a 1e-10 sine mode in a bulk phase 5e-8 away from phi_A or phi_B
+    decays like the diffusion equation's exp(-M_phi k^2 t) (3 %, the lattice and the residual
+    theta / eps = 0.05 of the regularisation) and stays a sine mode."""
+    nsteps, n, M = 500, 32, 0.02
+    ratio, resid = bulk_mode_decay(phi0, nsteps, n)
+    k = 2.0 * np.pi / n
+    assert ratio == pytest.approx(np.exp(-M * k * k * nsteps), rel=0.03)
+    assert resid < 1e-3
+
+
+def test_normal_regularisation_pins_reject_other_eps():
+    """The two R6 pins fail for an eps far from 1e-6: with 1e-9 or the cut-off 1e-24 the bulk
+    mode grows instead of decaying; with 1e-3 the flat interface leaves its tanh profile."""
+    default = O.normal_eps()
+    assert default == 1e-6
+    try:
+        for eps in (1e-24, 1e-9):
+            O.set_normal_eps(eps)
+            ratio, _ = bulk_mode_decay(1.0 - 5e-8)
+            assert abs(ratio) > 5.0, eps
+        O.set_normal_eps(1e-3)
+        width = 8.0
+        case = W.flat(nx=4, ny=int(16 * width), width=width, mobility=0.05, rho_ratio=10.0)
+        _, _, _, fl = run_case(case, 2000)
+        assert np.abs(fl["phi"] - case["fields"]["phi"]).max() > 0.11 / width ** 2
+    finally:
+        O.set_normal_eps(default)
