@@ -207,8 +207,10 @@ int lbm_init_fields_device(lbm_ctx* ctx, const double* phi, const double* p, con
 
 /* Advance nsteps (>= 0) time steps: one fused kernel launch per step on params.stream,
  * asynchronous; launch errors are returned.  A run of two or more steps is issued as replays of
- * CUDA graphs of 32, 16, 8, 4 and 2 launches (largest first; built on first use, see
- * lbm_set_graphs), a last odd step as a single launch.  Inside a graph each launch is chained to
+ * CUDA graphs of 32, 16, 8, 4 and 2 launches (largest first), a last odd step as a single
+ * launch.  The first call that needs a graph builds all of them (every size, from either state
+ * buffer; a few milliseconds), so later calls of any length launch at once; lbm_set_launch
+ * drops them, lbm_set_graphs switches them off.  Inside a graph each launch is chained to
  * the previous one by a programmatic dependency: it may be scheduled while the previous step's
  * last blocks still run and waits on the device, before touching the state, until that step has
  * completed, so the launch latency between steps is hidden. */

@@ -130,8 +130,8 @@ cudaError_t launch_one(lbm_ctx* c, const void* src, void* dst, int sign)
     });
 }
 
-// The graph of 2^(lg+1) steps from buffer `start` with flow sign `sign`, built on first use.
-cudaError_t ensure_graph(lbm_ctx* c, int start, int sign, int lg)
+// The graph of 2^(lg+1) steps from buffer `start` with flow sign `sign`.
+cudaError_t build_graph(lbm_ctx* c, int start, int sign, int lg)
 {
     cudaGraphExec_t* slot = &c->graph[start][sign < 0 ? 1 : 0][lg];
     if (*slot) return cudaSuccess;
@@ -149,6 +149,17 @@ cudaError_t ensure_graph(lbm_ctx* c, int start, int sign, int lg)
 cudaError_t clear_device_error(lbm_ctx* c)
 {
     return cudaMemsetAsync(c->err, 0, sizeof(int), c->st);
+}
+
+// Every graph size from both start buffers for flow sign `sign`, built together the first time
+// any of them is needed, so that later runs of any length (and parity) launch without building.
+cudaError_t ensure_graphs(lbm_ctx* c, int sign)
+{
+    cudaError_t e = cudaSuccess;
+    for (int start = 0; start < 2 && e == cudaSuccess; ++start)
+        for (int lg = 0; lg < kGraphSizes && e == cudaSuccess; ++lg)
+            e = build_graph(c, start, sign, lg);
+    return e;
 }
 
 // Read the step kernel's error word (synchronises the stream).
@@ -473,7 +484,7 @@ int lbm_step(lbm_ctx* c, int32_t nsteps)
             int lg = 0;   // chunk = 2^(lg+1) <= run
             while (lg + 1 < kGraphSizes && (4LL << lg) <= run) ++lg;
             const int chunk = 2 << lg;
-            cudaError_t e = ensure_graph(c, c->cur, sign, lg);
+            cudaError_t e = ensure_graphs(c, sign);
             if (e == cudaSuccess)
                 e = cudaGraphLaunch(c->graph[c->cur][sign < 0 ? 1 : 0][lg], c->st);
             if (e != cudaSuccess) return cuda_fail(c, e);

@@ -173,15 +173,21 @@ cudaError_t launch_one(lbm_batch* b)
     });
 }
 
-cudaError_t ensure_graph(lbm_batch* b, int lg)
+// Every graph size from both buffer parities, built together the first time any is needed.
+cudaError_t ensure_graphs(lbm_batch* b)
 {
-    if (b->graph[b->cur][lg]) return cudaSuccess;
-    return with_batch_kernel(b, [&](auto r, auto s, auto v) {
-        using R = decltype(r);
-        return build_batch_graph<R, decltype(s), decltype(v)::value>(
-            b->base, static_cast<BatchCase<R>*>(b->dcases), b->dtasks, b->ntasks, b->cur,
-            b->block, b->err, 2 << lg, &b->graph[b->cur][lg]);
-    });
+    cudaError_t e = cudaSuccess;
+    for (int par = 0; par < 2 && e == cudaSuccess; ++par)
+        for (int lg = 0; lg < kBatchGraphSizes && e == cudaSuccess; ++lg) {
+            if (b->graph[par][lg]) continue;
+            e = with_batch_kernel(b, [&](auto r, auto s, auto v) {
+                using R = decltype(r);
+                return build_batch_graph<R, decltype(s), decltype(v)::value>(
+                    b->base, static_cast<BatchCase<R>*>(b->dcases), b->dtasks, b->ntasks, par,
+                    b->block, b->err, 2 << lg, &b->graph[par][lg]);
+            });
+        }
+    return e;
 }
 
 template <typename R> const Consts<R>& kref(const HostCase& hc);
@@ -325,7 +331,7 @@ int lbm_batch_step(lbm_batch* b, int32_t nsteps)
     while (nsteps - k >= 2) {
         int lg = 0;   // chunk = 2^(lg+1) <= steps left
         while (lg + 1 < kBatchGraphSizes && (4LL << lg) <= nsteps - k) ++lg;
-        cudaError_t e = ensure_graph(b, lg);
+        cudaError_t e = ensure_graphs(b);
         if (e == cudaSuccess) e = cudaGraphLaunch(b->graph[b->cur][lg], b->st);
         if (e != cudaSuccess) return fail_cuda(b, e);
         k += 2 << lg;                      // even chunk: parity unchanged

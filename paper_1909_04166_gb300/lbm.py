@@ -298,10 +298,10 @@ def lbm_check(ctx) -> None:
     _check(lib().lbm_check(ctx), "lbm_check")
 
 
-def lbm_inject_timeout(ctx, enable: bool) -> None:
+def lbm_inject_timeout(ctx, enable) -> None:
     """Test hook of the failure path: while enabled the first bounded wait of every warp of a
     step gives up at once (the step reports LBM_ERR_TIMEOUT; nothing faults or hangs)."""
-    _check(lib().lbm_inject_timeout(ctx, int(bool(enable))), "lbm_inject_timeout")
+    _check(lib().lbm_inject_timeout(ctx, int(enable)), "lbm_inject_timeout")
 
 
 def lbm_diagnostics(ctx, xc=0.0, yc=0.0, r_in=-1.0, r_out=0.0, allow_nonfinite=True) -> dict:
