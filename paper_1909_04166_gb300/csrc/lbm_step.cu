@@ -122,15 +122,6 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
-// Programmatic dependent launch: a step launched behind another step of the same graph may be
-// scheduled while its predecessor's last blocks still run; it waits here, before its first
-// access to either state buffer, until the predecessor has finished and its writes are visible.
-// (Without a programmatic predecessor this returns at once.)
-__device__ __forceinline__ void wait_for_previous_step()
-{
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
 template <typename R>
 __device__ __forceinline__ R shfl_up(R v) { return __shfl_up_sync(FULL, v, 1); }
 template <typename R>
@@ -1047,7 +1038,6 @@ __device__ __forceinline__ void step_body(const S* __restrict__ src, S* __restri
     const int strip = warp % wstrips;
     const int seg = warp / wstrips;
     if (seg >= L.nseg) return;                       // warp-uniform
-    wait_for_previous_step();
     const bool cut = L.cut_first_wait != 0;
     if constexpr (NT == 2)
         march2<S, V, CK>(src, dst, G, K, strip, seg, L.seg_h, L.err, L.flow_sign, L.flip,
@@ -1122,7 +1112,6 @@ __device__ __forceinline__ void batch_body(S* __restrict__ base,
     const int seg = t.y / wstrips;
     const S* src = base + (parity ? c.off1 : c.off0);
     S* dst = base + (parity ? c.off0 : c.off1);
-    wait_for_previous_step();
     if constexpr (NT == 2) march2<S, V>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1, parity);
     else march<R, S, V>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1, parity);
 }
@@ -1403,19 +1392,6 @@ cudaError_t launch_step_checked(const void* src, void* dst, const Geometry& G,
     return cudaGetLastError();
 }
 
-// Chain `node` behind `prev` in a graph with a programmatic edge: the step of `node` may be
-// scheduled once every block of `prev` has started, and waits in wait_for_previous_step for
-// `prev` to complete before it touches the state.  This hides the launch latency between
-// consecutive steps of a replay.
-inline cudaError_t chain_steps(cudaGraph_t graph, cudaGraphNode_t prev, cudaGraphNode_t node)
-{
-    cudaGraphEdgeData ed = {};
-    ed.from_port = cudaGraphKernelNodePortLaunchCompletion;
-    ed.to_port = 0;
-    ed.type = cudaGraphDependencyTypeProgrammatic;
-    return cudaGraphAddDependencies(graph, &prev, &node, &ed, 1);
-}
-
 // A graph of `chunk` consecutive steps starting from buffer `a` (a -> b -> a -> ...), replayed
 // by lbm_step to cut the per-launch gaps between steps.
 template <typename R, typename S, int V>
@@ -1449,8 +1425,7 @@ cudaError_t build_step_graph(const void* a, const void* b, const Geometry& G, co
         p.sharedMemBytes = (unsigned)step_smem_bytes<R, S, V>(block);
         p.kernelParams = args;
         cudaGraphNode_t node;
-        e = cudaGraphAddKernelNode(&node, graph, nullptr, 0, &p);
-        if (e == cudaSuccess && prev) e = chain_steps(graph, prev, node);
+        e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &p);
         prev = node;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
@@ -1481,8 +1456,7 @@ cudaError_t launch_batch_step(void* base, const BatchCase<R>* cases, const int2*
     return cudaGetLastError();
 }
 
-// A graph of `chunk` consecutive batched steps starting from buffer parity `parity0`, chained
-// like the steps of build_step_graph.
+// A graph of `chunk` consecutive batched steps starting from buffer parity `parity0`.
 template <typename R, typename S, int V>
 cudaError_t build_batch_graph(void* base, const BatchCase<R>* cases, const int2* tasks,
                               int ntasks, int parity0, int block, int* err, int chunk,
@@ -1507,8 +1481,7 @@ cudaError_t build_batch_graph(void* base, const BatchCase<R>* cases, const int2*
         p.sharedMemBytes = (unsigned)step_smem_bytes<R, S, V>(block);
         p.kernelParams = args;
         cudaGraphNode_t node;
-        e = cudaGraphAddKernelNode(&node, graph, nullptr, 0, &p);
-        if (e == cudaSuccess && prev) e = chain_steps(graph, prev, node);
+        e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &p);
         prev = node;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);

@@ -64,6 +64,34 @@ def oracle_series(case, checkpoints=CHECKPOINTS, mode="fp64") -> dict:
     return out
 
 
+def ulp_spread(case, checkpoints, seeds=(0, 1, 2)) -> dict:
+    """The oracle's own response to a one-ulp change of its initial state: for each checkpoint,
+    the largest relative L2 deviation (fields and populations g, f) over runs whose initial
+    populations carry i.i.d. relative noise of 2^-52 (seeded), from the plain run."""
+    oc = O.OracleCase.from_dict(case.params)
+    fl = case["fields"]
+    g0, f0 = O.init(oc, fl["phi"], fl["p"], fl["ux"], fl["uy"])
+
+    def series(g, f):
+        out, t = {}, 0
+        for c in checkpoints:
+            g, f = O.run(oc, g, f, c - t)
+            t = c
+            out[c] = dict(O.fields(oc, g, f), g=g, f=f)
+        return out
+
+    ref = series(g0, f0)
+    worst = {c: dict.fromkeys(FIELDS + ("g", "f"), 0.0) for c in checkpoints}
+    for s in seeds:
+        rng = np.random.default_rng(s)
+        run = series(g0 * (1 + 2.0 ** -52 * rng.standard_normal(g0.shape)),
+                     f0 * (1 + 2.0 ** -52 * rng.standard_normal(f0.shape)))
+        for c in checkpoints:
+            for k in worst[c]:
+                worst[c][k] = max(worst[c][k], rel_l2(run[c][k], ref[c][k]))
+    return {"ref": ref, "spread": worst}
+
+
 def gpu_series(case, precision, checkpoints=CHECKPOINTS) -> dict:
     """Library fields at each checkpoint (the default launch, graph replays as lbm_step issues
     them)."""
