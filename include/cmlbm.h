@@ -207,10 +207,11 @@ int lbm_init_fields_device(lbm_ctx* ctx, const double* phi, const double* p, con
 
 /* Advance nsteps (>= 0) time steps: one fused kernel launch per step on params.stream,
  * asynchronous; launch errors are returned.  A run of two or more steps is issued as replays of
- * CUDA graphs of 32, 16, 8, 4 and 2 launches (largest first), a last odd step as a single
- * launch.  The first call that needs a graph builds all of them (every size, from either state
- * buffer; a few milliseconds), so later calls of any length launch at once; lbm_set_launch
- * drops them, lbm_set_graphs switches them off. */
+ * CUDA graphs: graphs of 32 launches while 32 or more steps are left, then one graph for the
+ * even rest (2 .. 30 launches), a last odd step as a single launch.  The first call that needs
+ * a graph builds all of them (every even size up to 32, from either state buffer; a few
+ * milliseconds), so later calls of any length launch at once; lbm_set_launch drops them,
+ * lbm_set_graphs switches them off. */
 int lbm_step(lbm_ctx* ctx, int32_t nsteps);
 
 /* Enable (default) or disable the graph replays of lbm_step; results are identical. */
@@ -330,8 +331,8 @@ int lbm_diagnostics_noalloc(const double* phi, const double* p, const double* ux
  * Batches: many independent cases (any mix of grid sizes, boundaries and physical parameters)
  * advanced together.  Every lbm_batch_step advances all cases by one time step with ONE launch
  * of the batched step kernel (each warp takes one strip x segment task of one case from a
- * flattened task list); runs of two or more steps are replays of CUDA graphs of 32, 16, 8, 4 and
- * 2 launches as in lbm_step.  The per-node arithmetic
+ * flattened task list); runs of two or more steps are replays of CUDA graphs as in lbm_step.
+ * The per-node arithmetic
  * is the one of lbm_step.  A warp owns strips of 64 columns (32 in FP64), so a case whose width
  * is not a multiple of that leaves lanes idle; lbm_batch_create therefore stores each case in
  * the orientation whose padded strips cover fewer nodes (LBM_BATCH_FEWEST_COLUMNS): a case

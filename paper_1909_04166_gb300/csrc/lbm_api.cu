@@ -34,8 +34,8 @@ struct lbm_ctx {
     double* partials;      // reduction partials
     int* err;              // device error word of the step kernel (bounded waits)
     int variant;           // step variant (lbm_host.h step_variant)
-    // graphs of 2^(k+1) steps (k < kGraphSizes) from buffer 0 / 1, flow sign + / -
-    cudaGraphExec_t graph[2][2][5];
+    // graphs of 2 (k + 1) steps (k < kGraphSizes) from buffer 0 / 1, flow sign + / -
+    cudaGraphExec_t graph[2][2][16];
     int use_graph;
     int cut_first_wait;    // lbm_inject_timeout
     int checked;           // steps run through the bounds-checked kernel (lbm_set_checked)
@@ -46,9 +46,10 @@ struct lbm_ctx {
 namespace {
 
 constexpr int kReduceSlots = 8;
-// Runs of n >= 2 steps replay graphs of 32, 16, 8, 4 and 2 steps (even: the buffer parity
-// returns); a last odd step is a single launch.
-constexpr int kGraphSizes = 5;
+// Runs of n >= 2 steps replay graphs of an even number of steps, 2 .. 32 (even: the buffer
+// parity returns): 32-step graphs while at least 32 steps are left, then one graph for the even
+// rest; a last odd step is a single launch.
+constexpr int kGraphSizes = 16;
 
 template <typename R> const Consts<R>& kref(const lbm_ctx* c);
 template <> const Consts<double>& kref<double>(const lbm_ctx* c) { return c->Kd; }
@@ -130,17 +131,17 @@ cudaError_t launch_one(lbm_ctx* c, const void* src, void* dst, int sign)
     });
 }
 
-// The graph of 2^(lg+1) steps from buffer `start` with flow sign `sign`.
-cudaError_t build_graph(lbm_ctx* c, int start, int sign, int lg)
+// The graph of 2 (k + 1) steps from buffer `start` with flow sign `sign`.
+cudaError_t build_graph(lbm_ctx* c, int start, int sign, int k)
 {
-    cudaGraphExec_t* slot = &c->graph[start][sign < 0 ? 1 : 0][lg];
+    cudaGraphExec_t* slot = &c->graph[start][sign < 0 ? 1 : 0][k];
     if (*slot) return cudaSuccess;
     const void* a = c->buf + (size_t)start * c->state_bytes;
     const void* b = c->buf + (size_t)(1 - start) * c->state_bytes;
     return with_variant(c->P.precision, c->variant, [&](auto r, auto s, auto v) {
         using R = decltype(r);
         return build_step_graph<R, decltype(s), decltype(v)::value>(
-            a, b, c->G, kref<R>(c), c->seg_h, c->block, c->err, sign ? sign : 1, 2 << lg,
+            a, b, c->G, kref<R>(c), c->seg_h, c->block, c->err, sign ? sign : 1, 2 * (k + 1),
             slot);
     });
 }
@@ -157,8 +158,8 @@ cudaError_t ensure_graphs(lbm_ctx* c, int sign)
 {
     cudaError_t e = cudaSuccess;
     for (int start = 0; start < 2 && e == cudaSuccess; ++start)
-        for (int lg = 0; lg < kGraphSizes && e == cudaSuccess; ++lg)
-            e = build_graph(c, start, sign, lg);
+        for (int k = 0; k < kGraphSizes && e == cudaSuccess; ++k)
+            e = build_graph(c, start, sign, k);
     return e;
 }
 
@@ -479,14 +480,12 @@ int lbm_step(lbm_ctx* c, int32_t nsteps)
         long long run = nsteps - k;
         if (sign > 0 && c->P.reverse_step > 0)
             run = std::min<long long>(run, c->P.reverse_step - c->steps);
-        // runs of two or more steps as replays of prebuilt graphs of 32, 16, ..., 2 launches
+        // runs of two or more steps as replays of prebuilt graphs of 2 .. 32 launches
         while (c->use_graph && !c->checked && !c->cut_first_wait && run >= 2) {
-            int lg = 0;   // chunk = 2^(lg+1) <= run
-            while (lg + 1 < kGraphSizes && (4LL << lg) <= run) ++lg;
-            const int chunk = 2 << lg;
+            const int chunk = (int)std::min<long long>(run & ~1LL, 2 * kGraphSizes);
             cudaError_t e = ensure_graphs(c, sign);
             if (e == cudaSuccess)
-                e = cudaGraphLaunch(c->graph[c->cur][sign < 0 ? 1 : 0][lg], c->st);
+                e = cudaGraphLaunch(c->graph[c->cur][sign < 0 ? 1 : 0][chunk / 2 - 1], c->st);
             if (e != cudaSuccess) return cuda_fail(c, e);
             k += chunk;
             run -= chunk;

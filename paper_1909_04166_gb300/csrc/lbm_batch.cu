@@ -26,8 +26,9 @@ using namespace cmlbm;
 
 namespace {
 
-// runs of n >= 2 steps replay graphs of 32, 16, 8, 4 and 2 steps (parity returns after each)
-constexpr int kBatchGraphSizes = 5;
+// runs of n >= 2 steps replay graphs of an even number of steps, 2 .. 32 (32-step graphs while at
+// least 32 steps are left, then one for the even rest; the parity returns after each)
+constexpr int kBatchGraphSizes = 16;
 
 struct HostCase {
     lbm_params P;           // as stored: the reflected problem when tr
@@ -80,7 +81,7 @@ struct lbm_batch {
     int variant;            // step variant shared by all cases (lbm_host.h step_variant)
     int cur;                // shared buffer parity
     int seg_h, block;
-    cudaGraphExec_t graph[2][5];   // 2^(k+1) steps from parity 0 / 1
+    cudaGraphExec_t graph[2][16];  // 2 (k + 1) steps from parity 0 / 1
     int last_cuda;
 };
 
@@ -178,13 +179,13 @@ cudaError_t ensure_graphs(lbm_batch* b)
 {
     cudaError_t e = cudaSuccess;
     for (int par = 0; par < 2 && e == cudaSuccess; ++par)
-        for (int lg = 0; lg < kBatchGraphSizes && e == cudaSuccess; ++lg) {
-            if (b->graph[par][lg]) continue;
+        for (int k = 0; k < kBatchGraphSizes && e == cudaSuccess; ++k) {
+            if (b->graph[par][k]) continue;
             e = with_batch_kernel(b, [&](auto r, auto s, auto v) {
                 using R = decltype(r);
                 return build_batch_graph<R, decltype(s), decltype(v)::value>(
                     b->base, static_cast<BatchCase<R>*>(b->dcases), b->dtasks, b->ntasks, par,
-                    b->block, b->err, 2 << lg, &b->graph[par][lg]);
+                    b->block, b->err, 2 * (k + 1), &b->graph[par][k]);
             });
         }
     return e;
@@ -329,12 +330,11 @@ int lbm_batch_step(lbm_batch* b, int32_t nsteps)
     cudaSetDevice(b->device);
     int32_t k = 0;
     while (nsteps - k >= 2) {
-        int lg = 0;   // chunk = 2^(lg+1) <= steps left
-        while (lg + 1 < kBatchGraphSizes && (4LL << lg) <= nsteps - k) ++lg;
+        const int chunk = std::min((nsteps - k) & ~1, 2 * kBatchGraphSizes);
         cudaError_t e = ensure_graphs(b);
-        if (e == cudaSuccess) e = cudaGraphLaunch(b->graph[b->cur][lg], b->st);
+        if (e == cudaSuccess) e = cudaGraphLaunch(b->graph[b->cur][chunk / 2 - 1], b->st);
         if (e != cudaSuccess) return fail_cuda(b, e);
-        k += 2 << lg;                      // even chunk: parity unchanged
+        k += chunk;                        // even chunk: parity unchanged
     }
     for (; k < nsteps; ++k) {
         cudaError_t e = launch_one(b);

@@ -2,39 +2,43 @@
 
 * One step at the bench workload (2048 x 1024 drop impact, density ratio 1000, default launch as
   bench.py times it): GPU vs the FP64 oracle stepping the same state, element by element.
-* 1000 steps: the step map of the method amplifies perturbations (interface over/undershoot
-  takes phi outside [0, 1], where theta n acts on small gradients; at impact the flow itself is
-  sensitive), so two FP64 runs whose initial states differ by rounding-sized noise no longer
-  agree to 1e-12 after 1000 steps.  The acceptance criterion bounds the GPU's deviation from
-  the reference by the reference's own deviation when its initial populations are perturbed by
-  the worst-case accumulated rounding of the GPU precision over the horizon, N u (u = 2^-53 for
-  FP64, 2^-24 for FP32), times 2 (a single perturbed run estimates that spread only roughly once
-  it saturates), or by the fixed tolerance (1e-12 FP64, 2e-5 FP32) if that is larger.
-  Reference: the oracle where it finishes in seconds (Marangoni 512 x 256, Rayleigh-Taylor
-  256 x 1024); for the 2048 x 1024 impact the GPU FP64 mode (pinned to the oracle above).
+* 100 and 1000 steps on the Marangoni drop (512 x 256, density ratio 10), Rayleigh-Taylor
+  (256 x 1024, Atwood 0.5) and the impact, against the FP64 oracle.  The step map amplifies
+  perturbations (tests/_conditioning.py): a 2^-52 change of the oracle's initial state grows to
+  3e-5 within 100 steps on Rayleigh-Taylor and saturates near 1.5e-3 by 1000, so a fixed
+  element-wise tolerance cannot hold there for any implementation that rounds differently.  The
+  gates are therefore set by what rounding alone does in the oracle, measured in the test:
+    - FP32: the FP64 oracle with its populations rounded to float32 after every step (FP32
+      storage, FP64 arithmetic) and, where it is larger, its one-ulp spread.  The FP32 step also
+      rounds its arithmetic: every population passes through about ten roundings at its own
+      scale per step (zeroth-moment sums, the interface collision's moments and their inverse,
+      the fluid source terms) against one for storage.  On the well-conditioned Marangoni drop
+      the FP32 deviation is 5 - 13 times the storage-alone deviation; evaluating the interface
+      collision in double about halves it, the fluid collision or the forces in double change it
+      by under 15 % (measured with variants of the kernel that evaluate one part in double, not
+      part of the library).  The gate is max(2e-5, 16 x that reference).
+    - FP64: 1e-12, or twenty times the oracle's one-ulp spread where that is larger (the
+      library's fused multiply-adds and evaluation order differ from the oracle's by a few ulps
+      per step).
 * Strict FP32 gate on a well-conditioned case: phi and p within 2e-5 after 1000 steps.
 """
 import numpy as np
 import pytest
 
+import _conditioning as C
 from oracle import oracle as O
 from paper_1909_04166_gb300 import lbm
 from paper_1909_04166_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
-FIELDS = ("phi", "p", "ux", "uy")
+
+CHECKS = (100, 1000)
+FP32_FACTOR = 16.0
+FP64_FACTOR = 20.0
 
 
 def rel_l2(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-
-
-def oracle_fields(case, nsteps):
-    oc = O.OracleCase.from_dict(case.params)
-    fl = case["fields"]
-    g, f = O.init(oc, fl["phi"], fl["p"], fl["ux"], fl["uy"])
-    g, f = O.run(oc, g, f, nsteps)
-    return O.fields(oc, g, f)
+    return C.rel_l2(a, b)
 
 
 @pytest.fixture(scope="module")
@@ -53,64 +57,54 @@ def test_one_step_at_full_size(impact_case, prec, tol):
     g_ref, f_ref = O.step(oc, g0, f0)
     assert rel_l2(g1, g_ref) <= tol
     assert rel_l2(f1, f_ref) <= tol
-    # sampled nodes, element by element (interface, film, wall rows, periodic seam)
-    for (x, y) in [(1024, 120), (1024, 20), (0, 0), (2047, 1023), (900, 200), (1100, 5)]:
-        for a in range(9):
-            assert abs(g1[a, y, x] - g_ref[a, y, x]) <= 1e-5 * np.abs(g_ref).max()
-            assert abs(f1[a, y, x] - f_ref[a, y, x]) <= 1e-5
+    # every node, element by element, against the scale of each lattice
+    assert np.abs(g1 - g_ref).max() <= (1e-13 if prec == "fp64" else 1e-6) * np.abs(g_ref).max()
+    assert np.abs(f1 - f_ref).max() <= (1e-13 if prec == "fp64" else 1e-6) * np.abs(f_ref).max()
 
 
-NSTEPS = 1000
-UNIT = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24}
-TOL = {"fp64": 1e-12, "fp32": 2e-5}
+_REFS = {}
 
 
-def perturb_pops(g, f, eps, seed=1):
-    rng = np.random.default_rng(seed)
-    return (g * (1 + eps * rng.standard_normal(g.shape)),
-            f * (1 + eps * rng.standard_normal(f.shape)))
+def references(name):
+    """The oracle's plain FP64 fields at CHECKS, the float32-storage deviation and (except for
+    the impact, where it costs another minute of host time and the storage deviation is of the
+    same size) the one-ulp spread; computed once per case."""
+    if name not in _REFS:
+        case = C.CASES[name]()
+        if name == "impact":
+            ref = C.oracle_series(case, CHECKS, "fp64")
+            ulp = None
+        else:
+            u = C.ulp_spread(case, CHECKS, seeds=(0,))
+            ref, ulp = u["ref"], u["spread"]
+        stor = C.deviations(C.oracle_series(case, CHECKS, "float_storage"), ref)
+        _REFS[name] = (case, ref, stor, ulp)
+    return _REFS[name]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["marangoni", "rt", "impact"])
+def test_fp32_horizon_within_rounding_conditioning(name):
+    case, ref, stor, ulp = references(name)
+    got = C.deviations(C.gpu_series(case, "fp32", CHECKS), ref)
+    for c in CHECKS:
+        for k in C.FIELDS:
+            floor = max(stor[c][k], ulp[c][k] if ulp else 0.0)
+            assert got[c][k] <= max(2e-5, FP32_FACTOR * floor), (c, k, got[c][k], floor)
+
+
 @pytest.mark.parametrize("name", ["marangoni", "rt"])
-def test_1000_steps_against_oracle_within_conditioning(name, prec):
-    case = W.marangoni() if name == "marangoni" else W.rt()
-    oc = O.OracleCase.from_dict(case.params)
-    fl = case["fields"]
-    g0, f0 = O.init(oc, fl["phi"], fl["p"], fl["ux"], fl["uy"])
-    ref = O.fields(oc, *O.run(oc, g0, f0, NSTEPS))
-    gp, fp = perturb_pops(g0, f0, NSTEPS * UNIT[prec])
-    floor_run = O.fields(oc, *O.run(oc, gp, fp, NSTEPS))
-    with lbm.Simulation(case, precision=prec) as sim:
-        got = sim.init_case().step(NSTEPS).fields()
-    for k in FIELDS:
-        floor = rel_l2(floor_run[k], ref[k])
-        dev = rel_l2(got[k], ref[k])
-        assert dev <= max(TOL[prec], 2.0 * floor), (k, dev, floor)
-
-
-def test_impact_1000_steps_within_conditioning(impact_case):
-    with lbm.Simulation(impact_case, "fp64") as a, \
-            lbm.Simulation(impact_case, "fp64") as b, \
-            lbm.Simulation(impact_case, "fp32") as c:
-        a.init_case()
-        g0, f0 = a.populations()
-        ref = a.step(NSTEPS).fields()
-        b.set_populations(*perturb_pops(g0, f0, NSTEPS * UNIT["fp32"]))
-        floor_run = b.step(NSTEPS).fields()
-        got = c.init_case().step(NSTEPS).fields()
-    for k in FIELDS:
-        floor = rel_l2(floor_run[k], ref[k])
-        dev = rel_l2(got[k], ref[k])
-        assert dev <= max(TOL["fp32"], 2.0 * floor), (k, dev, floor)
+def test_fp64_horizon_within_ulp_spread(name):
+    case, ref, _, ulp = references(name)
+    got = C.deviations(C.gpu_series(case, "fp64", CHECKS), ref)
+    for c in CHECKS:
+        for k in C.FIELDS:
+            assert got[c][k] <= max(1e-12, FP64_FACTOR * ulp[c][k]), (c, k, got[c][k], ulp[c][k])
 
 
 def test_fp32_strict_gate_on_a_well_conditioned_case():
     """Marangoni drop (density ratio 10): phi and p of the FP32 path within 2e-5 relative L2 of
     the FP64 oracle after 1000 steps."""
-    case = W.marangoni()
-    ref = oracle_fields(case, 1000)
-    with lbm.Simulation(case, precision="fp32") as sim:
-        got = sim.init_case().step(1000).fields()
+    _, ref, _, _ = references("marangoni")
+    got = C.gpu_series(C.CASES["marangoni"](), "fp32", (1000,))
     for k in ("phi", "p"):
-        assert rel_l2(got[k], ref[k]) <= 2e-5, k
+        assert rel_l2(got[1000][k], ref[1000][k]) <= 2e-5, k
