@@ -299,9 +299,10 @@ def run_ours(args):
     if args.variants:
         line["variants"] = {"ensemble_512_cases": measure_ensemble(
             args.ensemble_steps, 16, args.precision, local, stream.cuda_stream)}
-        if args.precision == "fp32":   # the same batch with BF16 storage
-            line["variants"]["ensemble_512_cases_bf16"] = measure_ensemble(
-                args.ensemble_steps, 0, "bf16", local, stream.cuda_stream)
+        if args.precision == "fp32":   # the same batch with 16-bit storage
+            for p16 in ("fp16", "bf16"):
+                line["variants"][f"ensemble_512_cases_{p16}"] = measure_ensemble(
+                    args.ensemble_steps, 0, p16, local, stream.cuda_stream)
         line["variants"].update(measure_storage(case, args.storage_steps, local,
                                                 stream.cuda_stream))
         line["variants"]["forms"] = measure_forms(args.storage_steps, peak, local,
