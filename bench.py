@@ -89,11 +89,11 @@ def kernel_source_hash() -> str:
 # figures are steady-state launches (caches not flushed between launches, as in the timed run;
 # mean of three consecutive launches).
 NCU_TRAFFIC = {
-    # FP32 step on the 2048 x 1024 impact, sources 4b7abf78c1218550: read 106.52 MB + write
-    # 150.91 MB per launch
-    ("4b7abf78c1218550", "impact", "fp32"): 257_428_651,
-    # FP16-storage step on the same grid and sources: read 46.10 MB + write 92.23 MB per launch
-    ("4b7abf78c1218550", "impact", "fp16"): 138_330_112,
+    # FP32 step on the 2048 x 1024 impact, sources b8dfb5b8d97d5c25: read 106.02 MB + write
+    # 149.93 MB per launch
+    ("b8dfb5b8d97d5c25", "impact", "fp32"): 255_952_128,
+    # FP16-storage step on the same grid and sources: read 46.23 MB + write 92.41 MB per launch
+    ("b8dfb5b8d97d5c25", "impact", "fp16"): 138_637_824,
 }
 
 

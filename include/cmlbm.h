@@ -174,7 +174,8 @@ typedef struct {
     double sum_p;        /* sum over nodes of the corrected pressure p */
     double max_speed;    /* max over nodes of |u| */
     double dp_laplace;   /* mean p over r < r_in minus mean p over r > r_out about (xc, yc)
-                            (periodic distances), 0 if a region is empty */
+                            (periodic distances; compared as r^2 against r_in^2, r_out^2), 0 if
+                            a region is empty */
     int64_t nonfinite;   /* nodes whose phi, p or u is NaN or Inf */
 } lbm_diag;
 

@@ -153,13 +153,19 @@ cudaError_t clear_device_error(lbm_ctx* c)
 }
 
 // Every graph size from both start buffers for flow sign `sign`, built together the first time
-// any of them is needed, so that later runs of any length (and parity) launch without building.
+// any of them is needed and uploaded to the device at once (a graph is otherwise uploaded at its
+// first launch, which then starts late), so that later runs of any length (and parity) launch
+// without building or uploading.
 cudaError_t ensure_graphs(lbm_ctx* c, int sign)
 {
     cudaError_t e = cudaSuccess;
     for (int start = 0; start < 2 && e == cudaSuccess; ++start)
-        for (int k = 0; k < kGraphSizes && e == cudaSuccess; ++k)
+        for (int k = 0; k < kGraphSizes && e == cudaSuccess; ++k) {
+            cudaGraphExec_t& slot = c->graph[start][sign < 0 ? 1 : 0][k];
+            if (slot) continue;
             e = build_graph(c, start, sign, k);
+            if (e == cudaSuccess) e = cudaGraphUpload(slot, c->st);
+        }
     return e;
 }
 
@@ -261,8 +267,11 @@ int run_fields(lbm_ctx* c, double* phi, double* p, double* ux, double* uy, doubl
 // ---------------------------------------------------------------------------------------------
 struct DiagArgs {
     int nx, ny, wall_x, wall_y;
-    double xc, yc, r_in, r_out;
+    double xc, yc, r_in, r_out;   // regions r < r_in, r > r_out (r_in < 0: none)
 };
+
+// Threads of the final reduction: kReduceSlots slots x kFinalLanes fixed-order partial sums.
+constexpr int kFinalLanes = 32;
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -275,14 +284,17 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
-// slots: 0 sum phi, 1 sum p, 2 max |u|, 3 sum p inside, 4 count inside, 5 sum p outside,
-// 6 count outside, 7 non-finite count
+// slots: 0 sum phi, 1 sum p, 2 max |u|^2, 3 sum p inside, 4 count inside, 5 sum p outside,
+// 6 count outside, 7 non-finite count.  The regions compare squared distances with r_in^2 and
+// r_out^2 and the speed is squared (square root of the maximum at the end): no FP64 square root
+// per node.
 __global__ void diag_partial_kernel(const double* __restrict__ phi, const double* __restrict__ p,
                                     const double* __restrict__ ux, const double* __restrict__ uy,
                                     DiagArgs A, double* __restrict__ part)
 {
     double acc[kReduceSlots] = {0, 0, 0, 0, 0, 0, 0, 0};
     const long long N = (long long)A.nx * A.ny;
+    const double rin2 = A.r_in * A.r_in, rout2 = A.r_out < 0 ? -1.0 : A.r_out * A.r_out;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         const double ph = phi[n], pp = p[n], u = ux[n], v = uy[n];
@@ -292,15 +304,15 @@ __global__ void diag_partial_kernel(const double* __restrict__ phi, const double
         }
         acc[0] += ph;
         acc[1] += pp;
-        acc[2] = fmax(acc[2], sqrt(u * u + v * v));
+        acc[2] = fmax(acc[2], u * u + v * v);
         if (A.r_in >= 0) {
             const int y = (int)(n / A.nx), x = (int)(n % A.nx);
             double dx = fabs(x - A.xc), dy = fabs(y - A.yc);
             if (!A.wall_x) dx = fmin(dx, A.nx - dx);
             if (!A.wall_y) dy = fmin(dy, A.ny - dy);
-            const double r = sqrt(dx * dx + dy * dy);
-            if (r < A.r_in) { acc[3] += pp; acc[4] += 1.0; }
-            if (r > A.r_out) { acc[5] += pp; acc[6] += 1.0; }
+            const double r2 = dx * dx + dy * dy;
+            if (r2 < rin2) { acc[3] += pp; acc[4] += 1.0; }
+            if (r2 > rout2) { acc[5] += pp; acc[6] += 1.0; }
         }
     }
     __shared__ double sh[32][kReduceSlots];
@@ -319,17 +331,35 @@ __global__ void diag_partial_kernel(const double* __restrict__ phi, const double
     }
 }
 
-__global__ void diag_final_kernel(double* __restrict__ part, int nblocks)
+// The block partials of diag_partial_kernel combined in a fixed order (one block of
+// kReduceSlots x kFinalLanes threads): thread (j, k) folds blocks j, j + 32, j + 64, ... of
+// slot k, then one thread per slot folds the 32 results in lane order.  Deterministic for a
+// given block count.
+__device__ __forceinline__ void fold_partials(const double* __restrict__ part, int nblocks,
+                                              double r[kReduceSlots])
 {
-    // one warp; lanes take slots, blocks summed in index order
-    const int k = threadIdx.x;
-    if (k >= kReduceSlots) return;
-    double r = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
+    __shared__ double sh[kFinalLanes][kReduceSlots];
+    const int k = threadIdx.x % kReduceSlots, j = threadIdx.x / kReduceSlots;
+    double a = 0.0;
+    for (int b = j; b < nblocks; b += kFinalLanes) {
         const double v = part[(size_t)b * kReduceSlots + k];
-        r = (k == 2) ? fmax(r, v) : r + v;
+        a = (k == 2) ? fmax(a, v) : a + v;
     }
-    part[(size_t)nblocks * kReduceSlots + k] = r;
+    sh[j][k] = a;
+    __syncthreads();
+    if (threadIdx.x < kReduceSlots) {
+        double t = 0.0;
+        for (int i = 0; i < kFinalLanes; ++i) t = (k == 2) ? fmax(t, sh[i][k]) : t + sh[i][k];
+        r[k] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kReduceSlots * kFinalLanes)
+diag_final_kernel(double* __restrict__ part, int nblocks)
+{
+    double r[kReduceSlots];
+    fold_partials(part, nblocks, r);
+    if (threadIdx.x < kReduceSlots) part[(size_t)nblocks * kReduceSlots + threadIdx.x] = r[threadIdx.x];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -380,19 +410,18 @@ bool current_context_id(unsigned long long* id)
     return get_id(ctx, id) == 0;
 }
 
-__global__ void diag_store_kernel(const double* __restrict__ part, int nblocks, lbm_diag* out)
+__global__ void __launch_bounds__(kReduceSlots * kFinalLanes)
+diag_store_kernel(const double* __restrict__ part, int nblocks, lbm_diag* out)
 {
+    __shared__ double r[kReduceSlots];
+    double mine[kReduceSlots];
+    fold_partials(part, nblocks, mine);
+    if (threadIdx.x < kReduceSlots) r[threadIdx.x] = mine[threadIdx.x];
+    __syncthreads();
     if (threadIdx.x != 0) return;
-    double r[kReduceSlots];
-    for (int k = 0; k < kReduceSlots; ++k) r[k] = 0.0;
-    for (int b = 0; b < nblocks; ++b)
-        for (int k = 0; k < kReduceSlots; ++k) {
-            const double v = part[(size_t)b * kReduceSlots + k];
-            r[k] = (k == 2) ? fmax(r[k], v) : r[k] + v;
-        }
     out->sum_phi = r[0];
     out->sum_p = r[1];
-    out->max_speed = r[2];
+    out->max_speed = sqrt(r[2]);
     out->dp_laplace = (r[4] > 0 && r[6] > 0) ? r[3] / r[4] - r[5] / r[6] : 0.0;
     out->nonfinite = (int64_t)r[7];
 }
@@ -662,7 +691,7 @@ int lbm_diagnostics(lbm_ctx* c, double xc, double yc, double r_in, double r_out,
     const int nb = 4 * c->nsm;
     diag_partial_kernel<<<nb, 256, 0, c->st>>>(c->scratch, c->scratch + N, c->scratch + 2 * N,
                                                c->scratch + 3 * N, A, c->partials);
-    diag_final_kernel<<<1, 32, 0, c->st>>>(c->partials, nb);
+    diag_final_kernel<<<1, kReduceSlots * kFinalLanes, 0, c->st>>>(c->partials, nb);
     double r[kReduceSlots];
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
@@ -672,7 +701,7 @@ int lbm_diagnostics(lbm_ctx* c, double xc, double yc, double r_in, double r_out,
     if (e != cudaSuccess) return cuda_fail(c, e);
     out->sum_phi = r[0];
     out->sum_p = r[1];
-    out->max_speed = r[2];
+    out->max_speed = std::sqrt(r[2]);
     out->dp_laplace = (r[4] > 0 && r[6] > 0) ? r[3] / r[4] - r[5] / r[6] : 0.0;
     out->nonfinite = (int64_t)r[7];
     int s2 = check_device_error(c);
@@ -778,7 +807,8 @@ int lbm_diagnostics_noalloc(const double* phi, const double* p, const double* ux
     if (e != cudaSuccess) return LBM_ERR_CUDA;
     int nblocks = nb;
     void* a2[] = {(void*)&part, (void*)&nblocks, (void*)&out};
-    e = cudaLaunchKernel((const void*)diag_store_kernel, dim3(1), dim3(32), a2, 0, st);
+    e = cudaLaunchKernel((const void*)diag_store_kernel, dim3(1), dim3(kReduceSlots * kFinalLanes),
+                         a2, 0, st);
     return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 

@@ -174,7 +174,8 @@ cudaError_t launch_one(lbm_batch* b)
     });
 }
 
-// Every graph size from both buffer parities, built together the first time any is needed.
+// Every graph size from both buffer parities, built together the first time any is needed and
+// uploaded to the device at once (as in lbm_api.cu).
 cudaError_t ensure_graphs(lbm_batch* b)
 {
     cudaError_t e = cudaSuccess;
@@ -187,6 +188,7 @@ cudaError_t ensure_graphs(lbm_batch* b)
                     b->base, static_cast<BatchCase<R>*>(b->dcases), b->dtasks, b->ntasks, par,
                     b->block, b->err, 2 * (k + 1), &b->graph[par][k]);
             });
+            if (e == cudaSuccess) e = cudaGraphUpload(b->graph[par][k], b->st);
         }
     return e;
 }
