@@ -94,6 +94,9 @@ NCU_TRAFFIC = {
     ("b8dfb5b8d97d5c25", "impact", "fp32"): 255_952_128,
     # FP16-storage step on the same grid and sources: read 46.23 MB + write 92.41 MB per launch
     ("b8dfb5b8d97d5c25", "impact", "fp16"): 138_637_824,
+    # batched step of the 512-case ensemble (autotuned: 8 rows per task, 128-thread blocks), same
+    # sources: read 832.14 MB + write 760.76 MB per launch
+    ("b8dfb5b8d97d5c25", "ensemble", "fp32"): 1_592_908_032,
 }
 
 
@@ -606,7 +609,9 @@ def run_ensemble_line(args):
         "config": {"workload": f"ensemble of {r['cases']} drop cases, {r['nodes']} nodes, "
                                f"{args.precision} populations", "nodes": r["nodes"]},
         "roofline": {"bound": "hbm", "achieved": r["batched_gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": round(r["batched_gbs"] / peak, 4), "traffic": None,
+                     "frac": round(r["batched_gbs"] / peak, 4),
+                     "traffic": NCU_TRAFFIC.get((kernel_source_hash(), "ensemble",
+                                                 args.precision)),
                      "peak_source": f"{peak_kind} HBM copy bandwidth",
                      "kernel": "cmlbm::batch_step_kernel"},
         "clocks": clk.summary(), "ensemble": r, "gpu_launches": args.steps,
