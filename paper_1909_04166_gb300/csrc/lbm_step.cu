@@ -9,9 +9,11 @@
 //
 // Step kernel (one launch = one time step of both lattices over the whole grid):
 //   * Each warp owns a strip of columns and a segment of rows and marches along the rows.  With
-//     FP32 arithmetic (march2) the strip is two adjacent tiles and lane l owns columns x0 + l
-//     and x0 + 32 + l, updated together on the packed FP32x2 instructions; in FP64 (march) the
-//     strip is one tile and lane l owns column x0 + l.  Segments alternate direction so that
+//     FP32 arithmetic (march2) the strip is two adjacent tiles and lane l owns the two adjacent
+//     columns x0 + 32 (l / 16) + 2 (l % 16) and the next one, updated together on the packed
+//     FP32x2 instructions (one 64- or 32-bit shared load brings a plane's pair; in full strips
+//     without walls FP32 pairs are stored as aligned 64-bit words); in FP64 (march) the strip is
+//     one tile and lane l owns column x0 + l.  Segments alternate direction so that
 //     neighbours read a shared boundary row at about the same time and the re-read hits L2;
 //     every segment also reverses its direction from one step to the next, so that a step
 //     starts on the rows the previous one wrote last, many of which are still in L2.
@@ -515,6 +517,134 @@ __device__ __forceinline__ void push_pair_z(const F2 g[9], const F2 f[9], const 
     put(0, gA, gB, fA, fB);
 }
 
+// Global store executed only where p holds, as one predicated instruction (no branch): the FP32
+// pair and edge stores of the packed fast path are taken by all but one or two lanes of a warp.
+// The bounds-checked kernel keeps its checked, branching form.
+__device__ __forceinline__ void st_global_if(bool p, float2* a, float2 v)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t"
+                 "@q st.global.v2.f32 [%1], {%2, %3};\n\t}" ::"r"((int)p), "l"(a), "f"(v.x),
+                 "f"(v.y));
+}
+__device__ __forceinline__ void st_global_if(bool p, float* a, float v)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t"
+                 "@q st.global.f32 [%1], %2;\n\t}" ::"r"((int)p), "l"(a), "f"(v));
+}
+template <class BND, typename T>
+__device__ __forceinline__ void st_chk_if(const BND& B, bool p, T* a, T v)
+{
+    if constexpr (std::is_same<BND, Bounds<false>>::value) st_global_if(p, a, v);
+    else if (p) st_chk(B, a, v);
+}
+
+// The packed form of encode_pair: the two stored 16-bit values as one 32-bit word (node A in the
+// low half, node B in the high half); same roundings, same returned errors.
+template <typename S, bool ADJ>
+__device__ __forceinline__ F2 encode_word(F2 v, F2 z, float w, float scale, F2 adj,
+                                          uint32_t& word)
+{
+    F2 d = fmad(F2(-w), z, v) * F2(scale);
+    if constexpr (ADJ) d = d - adj;
+    float2 back;
+    if constexpr (std::is_same<S, __half>::value) {
+        const __half2 h = __float22half2_rn(d.v);
+        word = *reinterpret_cast<const uint32_t*>(&h);
+        back = __half22float2(h);
+    } else {
+        const __nv_bfloat162 h = __float22bfloat162_rn(d.v);
+        word = *reinterpret_cast<const uint32_t*>(&h);
+        back = __bfloat1622float2(h);
+    }
+    return F2(back) - d;
+}
+
+// Stores of the fast path for a full strip (64 active columns, no wall in the warp row).  FP32:
+// for every population plane one store writes a whole aligned pair of adjacent columns for most
+// lanes.  With e_x = 0 a lane writes its own pair; with e_x = +1 the pair (c_A, c_B) receives the
+// previous lane's B and this lane's A (one shuffle), lane 0 writing only its B half and lane 31
+// sending its B into the next strip (column offset ceB); with e_x = -1 it receives this lane's B
+// and the next lane's A, lane 31 writing only its A half and lane 0 sending its A into the
+// previous strip (cwA).  16-bit forms: one 32-bit store of the lane's pair for the planes with
+// e_x = 0 and one 16-bit store per node for the others (measured faster there than shuffled
+// pairs); every population is encoded against the rest state of the node it lands on (the window
+// values at its offset), and the rest population goes last with the rounding errors of the
+// moving ones subtracted (see encode_err).  woff / zoff: element offsets of column c_A's plane 0
+// and zeroth moments; ccB: column c_B's.  The stored values are those of push_node / push_pair_z,
+// bit for bit.
+template <typename S, bool F_ONLY, class BND>
+__device__ __forceinline__ void push_packed(const F2 g[9], const F2 f[9], const Win<F2>& ps,
+                                            const Win<F2>& ph, S* rS, S* rC, S* rN, int woff,
+                                            int ccB, int cwA, int ceB, int zoff, int lane,
+                                            const Consts<float>& K, const BND& B)
+{
+    constexpr bool NARROW = Narrow<S>::value;
+    constexpr int EXc[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    constexpr int EYc[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    auto row_at = [&](int ey) { return ey < 0 ? rS : (ey > 0 ? rN : rC); };
+    if constexpr (NARROW) {
+        // plane `plane` of the pair word `mine` (node A low half, B high half), moving by ex
+        auto put = [&](S* row, int plane, int ex, uint32_t mine) {
+            S* base = row + plane * 32;
+            if (ex == 0) {
+                st_chk(B, reinterpret_cast<uint32_t*>(base + woff), mine);
+                return;
+            }
+            auto* pa = reinterpret_cast<unsigned short*>(base + (ex > 0 ? ccB : cwA));
+            auto* pb = reinterpret_cast<unsigned short*>(base + (ex > 0 ? ceB : woff));
+            st_chk(B, pa, static_cast<unsigned short>(mine & 0xffffu));
+            st_chk(B, pb, static_cast<unsigned short>(mine >> 16));
+        };
+        float* z = reinterpret_cast<float*>(rC + zoff);
+        st_chk(B, reinterpret_cast<float2*>(z), ps.c.v);
+        st_chk(B, reinterpret_cast<float2*>(z + 32), ph.c.v);
+        F2 eg(0.0f), ef(0.0f);   // rounding errors of the moving populations (see encode_err)
+#pragma unroll
+        for (int a = 1; a < 9; ++a) {
+            const float w = float(d2q9_w(a));
+            uint32_t wg, wf;
+            eg += encode_word<S, false>(g[a], win_at(ps, EXc[a], EYc[a]), w, K.st_scale[0],
+                                        F2(0.0f), wg);
+            ef += encode_word<S, false>(f[a], win_at(ph, EXc[a], EYc[a]), w, K.st_scale[1],
+                                        F2(0.0f), wf);
+            put(row_at(EYc[a]), a, EXc[a], wg);
+            put(row_at(EYc[a]), 9 + a, EXc[a], wf);
+        }
+        const float w0 = float(d2q9_w(0));
+        uint32_t wg, wf;
+        encode_word<S, true>(g[0], ps.c, w0, K.st_scale[0], eg, wg);
+        encode_word<S, true>(f[0], ph.c, w0, K.st_scale[1], ef, wf);
+        put(rC, 0, 0, wg);
+        put(rC, 9, 0, wf);
+    } else {
+        // the edge stores: lane 0 writes its A, lane 31 its B, at these element offsets for
+        // e_x = +1 / -1
+        const int eoff_p = lane == 0 ? woff + 1 : ceB;
+        const int eoff_m = lane == 31 ? woff : cwA;
+        const bool edge = lane == 0 || lane == 31;
+        auto put = [&](S* row, int plane, int ex, float2 mine) {
+            S* base = row + plane * 32;
+            float2* wp = reinterpret_cast<float2*>(base + woff);
+            if (ex == 0) {
+                st_chk(B, wp, mine);
+                return;
+            }
+            if (ex > 0)   // (previous lane's B, this A)
+                st_chk_if(B, lane >= 1, wp,
+                          make_float2(__shfl_up_sync(FULL, mine.y, 1), mine.x));
+            else          // (this B, next lane's A)
+                st_chk_if(B, lane <= 30, wp,
+                          make_float2(mine.y, __shfl_down_sync(FULL, mine.x, 1)));
+            st_chk_if(B, edge, base + (ex > 0 ? eoff_p : eoff_m), lane == 0 ? mine.x : mine.y);
+        };
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            if (!F_ONLY) put(row_at(EYc[a]), a, EXc[a], g[a].v);
+            put(row_at(EYc[a]), 9 + a, EXc[a], f[a].v);
+        }
+    }
+}
+
 // The march of one warp over one strip x segment of one grid: everything the step does for
 // those nodes.  Used by the single-grid kernel and by the batched kernel.
 template <typename R, typename S, int V, bool CK = false>
@@ -703,40 +833,66 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
 }
 
 // ---------------------------------------------------------------------------------------------
-// Paired FP32 march: a warp owns two adjacent tiles (64 columns) and lane l the columns x0 + l
-// (node A) and x0 + 32 + l (node B); both nodes go through the update at once in the packed FP32x2
-// arithmetic (F2), which halves the issued floating-point instructions per node, and the per-row
-// work of the pipeline (waits, copies, halo, row addressing) is shared by 64 nodes.  One bulk copy
-// per row brings both tiles (they are adjacent in memory).  An odd last strip has one tile; its
-// B half then repeats A (and stores nothing).
+// Paired FP32 march: a warp owns two adjacent tiles (64 columns) and lane l the two adjacent
+// columns c_A = 32 t + 2 j and c_B = c_A + 1 of tile t = l / 16 (j = l % 16): node A and node B.
+// Both nodes go through the update at once in the packed FP32x2 arithmetic (F2), which halves the
+// issued floating-point instructions per node, and the per-row work of the pipeline (waits,
+// copies, halo, row addressing) is shared by 64 nodes.  A lane's two values of a population plane
+// are adjacent in memory, so one 64-bit (FP32) or 32-bit (16-bit) shared load brings both, and
+// where no node of the warp row touches a wall, one store per plane writes a whole aligned pair
+// for most lanes (the x-shifted planes take one shuffle for that; the two pairs at the strip's
+// ends are split into single stores).  One bulk copy per row brings both tiles (they are adjacent
+// in memory).  An odd last strip has one tile; lanes of the missing tile read tile A again and
+// store nothing.
 // ---------------------------------------------------------------------------------------------
 struct Row3P {
     F2 phw, phc, phe, psw, psc, pse;
 };
 
+// The two values of population plane p at a lane's pair of columns (tp: the lane's tile plus
+// 2 j), converted to float.
+template <typename S>
+__device__ __forceinline__ F2 load_pair(const S* tp, int p)
+{
+    const S* q = tp + Tile<S>::P0 + p * 32;
+    if constexpr (std::is_same<S, float>::value) {
+        return F2(*reinterpret_cast<const float2*>(q));
+    } else if constexpr (std::is_same<S, __half>::value) {
+        return F2(__half22float2(*reinterpret_cast<const __half2*>(q)));
+    } else {
+        return F2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(q)));
+    }
+}
+
+// The zeroth moments Z (lattice lat) of a lane's two columns in a 16-bit tile (tz: the lane's
+// tile; j: its pair index).
+template <typename S>
+__device__ __forceinline__ F2 load_z_pair(const S* tz, int j, int lat)
+{
+    return F2(*reinterpret_cast<const float2*>(reinterpret_cast<const float*>(tz) + 32 * lat +
+                                               2 * j));
+}
+
 // Sums of a lane's two columns and their east / west neighbours; hl / hr: this lane's halo
 // loads (summed over the half warp into the halo columns' zeroth moments); lastA / lastB: this
 // lane's node A / B is the last active column of the warp (its east neighbour is the right halo
-// column).  ta / tb: the two tiles of the row in shared memory.
+// column).  tt: the lane's tile in shared memory, j: its pair index.
 template <typename S, bool PHI_ONLY = false>
-__device__ __forceinline__ void window_row2(const S* ta, const S* tb, int lane, bool lastA,
-                                            bool lastB, float hl, float hr,
-                                            const Consts<float>& K, Row3P& row)
+__device__ __forceinline__ void window_row2(const S* tt, int j, int lane, bool lastA, bool lastB,
+                                            float hl, float hr, const Consts<float>& K,
+                                            Row3P& row)
 {
-    constexpr int P0 = Tile<S>::P0;
-    auto val = [&](const S* t, int p) { return float(narrow_to_f_or_self(t[P0 + p * 32 + lane])); };
-    F2 ps(0.0f), ph(val(ta, 9), val(tb, 9));
-    if (!PHI_ONLY) ps = F2(val(ta, 0), val(tb, 0));
+    const S* tp = tt + 2 * j;
+    F2 ps(0.0f), ph = load_pair(tp, 9);
+    if (!PHI_ONLY) ps = load_pair(tp, 0);
 #pragma unroll
     for (int a = 1; a < 9; ++a) {
-        if (!PHI_ONLY) ps += F2(val(ta, a), val(tb, a));
-        ph += F2(val(ta, 9 + a), val(tb, 9 + a));
+        if (!PHI_ONLY) ps += load_pair(tp, a);
+        ph += load_pair(tp, 9 + a);
     }
     if constexpr (Narrow<S>::value) {   // Z + (sum of the deviations) / s
-        const float* za = reinterpret_cast<const float*>(ta);
-        const float* zb = reinterpret_cast<const float*>(tb);
-        ps = fmad(ps, F2(K.st_inv[0]), F2(za[lane], zb[lane]));
-        ph = fmad(ph, F2(K.st_inv[1]), F2(za[32 + lane], zb[32 + lane]));
+        ps = fmad(ps, F2(K.st_inv[0]), load_z_pair(tt, j, 0));
+        ph = fmad(ph, F2(K.st_inv[1]), load_z_pair(tt, j, 1));
     }
     F2 h(hl, hr);
 #pragma unroll
@@ -744,13 +900,13 @@ __device__ __forceinline__ void window_row2(const S* ta, const S* tb, int lane, 
         h += F2(__shfl_xor_sync(FULL, h.v.x, off), __shfl_xor_sync(FULL, h.v.y, off));
     const float psl = __shfl_sync(FULL, h.v.x, 0), phl = __shfl_sync(FULL, h.v.x, 16);
     const float psr = __shfl_sync(FULL, h.v.y, 0), phr = __shfl_sync(FULL, h.v.y, 16);
+    // west of A: the previous lane's B (the left halo column for lane 0); east of A: B; west of
+    // B: A; east of B: the next lane's A (the right halo column after the last active column)
     auto neighbours = [&](F2 c, float left, float right, F2& w, F2& e) {
-        const float upA = __shfl_up_sync(FULL, c.v.x, 1), upB = __shfl_up_sync(FULL, c.v.y, 1);
+        const float upB = __shfl_up_sync(FULL, c.v.y, 1);
         const float dnA = __shfl_down_sync(FULL, c.v.x, 1);
-        const float dnB = __shfl_down_sync(FULL, c.v.y, 1);
-        const float a31 = __shfl_sync(FULL, c.v.x, 31), b0 = __shfl_sync(FULL, c.v.y, 0);
-        w = F2(lane == 0 ? left : upA, lane == 0 ? a31 : upB);
-        e = F2(lastA ? right : (lane == 31 ? b0 : dnA), lastB ? right : dnB);
+        w = F2(lane == 0 ? left : upB, c.v.x);
+        e = F2(lastA ? right : c.v.y, lastB ? right : dnA);
     };
     row.psc = ps;
     row.phc = ph;
@@ -808,11 +964,14 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
     const int x0 = t0 * 32;
     const int w = min(64, G.nx - x0);                // active columns
     const int wl = w - 1;                            // last active column (0..63)
-    const bool actA = lane < w, actB = lane + 32 < w;
-    const bool lastA = lane == wl, lastB = lane + 32 == wl;
-    const int TB = nt == 2 ? TE : 0;                 // offset of tile B in a stage
-    const int xA = actA ? x0 + lane : x0 + wl;       // idle lanes shadow the last column
-    const int xB = actB ? x0 + 32 + lane : x0 + wl;
+    const int jp = lane & 15;                        // the lane's pair within its tile
+    const int cA = 32 * (lane >> 4) + 2 * jp;        // its columns c_A and c_B = c_A + 1
+    const bool actA = cA < w, actB = cA + 1 < w;
+    const bool lastA = cA == wl, lastB = cA + 1 == wl;
+    const int TB = (nt == 2 && lane >= 16) ? TE : 0; // offset of the lane's tile in a stage
+    const int xA = actA ? x0 + cA : x0 + wl;         // idle lanes shadow the last column
+    const int xB = actB ? x0 + cA + 1 : x0 + wl;
+    const bool full = w == 64;                       // warp-uniform: pair stores
     const int xl = map_col(x0 - 1, G), xr = map_col(x0 + w, G);
     const int row_elems = G.nstrips * TE;
     auto row_ptr = [&](const S* base, int row) { return base + (long long)row * row_elems; };
@@ -889,11 +1048,11 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
     float hl, hr, hl2, hr2;
     halo_load(-1, hl, hr);
     if (cut_first || !wait_k(-1, 0)) { fail(-1); return; }
-    window_row2<S, SHEAR>(tiles, tiles + TB, lane, lastA, lastB, hl, hr, K, rb);
+    window_row2<S, SHEAR>(tiles + TB, jp, lane, lastA, lastB, hl, hr, K, rb);
     issue(NS - 1, 0);
     halo_load(0, hl, hr);
     if (!wait_k(0, 1)) { fail(0); return; }
-    window_row2<S, SHEAR>(tiles + STAGE, tiles + STAGE + TB, lane, lastA, lastB, hl, hr, K, rc);
+    window_row2<S, SHEAR>(tiles + STAGE + TB, jp, lane, lastA, lastB, hl, hr, K, rc);
     halo_load(1, hl2, hr2);
 
     // neighbour columns of the two nodes (periodic wrap; walls handled by the push)
@@ -930,30 +1089,24 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
     auto body = [&](int i, int st) {
         const int st1 = st + 1 == NS ? 0 : st + 1;
         if (!wait_k(i + 1, st1)) { fail(i + 1); ok = false; return; }
-        window_row2<S, SHEAR>(tiles + st1 * STAGE, tiles + st1 * STAGE + TB, lane, lastA, lastB,
-                              hl2, hr2, K, rn);
+        window_row2<S, SHEAR>(tiles + st1 * STAGE + TB, jp, lane, lastA, lastB, hl2, hr2, K,
+                              rn);
         if (i + 2 <= nrows) halo_load(i + 2, hl2, hr2);
 
         const int y = up ? ys + i : ye - 1 - i;
         Win<F2> ph, ps;
         if (up) make_window2(rb, rc, rn, ph, ps);
         else make_window2(rn, rc, rb, ph, ps);
-        const S* ta = tiles + st * STAGE;
-        const S* tb = ta + TB;
-        constexpr int P0 = Tile<S>::P0;
+        const S* tt = tiles + st * STAGE + TB;
+        const S* tp = tt + 2 * jp;
         F2 g[9], f[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            if (!SHEAR)
-                g[a] = F2(narrow_to_f_or_self(ta[P0 + a * 32 + lane]),
-                          narrow_to_f_or_self(tb[P0 + a * 32 + lane]));
-            f[a] = F2(narrow_to_f_or_self(ta[P0 + (9 + a) * 32 + lane]),
-                      narrow_to_f_or_self(tb[P0 + (9 + a) * 32 + lane]));
+            if (!SHEAR) g[a] = load_pair(tp, a);
+            f[a] = load_pair(tp, 9 + a);
         }
         if constexpr (NARROW) {   // q_a = w_a Z + d_a / s
-            const float* za = reinterpret_cast<const float*>(ta);
-            const float* zb = reinterpret_cast<const float*>(tb);
-            const F2 zg(za[lane], zb[lane]), zf(za[32 + lane], zb[32 + lane]);
+            const F2 zg = load_z_pair(tt, jp, 0), zf = load_z_pair(tt, jp, 1);
             const F2 ig(K.st_inv[0]), ifl(K.st_inv[1]);
 #pragma unroll
             for (int a = 0; a < 9; ++a) {
@@ -1001,7 +1154,10 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
                 push_node<S, float, SHEAR>(gq, fq, rS, rC, rN, cw, cc, ce, bxw, bxe, bys, byn,
                                            G.slip, fast, K, B);
         };
-        if (NARROW && fast) {
+        if (fast && full) {
+            push_packed<S, SHEAR>(g, f, ps, ph, rS, rC, rN, ccA, ccB, cwA, ceB, zcA, lane, K,
+                                  B);
+        } else if (NARROW && fast) {
             push_pair_z<S>(g, f, ps, ph, rS, rC, rN, cwA, ccA, ceA, cwB, ccB, ceB, zcA, zcB,
                            actA, actB, K, B);
         } else {
