@@ -89,14 +89,14 @@ def kernel_source_hash() -> str:
 # figures are steady-state launches (caches not flushed between launches, as in the timed run;
 # mean of three consecutive launches).
 NCU_TRAFFIC = {
-    # FP32 step on the 2048 x 1024 impact, sources b8dfb5b8d97d5c25: read 106.02 MB + write
-    # 149.93 MB per launch
-    ("b8dfb5b8d97d5c25", "impact", "fp32"): 255_952_128,
-    # FP16-storage step on the same grid and sources: read 46.23 MB + write 92.41 MB per launch
-    ("b8dfb5b8d97d5c25", "impact", "fp16"): 138_637_824,
+    # FP32 step on the 2048 x 1024 impact, sources 988d57dd778814ff: read 106.25 MB + write
+    # 149.92 MB per launch
+    ("988d57dd778814ff", "impact", "fp32"): 256_169_131,
+    # FP16-storage step on the same grid and sources: read 46.38 MB + write 92.38 MB per launch
+    ("988d57dd778814ff", "impact", "fp16"): 138_761_557,
     # batched step of the 512-case ensemble (autotuned: 8 rows per task, 128-thread blocks), same
-    # sources: read 832.14 MB + write 760.76 MB per launch
-    ("b8dfb5b8d97d5c25", "ensemble", "fp32"): 1_592_908_032,
+    # sources: read 833.36 MB + write 759.27 MB per launch
+    ("988d57dd778814ff", "ensemble", "fp32"): 1_592_624_725,
 }
 
 
