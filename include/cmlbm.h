@@ -273,7 +273,8 @@ int lbm_check(lbm_ctx* ctx);
  * none outlives the block, and returns without updating its nodes.  Nothing faults or hangs;
  * the state of those steps is invalid, lbm_check reports LBM_ERR_TIMEOUT, and re-initialising
  * the state (lbm_init_fields*, lbm_set_populations, lbm_load_state) clears the error.  Steps run
- * as single launches while enabled.  enable = 0 (default) returns to normal waits; other
+ * as single launches while enabled, through the plain step kernel (the bounds-checked kernel of
+ * lbm_set_checked keeps its normal waits).  enable = 0 (default) returns to normal waits; other
  * values: LBM_ERR_ARG. */
 int lbm_inject_timeout(lbm_ctx* ctx, int32_t enable);
 

@@ -67,7 +67,12 @@ def test_fp64_step_parity(nx, ny, wx, wy, nsteps):
         assert rel_l2(fl[k], ref[k]) <= 1e-12, k
 
 
-@pytest.mark.parametrize("nx,ny,wx,wy", SHAPES[:4] + SHAPES[7:])
+# full 64-column strips without x walls take the paired stores of the fast path: one strip that
+# wraps onto itself, and two strips whose edge lanes store into each other
+FULL_STRIPS = [(64, 40, False, False), (128, 24, False, True)]
+
+
+@pytest.mark.parametrize("nx,ny,wx,wy", SHAPES[:4] + SHAPES[7:] + FULL_STRIPS)
 def test_fp32_parity_200_steps(nx, ny, wx, wy):
     case = W.random_drop(nx, ny, seed=nx + 3 * ny, wall_x=wx, wall_y=wy, rho_ratio=100.0,
                          gravity=1e-6, marangoni=-2e-5)
