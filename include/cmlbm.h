@@ -206,17 +206,33 @@ int lbm_init_fields(lbm_ctx* ctx, const double* phi, const double* p, const doub
 int lbm_init_fields_device(lbm_ctx* ctx, const double* phi, const double* p, const double* ux,
                            const double* uy);
 
-/* Advance nsteps (>= 0) time steps: one fused kernel launch per step on params.stream,
+/* Advance nsteps (>= 0) time steps (the update of Secs. 3 - 5 on every node) on params.stream,
  * asynchronous; launch errors are returned.  A run of two or more steps is issued as replays of
- * CUDA graphs: graphs of 32 launches while 32 or more steps are left, then one graph for the
- * even rest (2 .. 30 launches), a last odd step as a single launch.  The first call that needs
- * a graph builds all of them (every even size up to 32, from either state buffer; a few
- * milliseconds), so later calls of any length launch at once; lbm_set_launch drops them,
- * lbm_set_graphs switches them off. */
+ * CUDA graphs of one launch per step: graphs of 32 launches while 32 or more steps are left,
+ * then one graph for the even rest (2 .. 30 launches); the first call that needs a graph builds
+ * all of them (every even size up to 32, from either state buffer; a few milliseconds), so
+ * later calls of any length launch at once; lbm_set_launch drops them, lbm_set_graphs switches
+ * them off.  With lbm_set_persistent(ctx, 1) such a run is instead one launch of the multi-step
+ * kernel: every warp keeps its strip of columns and segment of rows from step to step and
+ * waits, between steps, only for the warps of the neighbouring strips and segments (a
+ * cooperative launch, used when the launch shape of lbm_set_launch fits on the device at once;
+ * runs longer than 65536 steps take several launches).  A last odd step is a single launch.
+ * Every form computes the same values, bit for bit. */
 int lbm_step(lbm_ctx* ctx, int32_t nsteps);
 
 /* Enable (default) or disable the graph replays of lbm_step; results are identical. */
 int lbm_set_graphs(lbm_ctx* ctx, int32_t enable);
+
+/* Enable (enable = 1) or disable (0, default) the multi-step kernel of lbm_step; results are
+ * identical.  Other values: LBM_ERR_ARG. */
+int lbm_set_persistent(lbm_ctx* ctx, int32_t enable);
+
+/* How lbm_step issues a run of two or more steps under the current settings: *path receives
+ * LBM_PATH_MULTI (one multi-step launch), LBM_PATH_GRAPHS (graph replays of one launch per step)
+ * or LBM_PATH_SINGLE (one launch per step: graphs off, the bounds-checked kernel, or the first-
+ * wait timeout injection).  LBM_ERR_ARG for NULL arguments. */
+enum { LBM_PATH_SINGLE = 0, LBM_PATH_GRAPHS = 1, LBM_PATH_MULTI = 2 };
+int lbm_get_step_path(lbm_ctx* ctx, int32_t* path);
 
 /* Debugging aid standing in for a memory checker: run the following steps through a variant of
  * the step kernel that checks every global load, store and bulk copy of a step against the
@@ -267,15 +283,18 @@ int lbm_state_device(lbm_ctx* ctx, void** state, int32_t* nstrips, int64_t* elem
 int lbm_check(lbm_ctx* ctx);
 
 /* Fault injection for tests of the failure path (no counterpart in the paper).  While enabled
- * (enable = 1), every step launch makes the first bounded shared-memory wait of each warp give
- * up at once, as if its row copy had never arrived: the warp records LBM_ERR_TIMEOUT in the
+ * with enable = 1, every step launch makes the first bounded shared-memory wait of each warp
+ * give up at once, as if its row copy had never arrived: the warp records LBM_ERR_TIMEOUT in the
  * device error word, waits (with the normal bound) for the bulk copies it has in flight so that
- * none outlives the block, and returns without updating its nodes.  Nothing faults or hangs;
- * the state of those steps is invalid, lbm_check reports LBM_ERR_TIMEOUT, and re-initialising
- * the state (lbm_init_fields*, lbm_set_populations, lbm_load_state) clears the error.  Steps run
- * as single launches while enabled, through the plain step kernel (the bounds-checked kernel of
- * lbm_set_checked keeps its normal waits).  enable = 0 (default) returns to normal waits; other
- * values: LBM_ERR_ARG. */
+ * none outlives the block, and returns without updating its nodes.  Steps run as single launches
+ * of the plain step kernel then (the bounds-checked kernel of lbm_set_checked keeps its normal
+ * waits).  With enable = 2, runs of two or more steps of a context with the multi-step kernel
+ * enabled (lbm_set_persistent) go to it as usual, but its waits for the neighbouring warps
+ * between steps never succeed: after the first step every warp waits out its bound (two
+ * seconds), records LBM_ERR_TIMEOUT and returns, with no copy in flight.  Nothing faults or hangs in either mode; the state of those steps is invalid,
+ * lbm_check reports LBM_ERR_TIMEOUT, and re-initialising the state (lbm_init_fields*,
+ * lbm_set_populations, lbm_load_state) clears the error.  enable = 0 (default) returns to normal
+ * waits; other values: LBM_ERR_ARG. */
 int lbm_inject_timeout(lbm_ctx* ctx, int32_t enable);
 
 /* Diagnostics of the current state; see lbm_diag.  r_in < 0 skips dp_laplace.  Synchronises.

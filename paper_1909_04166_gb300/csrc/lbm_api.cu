@@ -37,7 +37,10 @@ struct lbm_ctx {
     // graphs of 2 (k + 1) steps (k < kGraphSizes) from buffer 0 / 1, flow sign + / -
     cudaGraphExec_t graph[2][2][16];
     int use_graph;
-    int cut_first_wait;    // lbm_inject_timeout
+    int cut_first_wait;    // lbm_inject_timeout (1: first shared-memory wait, 2: neighbour wait)
+    unsigned* prog;        // progress words of the multi-step kernel, one per warp
+    int use_multi;         // lbm_set_persistent
+    int multi_bps;         // resident blocks per SM of the multi-step kernel (0: not usable)
     int checked;           // steps run through the bounds-checked kernel (lbm_set_checked)
     int nsm;
     int last_cuda;
@@ -50,6 +53,11 @@ constexpr int kReduceSlots = 8;
 // parity returns): 32-step graphs while at least 32 steps are left, then one graph for the even
 // rest; a last odd step is a single launch.
 constexpr int kGraphSizes = 16;
+// Runs of n >= 2 steps go to the multi-step kernel instead where it is enabled and its grid is
+// co-resident, in launches of at most this many steps.
+constexpr int kMultiMaxSteps = 1 << 16;
+// Progress words allocated per SM (an SM holds at most 64 resident warps).
+constexpr int kMaxWarpsPerSm = 64;
 
 template <typename R> const Consts<R>& kref(const lbm_ctx* c);
 template <> const Consts<double>& kref<double>(const lbm_ctx* c) { return c->Kd; }
@@ -66,8 +74,14 @@ int cuda_fail(lbm_ctx* c, cudaError_t e)
 
 void* cur_state(lbm_ctx* c) { return c->buf + (size_t)c->cur * c->state_bytes; }
 
-// Rows per warp segment so that the warps of one launch fill the resident slots of every SM
-// about once (one wave): warps = strips * ceil(ny / rows).
+// Rows per warp segment: the warps of one launch fill the resident slots of every SM a whole
+// number of times (waves), with segments of about kSegRows rows.  One wave while its segments
+// are no taller than that; taller grids take more waves of shorter segments, which the block
+// scheduler balances across SMs (measured on the drop impact at 2048 columns: 4096 rows in one
+// wave of 72-row segments 36.8 GLUPS, in four waves of 18 rows 41.7; 2048 rows 38.1 against 39.4
+// in two waves; a partial wave is slower than one full wave).
+constexpr int kSegRows = 16;
+
 int default_seg_rows(const lbm_ctx* c)
 {
     int strips_per_row = 1;
@@ -82,6 +96,11 @@ int default_seg_rows(const lbm_ctx* c)
     long long nseg = resident / strips;
     if (nseg < 1) nseg = 1;
     long long h = (c->G.ny + nseg - 1) / nseg;
+    const long long waves = (h + kSegRows / 2) / kSegRows;
+    if (waves > 1) {
+        nseg *= waves;
+        h = (c->G.ny + nseg - 1) / nseg;
+    }
     if (h < 1) h = 1;
     if (h > c->G.ny) h = c->G.ny;
     return (int)h;
@@ -90,7 +109,44 @@ int default_seg_rows(const lbm_ctx* c)
 cudaError_t configure(lbm_ctx* c)
 {
     return with_variant(c->P.precision, c->variant, [&](auto r, auto s, auto v) {
-        return configure_step<decltype(r), decltype(s), decltype(v)::value>(c->block);
+        using R = decltype(r);
+        using S = decltype(s);
+        constexpr int V = decltype(v)::value;
+        cudaError_t e = configure_step<R, S, V>(c->block);
+        if (e != cudaSuccess) return e;
+        // the multi-step kernel is optional: without it runs go to the graphs
+        c->multi_bps = configure_multi<R, S, V>(c->block) == cudaSuccess
+                           ? multi_blocks_per_sm<R, S, V>(c->block)
+                           : 0;
+        cudaGetLastError();
+        return cudaSuccess;
+    });
+}
+
+// The multi-step kernel can take runs of this context: enabled, not in a test or debugging mode
+// that needs single launches, and its grid (the current segmentation) co-resident on the device.
+bool multi_fits(const lbm_ctx* c)
+{
+    if (!c->use_multi || c->multi_bps <= 0 || c->checked || c->cut_first_wait == 1) return false;
+    const int strips = with_variant(c->P.precision, c->variant, [&](auto r, auto s, auto v) {
+        return step_warp_strips<decltype(r), decltype(s), decltype(v)::value>(c->G.nstrips);
+    });
+    const long long nseg = (c->G.ny + c->seg_h - 1) / c->seg_h;
+    const long long warps = (long long)strips * nseg;
+    const int wpb = c->block / 32;
+    const long long blocks = (warps + wpb - 1) / wpb;
+    return blocks <= (long long)c->nsm * c->multi_bps && warps <= (long long)c->nsm * kMaxWarpsPerSm;
+}
+
+cudaError_t launch_multi_run(lbm_ctx* c, int nsteps, int sign)
+{
+    void* a = cur_state(c);
+    void* b = c->buf + (size_t)(1 - c->cur) * c->state_bytes;
+    return with_variant(c->P.precision, c->variant, [&](auto r, auto s, auto v) {
+        using R = decltype(r);
+        return launch_multi<R, decltype(s), decltype(v)::value>(
+            a, b, c->G, kref<R>(c), c->seg_h, c->block, c->err, sign ? sign : 1, nsteps,
+            c->prog, c->cut_first_wait == 2 ? 1 : 0, c->st);
     });
 }
 
@@ -203,6 +259,7 @@ int make_ctx(const lbm_params* params, void* ext, size_t ext_bytes, lbm_ctx** ou
     c->nsm = nsm > 0 ? nsm : 1;
     c->block = 128;
     c->use_graph = 1;
+    c->use_multi = 0;
     if (ext) {
         if (ext_bytes < 2 * c->state_bytes || (reinterpret_cast<uintptr_t>(ext) & 15)) {
             delete c;
@@ -222,12 +279,15 @@ int make_ctx(const lbm_params* params, void* ext, size_t ext_bytes, lbm_ctx** ou
     e = cudaMemsetAsync(c->buf, 0, 2 * c->state_bytes, c->st);
     if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->st);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&c->prog, (size_t)c->nsm * kMaxWarpsPerSm * sizeof(unsigned));
     if (e == cudaSuccess) e = configure(c);
     if (e == cudaSuccess) c->seg_h = default_seg_rows(c);
     if (e != cudaSuccess) {
         int r = cuda_fail(c, e);
         if (c->own) cudaFree(c->buf);
         if (c->err) cudaFree(c->err);
+        if (c->prog) cudaFree(c->prog);
         delete c;
         return r;
     }
@@ -509,7 +569,19 @@ int lbm_step(lbm_ctx* c, int32_t nsteps)
         long long run = nsteps - k;
         if (sign > 0 && c->P.reverse_step > 0)
             run = std::min<long long>(run, c->P.reverse_step - c->steps);
-        // runs of two or more steps as replays of prebuilt graphs of 2 .. 32 launches
+        // runs of two or more steps: one multi-step launch, or replays of prebuilt graphs of
+        // 2 .. 32 launches
+        if (run >= 2 && multi_fits(c)) {
+            while (run >= 2) {
+                const int chunk = (int)std::min<long long>(run, kMultiMaxSteps);
+                cudaError_t e = launch_multi_run(c, chunk, sign);
+                if (e != cudaSuccess) return cuda_fail(c, e);
+                if (chunk & 1) c->cur = 1 - c->cur;
+                k += chunk;
+                run -= chunk;
+                c->steps += chunk;
+            }
+        }
         while (c->use_graph && !c->checked && !c->cut_first_wait && run >= 2) {
             const int chunk = (int)std::min<long long>(run & ~1LL, 2 * kGraphSizes);
             cudaError_t e = ensure_graphs(c, sign);
@@ -539,9 +611,25 @@ int lbm_set_graphs(lbm_ctx* c, int32_t enable)
     return LBM_OK;
 }
 
-int lbm_inject_timeout(lbm_ctx* c, int32_t enable)
+int lbm_set_persistent(lbm_ctx* c, int32_t enable)
 {
     if (!c || enable < 0 || enable > 1) return LBM_ERR_ARG;
+    c->use_multi = enable;
+    return LBM_OK;
+}
+
+int lbm_get_step_path(lbm_ctx* c, int32_t* path)
+{
+    if (!c || !path) return LBM_ERR_ARG;
+    if (multi_fits(c)) *path = LBM_PATH_MULTI;
+    else if (c->use_graph && !c->checked && !c->cut_first_wait) *path = LBM_PATH_GRAPHS;
+    else *path = LBM_PATH_SINGLE;
+    return LBM_OK;
+}
+
+int lbm_inject_timeout(lbm_ctx* c, int32_t enable)
+{
+    if (!c || enable < 0 || enable > 2) return LBM_ERR_ARG;
     c->cut_first_wait = enable;
     return LBM_OK;
 }
@@ -747,6 +835,7 @@ void lbm_destroy(lbm_ctx* c)
     if (c->scratch) cudaFree(c->scratch);
     if (c->partials) cudaFree(c->partials);
     if (c->err) cudaFree(c->err);
+    if (c->prog) cudaFree(c->prog);
     drop_graphs(c);
     delete c;
 }

@@ -27,6 +27,16 @@ int step_warp_strips(int nstrips);
 template <typename R, typename S, int V>
 cudaError_t build_step_graph(const void*, const void*, const Geometry&, const Consts<R>&, int,
                              int, int*, int, int, cudaGraphExec_t*);
+// Several steps in one cooperative launch, each warp waiting only for its neighbours between
+// steps (lbm_step.cu, multi_body); multi_blocks_per_sm is its residency (0 if unknown).
+template <typename R, typename S, int V>
+cudaError_t configure_multi(int block);
+template <typename R, typename S, int V>
+int multi_blocks_per_sm(int block);
+template <typename R, typename S, int V>
+cudaError_t launch_multi(void* a, void* b, const Geometry&, const Consts<R>&, int seg_h,
+                         int block, int* err, int flow_sign, int nsteps, unsigned* prog,
+                         int far_wait, cudaStream_t);
 // The bounds-checked step (cascaded coupled form only): every global load, store and bulk copy
 // of a step is range-checked against the two state buffers; an access outside is skipped and
 // the error word gets bit 1 (LBM_ERR_INDEX).

@@ -55,6 +55,13 @@ struct StepLaunch {
                             // of the timeout path); the drain of copies in flight keeps its limit
 };
 
+// March direction parity of a step: the two state buffers alternate as source, so consecutive
+// steps march in opposite directions.
+__host__ __device__ inline int flip_of(const void* src, const void* dst)
+{
+    return reinterpret_cast<uintptr_t>(src) > reinterpret_cast<uintptr_t>(dst) ? 1 : 0;
+}
+
 // Step variants: bit 0 single relaxation time (Sec. 7) instead of the cascaded rates; bit 1 the
 // interface lattice alone in the imposed shear flow (Sec. 6.1); bit 2 the Langmuir isotherm
 // (Sec. 6.7) instead of the linear sigma(T).
@@ -81,6 +88,12 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p)
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+// Invalidate an mbarrier whose phases have all completed, so that its memory may be initialised
+// again (the multi-step kernel re-initialises the ring's barriers at every step).
+__device__ __forceinline__ void mbar_inval(uint32_t bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ void mbar_init_fence()
 {
@@ -122,6 +135,15 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity)
     for (unsigned it = 0; it < WAIT_LIMIT; ++it)
         if (__all_sync(FULL, mbar_try_wait(bar, parity))) return true;
     return false;
+}
+
+// A halo load: through the read-only cache, or (COH) through L2 only, for data that other SMs
+// wrote earlier in the same launch.
+template <bool COH, typename T>
+__device__ __forceinline__ T ld_halo(const T* p)
+{
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
 }
 
 template <typename R>
@@ -646,9 +668,12 @@ __device__ __forceinline__ void push_packed(const F2 g[9], const F2 f[9], const 
 }
 
 // The march of one warp over one strip x segment of one grid: everything the step does for
-// those nodes.  Used by the single-grid kernel and by the batched kernel.
-template <typename R, typename S, int V, bool CK = false>
-__device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__ dst,
+// those nodes.  Used by the single-grid kernels and by the batched kernel.  False if a wait
+// timed out (the error word is set and no copy is left in flight).  COH: the halo columns are
+// read through L2 only (ld.global.cg) instead of the read-only cache, as the multi-step kernel
+// needs, whose source buffer was written by other SMs during the same launch.
+template <typename R, typename S, int V, bool CK = false, bool COH = false>
+__device__ __forceinline__ bool march(const S* __restrict__ src, S* __restrict__ dst,
                                       const Geometry& G, const Consts<R>& K, int strip, int seg,
                                       int seg_h, int* err, int flow_sign, int flip,
                                       long long chk_shrink = 0, bool cut_first = false)
@@ -706,17 +731,17 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
         const S* rb = row_ptr(src, row_of(k));
         if (hlane) {
             if constexpr (NARROW) {
-                if (B.rd(rb + hoffl, sizeof(S))) hl = R(narrow_to_f(__ldg(rb + hoffl))) * hinv;
-                if (B.rd(rb + hoffr, sizeof(S))) hr = R(narrow_to_f(__ldg(rb + hoffr))) * hinv;
+                if (B.rd(rb + hoffl, sizeof(S))) hl = R(narrow_to_f(ld_halo<COH>(rb + hoffl))) * hinv;
+                if (B.rd(rb + hoffr, sizeof(S))) hr = R(narrow_to_f(ld_halo<COH>(rb + hoffr))) * hinv;
             } else {
-                if (B.rd(rb + hoffl, sizeof(S))) hl = R(__ldg(rb + hoffl));
-                if (B.rd(rb + hoffr, sizeof(S))) hr = R(__ldg(rb + hoffr));
+                if (B.rd(rb + hoffl, sizeof(S))) hl = R(ld_halo<COH>(rb + hoffl));
+                if (B.rd(rb + hoffr, sizeof(S))) hr = R(ld_halo<COH>(rb + hoffr));
             }
         } else if (zlane) {
             const float* zl = reinterpret_cast<const float*>(rb + hoffl);
             const float* zr = reinterpret_cast<const float*>(rb + hoffr);
-            if (B.rd(zl, sizeof(float))) hl = R(__ldg(zl));
-            if (B.rd(zr, sizeof(float))) hr = R(__ldg(zr));
+            if (B.rd(zl, sizeof(float))) hl = R(ld_halo<COH>(zl));
+            if (B.rd(zr, sizeof(float))) hr = R(ld_halo<COH>(zr));
         }
     };
 
@@ -750,11 +775,11 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     Row3<R> rb, rc, rn;   // rows behind, current, ahead (in marching order)
     R hl, hr, hl2, hr2;
     halo_load(-1, hl, hr);
-    if (cut_first || !wait_k(-1, 0)) { fail(-1); return; }
+    if (cut_first || !wait_k(-1, 0)) { fail(-1); return false; }
     window_row<R, S, SHEAR>(tiles, lane, wlast, hl, hr, K, rb);
     issue(NS - 1, 0);
     halo_load(0, hl, hr);
-    if (!wait_k(0, 1)) { fail(0); return; }
+    if (!wait_k(0, 1)) { fail(0); return false; }
     window_row<R, S, SHEAR>(tiles + TE, lane, wlast, hl, hr, K, rc);
     halo_load(1, hl2, hr2);
 
@@ -828,8 +853,14 @@ __device__ __forceinline__ void march(const S* __restrict__ src, S* __restrict__
     // misses in the instruction cache (measured slower)
     for (int i = 0, st = 1; i < nrows; ++i, st = (st + 1 == NS ? 0 : st + 1)) {
         body(i, st);
-        if (!ok) return;
+        if (!ok) return false;
     }
+    // every copy issued has completed (the last wait was for row nrows): release the barriers
+    __syncwarp();
+    if (lane == 0)
+        for (int s = 0; s < NS; ++s) mbar_inval(bar0 + 8 * s);
+    __syncwarp();
+    return true;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -932,8 +963,8 @@ __device__ __forceinline__ Win<float> half_win(const Win<F2>& w, bool b)
     return Win<float>{h(w.sw), h(w.s), h(w.se), h(w.w), h(w.c), h(w.e), h(w.nw), h(w.n), h(w.ne)};
 }
 
-template <typename S, int V, bool CK = false>
-__device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict__ dst,
+template <typename S, int V, bool CK = false, bool COH = false>
+__device__ __forceinline__ bool march2(const S* __restrict__ src, S* __restrict__ dst,
                                        const Geometry& G, const Consts<float>& K, int wstrip,
                                        int seg, int seg_h, int* err, int flow_sign, int flip,
                                        long long chk_shrink = 0, bool cut_first = false)
@@ -996,13 +1027,13 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
         hr = 0.0f;
         const S* rb = row_ptr(src, row_of(k));
         if (hlane) {
-            if (B.rd(rb + hoffl, sizeof(S))) hl = narrow_to_f_or_self(__ldg(rb + hoffl)) * hinv;
-            if (B.rd(rb + hoffr, sizeof(S))) hr = narrow_to_f_or_self(__ldg(rb + hoffr)) * hinv;
+            if (B.rd(rb + hoffl, sizeof(S))) hl = narrow_to_f_or_self(ld_halo<COH>(rb + hoffl)) * hinv;
+            if (B.rd(rb + hoffr, sizeof(S))) hr = narrow_to_f_or_self(ld_halo<COH>(rb + hoffr)) * hinv;
         } else if (zlane) {
             const float* zl = reinterpret_cast<const float*>(rb + hoffl);
             const float* zr = reinterpret_cast<const float*>(rb + hoffr);
-            if (B.rd(zl, sizeof(float))) hl = __ldg(zl);
-            if (B.rd(zr, sizeof(float))) hr = __ldg(zr);
+            if (B.rd(zl, sizeof(float))) hl = ld_halo<COH>(zl);
+            if (B.rd(zr, sizeof(float))) hr = ld_halo<COH>(zr);
         }
     };
 
@@ -1047,11 +1078,11 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
     Row3P rb, rc, rn;
     float hl, hr, hl2, hr2;
     halo_load(-1, hl, hr);
-    if (cut_first || !wait_k(-1, 0)) { fail(-1); return; }
+    if (cut_first || !wait_k(-1, 0)) { fail(-1); return false; }
     window_row2<S, SHEAR>(tiles + TB, jp, lane, lastA, lastB, hl, hr, K, rb);
     issue(NS - 1, 0);
     halo_load(0, hl, hr);
-    if (!wait_k(0, 1)) { fail(0); return; }
+    if (!wait_k(0, 1)) { fail(0); return false; }
     window_row2<S, SHEAR>(tiles + STAGE + TB, jp, lane, lastA, lastB, hl, hr, K, rc);
     halo_load(1, hl2, hr2);
 
@@ -1171,8 +1202,14 @@ __device__ __forceinline__ void march2(const S* __restrict__ src, S* __restrict_
 
     for (int i = 0, st = 1; i < nrows; ++i, st = (st + 1 == NS ? 0 : st + 1)) {
         body(i, st);
-        if (!ok) return;
+        if (!ok) return false;
     }
+    // every copy issued has completed (the last wait was for row nrows): release the barriers
+    __syncwarp();
+    if (lane == 0)
+        for (int s = 0; s < NS; ++s) mbar_inval(bar0 + 8 * s);
+    __syncwarp();
+    return true;
 }
 
 // Every step with FP32 arithmetic runs paired (two tiles per warp); FP64 one tile per warp.
@@ -1244,6 +1281,160 @@ constexpr auto step_kernel_of()
 {
     if constexpr (Narrow<S>::value) return step_kernel_narrow<R, S, V>;
     else return step_kernel<R, S, V>;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Several time steps in one launch.  Every warp keeps its strip and segment from step to step,
+// and before a step it waits only for the warps whose nodes that step reads or overwrites.  A
+// warp reads its nodes and one halo row and column around them; each of those was written in
+// the previous step by pushes from at most one row and column further out, and the nodes a warp
+// writes (its own and one row and column around them) were read in the previous step by the
+// warps whose halos reach them.  Both reach two nodes beyond the warp's own: the neighbouring
+// strip and segment in each direction when every strip and segment is at least two nodes wide
+// (reach 1), two strips or segments when one of them is a single column or row (reach 2, the
+// host decides).  A warp publishes s + 1 in its progress word once all its stores of step s are
+// visible at device scope; step s + 1 of a warp starts when the progress words of itself and of
+// the warps within the reach are all >= s + 1.
+// Within one step warps never wait for each other, so the step-to-step barrier of separate
+// launches (every warp waits for the slowest) becomes a local one; the launch must be
+// co-resident (cooperative), which the host guarantees.  Every wait is bounded: on a timeout,
+// or once another warp has set the error word, a warp returns between two steps, when none of
+// its copies is in flight.
+// ---------------------------------------------------------------------------------------------
+// Bound of a wait for the neighbouring warps: two seconds of the global timer (a neighbour's
+// step takes microseconds to tens of milliseconds), and an iteration cap in case the timer
+// does not advance.
+constexpr unsigned long long NEIGHBOUR_WAIT_NS = 2000000000ull;
+constexpr unsigned NEIGHBOUR_WAIT_ITERS = 1u << 27;
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Warp-collective: wait until the progress words of the warp at (seg, strip) and of the warps
+// within rx strips and ry segments of it (at most 25; periodic wrap in both directions, so a
+// warp beyond a wall is waited for without need, which is harmless) reach `target`.  False on
+// timeout (error word set) or when another warp has already failed.  far: test hook, the target
+// is never reached.
+__device__ __forceinline__ bool wait_neighbours(const unsigned* prog, int seg, int strip, int nseg,
+                                                int nstrip, int rx, int ry, unsigned target,
+                                                int* err, int lane, bool far)
+{
+    const unsigned* p = prog;
+    const int wx = 2 * rx + 1;
+    const bool mine = lane < wx * (2 * ry + 1);
+    if (mine) {
+        int s2 = seg + lane / wx - ry, t2 = strip + lane % wx - rx;
+        s2 = ((s2 % nseg) + nseg) % nseg;
+        t2 = ((t2 % nstrip) + nstrip) % nstrip;
+        p = prog + (long long)s2 * nstrip + t2;
+    }
+    if (far) target += 0x40000000u;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 0; it < NEIGHBOUR_WAIT_ITERS; ++it) {
+        const unsigned v = mine ? ld_acquire(p) : target;
+        if (__all_sync(FULL, (int)(v - target) >= 0)) {
+            __syncwarp();
+            __threadfence();
+            // the next copies go through the async proxy: order them after the acquired stores
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            return true;
+        }
+        // lane 0 decides for the warp: another warp failed, or this wait ran out of time
+        int stop = 0;
+        if (lane == 0)
+            stop = *reinterpret_cast<volatile int*>(err) != 0
+                       ? 1
+                       : (global_ns() - t0 > NEIGHBOUR_WAIT_NS ? 2 : 0);
+        stop = __shfl_sync(FULL, stop, 0);
+        if (stop == 1) return false;
+        if (stop == 2) break;
+        __nanosleep(64);
+    }
+    if (lane == 0) atomicCAS(err, 0, 4);   // 4: a neighbour wait (1: a shared-memory wait)
+    return false;
+}
+
+// Publish the end of step s of this warp: every lane's stores are made visible at device scope,
+// then lane 0 releases the progress word.
+__device__ __forceinline__ void publish_step(unsigned* word, unsigned v, int lane)
+{
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(word, v);
+}
+
+// Launch fields of the multi-step kernel beyond those of one step.
+struct MultiLaunch {
+    int nsteps;        // steps of this launch (the buffers alternate: a -> b -> a ...)
+    unsigned* prog;    // one progress word per warp, zero at launch
+    int rx, ry;        // reach of the waits in strips and segments (1 or 2)
+    int far_wait;      // test hook: the waits for neighbours never succeed
+};
+
+template <typename R, typename S, int V>
+__device__ __forceinline__ void multi_body(S* a, S* b, const Geometry& G, const Consts<R>& K,
+                                           const StepLaunch& L, const MultiLaunch& M)
+{
+    const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    constexpr int NT = tiles_per_warp<R, S, V>();
+    const int wstrips = (G.nstrips + NT - 1) / NT;
+    const int strip = warp % wstrips;
+    const int seg = warp / wstrips;
+    if (seg >= L.nseg) return;                       // warp-uniform; not anyone's neighbour
+    for (int s = 0; s < M.nsteps; ++s) {
+        if (s > 0 && !wait_neighbours(M.prog, seg, strip, L.nseg, wstrips, M.rx, M.ry,
+                                      (unsigned)s, L.err, lane, M.far_wait != 0))
+            return;
+        const S* src = (s & 1) ? b : a;
+        S* dst = (s & 1) ? a : b;
+        const int flip = flip_of(src, dst);
+        bool ok;
+        if constexpr (NT == 2)
+            ok = march2<S, V, false, true>(src, dst, G, K, strip, seg, L.seg_h, L.err,
+                                           L.flow_sign, flip);
+        else
+            ok = march<R, S, V, false, true>(src, dst, G, K, strip, seg, L.seg_h, L.err,
+                                             L.flow_sign, flip);
+        if (!ok) return;
+        publish_step(M.prog + warp, (unsigned)(s + 1), lane);
+    }
+}
+
+template <typename R, typename S, int V>
+__global__ void __launch_bounds__(256)
+step_kernel_multi(S* a, S* b, Geometry G, Consts<R> K, StepLaunch L, MultiLaunch M)
+{
+    multi_body<R, S, V>(a, b, G, K, L, M);
+}
+
+// The 16-bit forms, held to the register budget of step_kernel_narrow.
+template <typename R, typename S, int V>
+__global__ void __launch_bounds__(256) __maxnreg__(NarrowRegs<S>::value)
+step_kernel_multi_narrow(S* a, S* b, Geometry G, Consts<R> K, StepLaunch L, MultiLaunch M)
+{
+    multi_body<R, S, V>(a, b, G, K, L, M);
+}
+
+template <typename R, typename S, int V>
+constexpr auto multi_kernel_of()
+{
+    if constexpr (Narrow<S>::value) return step_kernel_multi_narrow<R, S, V>;
+    else return step_kernel_multi<R, S, V>;
 }
 
 // One time step of many independent grids in one launch: warp w takes task w = (case, local
@@ -1491,12 +1682,6 @@ int step_blocks_per_sm(int block)
     return nb > 0 ? nb : 1;
 }
 
-// March direction parity of a step: the two state buffers alternate as source, so consecutive
-// steps march in opposite directions.
-inline int flip_of(const void* src, const void* dst)
-{
-    return reinterpret_cast<uintptr_t>(src) > reinterpret_cast<uintptr_t>(dst) ? 1 : 0;
-}
 
 template <typename R, typename S, int V>
 cudaError_t launch_step(const void* src, void* dst, const Geometry& G, const Consts<R>& K,
@@ -1516,6 +1701,63 @@ cudaError_t launch_step(const void* src, void* dst, const Geometry& G, const Con
     step_kernel_of<R, S, V>()<<<(unsigned)grid, block, step_smem_bytes<R, S, V>(block), st>>>(
         static_cast<const S*>(src), static_cast<S*>(dst), G, K, L);
     return cudaGetLastError();
+}
+
+// The multi-step kernel: configuration, residency and launch.  launch_multi clears the progress
+// words, then launches cooperatively (every block resident at once, or the launch fails and
+// nothing runs); the host calls it only when the grid fits (multi_blocks_per_sm).
+template <typename R, typename S, int V>
+cudaError_t configure_multi(int block)
+{
+    cudaError_t e = cudaFuncSetAttribute(multi_kernel_of<R, S, V>(),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)step_smem_bytes<R, S, V>(block));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(multi_kernel_of<R, S, V>(),
+                                cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+
+template <typename R, typename S, int V>
+int multi_blocks_per_sm(int block)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, multi_kernel_of<R, S, V>(), block,
+                                                      step_smem_bytes<R, S, V>(block)) !=
+        cudaSuccess)
+        return 0;
+    return nb;
+}
+
+template <typename R, typename S, int V>
+cudaError_t launch_multi(void* a, void* b, const Geometry& G, const Consts<R>& K, int seg_h,
+                         int block, int* err, int flow_sign, int nsteps, unsigned* prog,
+                         int far_wait, cudaStream_t st)
+{
+    StepLaunch L = {};
+    L.seg_h = seg_h;
+    L.nseg = (G.ny + seg_h - 1) / seg_h;
+    L.err = err;
+    L.flow_sign = flow_sign;
+    // reach of the waits: 2 where the last strip (columns) or segment (rows) is one node wide
+    constexpr int COLS = 32 * tiles_per_warp<R, S, V>();
+    const int wstrips = step_warp_strips<R, S, V>(G.nstrips);
+    const int last_w = G.nx - (wstrips - 1) * COLS;
+    const int last_h = G.ny - (L.nseg - 1) * seg_h;
+    MultiLaunch M = {nsteps, prog, last_w >= 2 || wstrips == 1 ? 1 : 2,
+                     (seg_h >= 2 && last_h >= 2) || L.nseg == 1 ? 1 : 2, far_wait};
+    const long long warps = (long long)wstrips * L.nseg;
+    const int wpb = block / 32;
+    const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
+    cudaError_t e = cudaMemsetAsync(prog, 0, (size_t)warps * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    S* pa = static_cast<S*>(a);
+    S* pb = static_cast<S*>(b);
+    Geometry g = G;
+    Consts<R> k = K;
+    void* args[] = {(void*)&pa, (void*)&pb, (void*)&g, (void*)&k, (void*)&L, (void*)&M};
+    return cudaLaunchCooperativeKernel((const void*)multi_kernel_of<R, S, V>(), dim3(grid),
+                                       dim3(block), args, step_smem_bytes<R, S, V>(block), st);
 }
 
 // The bounds-checked step of the coupled cascaded form (variant 0): configuration and launch,
@@ -1695,7 +1937,12 @@ cudaError_t launch_unpack(const double* in, void* state, const Geometry& G, cons
                                                    cudaGraphExec_t*);                           \
     template cudaError_t launch_step<R, S, V>(const void*, void*, const Geometry&,              \
                                               const Consts<R>&, int, int, int*, int, int,       \
-                                              cudaStream_t);
+                                              cudaStream_t);                                    \
+    template cudaError_t configure_multi<R, S, V>(int);                                         \
+    template int multi_blocks_per_sm<R, S, V>(int);                                             \
+    template cudaError_t launch_multi<R, S, V>(void*, void*, const Geometry&, const Consts<R>&, \
+                                               int, int, int*, int, int, unsigned*, int,        \
+                                               cudaStream_t);
 
 #define CMLBM_INSTANTIATE(R, S)                                                                   \
     template cudaError_t configure_step_checked<R, S>(int);                                     \

@@ -50,7 +50,8 @@ EXPORTS = [
     "lbm_set_populations", "lbm_save_state", "lbm_load_state", "lbm_state_device",
     "lbm_diagnostics", "lbm_set_launch",
     "lbm_get_launch", "lbm_steps_done", "lbm_destroy", "lbm_strerror", "lbm_last_cuda_error",
-    "lbm_check", "lbm_set_graphs", "lbm_set_checked", "lbm_diagnostics_noalloc",
+    "lbm_check", "lbm_set_graphs", "lbm_set_persistent", "lbm_get_step_path",
+    "lbm_set_checked", "lbm_diagnostics_noalloc",
     "lbm_inject_timeout",
     "lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_get_fields",
     "lbm_batch_get_populations", "lbm_batch_set_launch", "lbm_batch_get_launch",
@@ -138,6 +139,8 @@ def lib(build_if_missing: bool = True):
     L.lbm_last_cuda_error.argtypes = [vp]
     L.lbm_check.argtypes = [vp]
     L.lbm_set_graphs.argtypes = [vp, i32]
+    L.lbm_set_persistent.argtypes = [vp, i32]
+    L.lbm_get_step_path.argtypes = [vp, P(i32)]
     L.lbm_set_checked.argtypes = [vp, i32]
     L.lbm_inject_timeout.argtypes = [vp, i32]
     dd = ctypes.c_double
@@ -289,6 +292,19 @@ def lbm_set_graphs(ctx, enable: bool) -> None:
     _check(lib().lbm_set_graphs(ctx, int(bool(enable))), "lbm_set_graphs")
 
 
+def lbm_set_persistent(ctx, enable: bool) -> None:
+    _check(lib().lbm_set_persistent(ctx, 1 if enable else 0), "lbm_set_persistent")
+
+
+LBM_PATH_SINGLE, LBM_PATH_GRAPHS, LBM_PATH_MULTI = 0, 1, 2
+
+
+def lbm_get_step_path(ctx) -> int:
+    v = ctypes.c_int32()
+    _check(lib().lbm_get_step_path(ctx, ctypes.byref(v)), "lbm_get_step_path")
+    return int(v.value)
+
+
 def lbm_set_checked(ctx, enable) -> None:
     """enable: 0 / False plain kernel, 1 / True checked kernel, 2 the checker's self-test."""
     _check(lib().lbm_set_checked(ctx, int(enable)), "lbm_set_checked")
@@ -299,8 +315,9 @@ def lbm_check(ctx) -> None:
 
 
 def lbm_inject_timeout(ctx, enable) -> None:
-    """Test hook of the failure path: while enabled the first bounded wait of every warp of a
-    step gives up at once (the step reports LBM_ERR_TIMEOUT; nothing faults or hangs)."""
+    """Test hook of the failure path: 1, the first bounded wait of every warp of a step gives
+    up at once; 2, the multi-step kernel's waits for neighbouring warps never succeed (both
+    report LBM_ERR_TIMEOUT; nothing faults or hangs)."""
     _check(lib().lbm_inject_timeout(ctx, int(enable)), "lbm_inject_timeout")
 
 

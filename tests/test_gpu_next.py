@@ -29,10 +29,13 @@ def oracle_run(case, nsteps):
     return oc, g, f
 
 
-def gpu_run(case, precision, nsteps, graphs=True):
+def gpu_run(case, precision, nsteps, path="graphs"):
+    """path: how runs of two or more steps are issued (one launch per step, graph replays, the
+    default, or the multi-step kernel)."""
     with lbm.Simulation(case, precision=precision) as sim:
         sim.init_case()
-        lbm.lbm_set_graphs(sim.ctx, graphs)
+        lbm.lbm_set_persistent(sim.ctx, path == "multi")
+        lbm.lbm_set_graphs(sim.ctx, path != "single")
         sim.step(nsteps)
         g, f = sim.populations()
         fl = sim.fields()
@@ -149,14 +152,15 @@ def _shear(L0, u0, reverse_step, collision=0, nx=None):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
-@pytest.mark.parametrize("graphs", [False, True])
+@pytest.mark.parametrize("path", ["single", "graphs", "multi"])
 @pytest.mark.parametrize("collision", [0, 1])
-def test_shear_flow_parity_across_the_reversal(precision, tol, graphs, collision):
-    """100 steps with the reversal at step 40: graph chunks of 32 on both sides of it, single
-    launches around it; f and the reported fields against the oracle."""
+def test_shear_flow_parity_across_the_reversal(precision, tol, path, collision):
+    """100 steps with the reversal at step 40: one launch per step, graph chunks of 32 on both
+    sides of it, or one multi-step launch on each side; f and the reported fields against the
+    oracle."""
     case = _shear(48, 0.03, 40, collision)
     oc, _, f_ref = oracle_run(case, 100)
-    _, f, fl = gpu_run(case, precision, 100, graphs=graphs)
+    _, f, fl = gpu_run(case, precision, 100, path=path)
     assert rel_l2(f, f_ref) <= tol
     oc.t = 100
     ref = O.fields(oc, np.zeros_like(f_ref), f_ref)

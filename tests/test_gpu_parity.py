@@ -106,19 +106,25 @@ def test_launch_shape_does_not_change_results(prec):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
 def test_graph_replays_match_single_launches(precision):
-    """Runs of every length (graphs of 32, 16, 8, 4 and 2 chained launches, a last odd step
-    alone) give the same state, bit for bit, as one launch per step."""
+    """Runs of every length give the same state, bit for bit, as one launch per step: as graph
+    replays (the default: graphs of 32, 16, 8, 4 and 2 chained launches, a last odd step alone)
+    and as multi-step launches."""
     case = W.random_drop(64, 48, seed=12, wall_y=True, rho_ratio=100.0)
     outs = []
-    for graphs in (False, True):
+    for persistent, graphs, path in ((False, False, lbm.LBM_PATH_SINGLE),
+                                     (False, True, lbm.LBM_PATH_GRAPHS),
+                                     (True, True, lbm.LBM_PATH_MULTI)):
         with lbm.Simulation(case, precision=precision) as sim:
             sim.init_case()
+            lbm.lbm_set_persistent(sim.ctx, persistent)
             lbm.lbm_set_graphs(sim.ctx, graphs)
+            assert lbm.lbm_get_step_path(sim.ctx) == path
             for n in (70, 33, 20, 3, 2, 1, 17, 31):
                 sim.step(n)
             assert lbm.lbm_steps_done(sim.ctx) == 177
             outs.append(sim.populations())
-    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    for g, f in outs[1:]:
+        assert np.array_equal(outs[0][0], g) and np.array_equal(outs[0][1], f)
 
 
 def test_checkpoint_restart_is_exact():
