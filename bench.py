@@ -84,10 +84,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-# DRAM traffic per launch of the step kernel from an ncu capture (profiles/), keyed by the
-# hash of the kernel sources it was taken on; scaled by node count to the bench workload.  The
-# figures are steady-state launches (caches not flushed between launches, as in the timed run;
-# mean of three consecutive launches).
+# DRAM traffic per launch of the step kernel from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by the hash of the kernel sources it was taken on; scaled by
+# node count to the bench workload.  The figures are steady-state launches (caches not flushed
+# between launches, as in the timed run; mean of three consecutive launches).
 NCU_TRAFFIC = {
     # FP32 step on the 2048 x 1024 impact, sources 988d57dd778814ff: read 106.25 MB + write
     # 149.92 MB per launch
