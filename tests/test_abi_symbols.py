@@ -147,3 +147,26 @@ def test_batch_layout_is_checked_without_a_device():
             lbm.lbm_batch_create_ex(p, layout)
         assert e.value.status == lbm.LBM_ERR_ARG
     assert lbm.lib().lbm_batch_case_transposed(ctypes.c_void_p(), 0) == lbm.LBM_ERR_ARG
+
+
+def test_grid_extents_are_validated_without_a_device():
+    """1 .. 65536 nodes along each axis (include/cmlbm.h); 0, negative and 65537 are refused
+    before any device work, and the state size of the largest extents is computed in 64 bits."""
+    from paper_1909_04166_gb300 import workloads as W
+
+    def state_bytes(nx, ny, precision="fp32"):
+        case = W.random_drop(8, 8, seed=0)
+        case.update(nx=nx, ny=ny)
+        return lbm.lbm_state_bytes(lbm.make_params(case, precision))
+
+    for nx, ny in ((0, 8), (8, 0), (-1, 8), (8, -5), (65537, 8), (8, 65537)):
+        with pytest.raises(lbm.LbmError) as e:
+            state_bytes(nx, ny)
+        assert e.value.status == lbm.LBM_ERR_ARG, (nx, ny)
+    # two buffers of ny rows x ceil(nx / 32) tiles (2304 B per FP32 tile, 1408 B 16-bit,
+    # 4608 B FP64)
+    assert state_bytes(1, 1) == 2 * 2304
+    assert state_bytes(65536, 65536) == 2 * 65536 * 2048 * 2304
+    assert state_bytes(65536, 65536, "fp16") == 2 * 65536 * 2048 * 1408
+    assert state_bytes(65536, 65536, "fp64") == 2 * 65536 * 2048 * 4608
+    assert state_bytes(33, 1, "bf16") == 2 * 2 * 1408

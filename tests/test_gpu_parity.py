@@ -127,6 +127,25 @@ def test_graph_replays_match_single_launches(precision):
         assert np.array_equal(outs[0][0], g) and np.array_equal(outs[0][1], f)
 
 
+@pytest.mark.parametrize("persistent", [False, True])
+def test_zero_steps_change_nothing(persistent):
+    """lbm_step(ctx, 0) is a no-op (state bytes and step counter), before and after other
+    runs, on every launch path."""
+    case = W.random_drop(37, 29, seed=4, wall_x=True, rho_ratio=100.0)
+    with lbm.Simulation(case, precision="fp32") as sim:
+        sim.init_case()
+        lbm.lbm_set_persistent(sim.ctx, persistent)
+        a, ta = sim.save_state()
+        sim.step(0)
+        b, tb = sim.save_state()
+        assert ta == tb == 0 and np.array_equal(a, b)
+        sim.step(5)
+        a, ta = sim.save_state()
+        sim.step(0)
+        b, tb = sim.save_state()
+        assert ta == tb == 5 and np.array_equal(a, b)
+
+
 def test_checkpoint_restart_is_exact():
     case = W.random_drop(48, 40, seed=8, wall_x=True, rho_ratio=50.0)
     for prec in ("fp64", "fp32"):
