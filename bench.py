@@ -89,14 +89,14 @@ def kernel_source_hash() -> str:
 # node count to the bench workload.  The figures are steady-state launches (caches not flushed
 # between launches, as in the timed run; mean of three consecutive launches).
 NCU_TRAFFIC = {
-    # FP32 step on the 2048 x 1024 impact, sources 988d57dd778814ff: read 106.25 MB + write
-    # 149.92 MB per launch
-    ("988d57dd778814ff", "impact", "fp32"): 256_169_131,
-    # FP16-storage step on the same grid and sources: read 46.38 MB + write 92.38 MB per launch
-    ("988d57dd778814ff", "impact", "fp16"): 138_761_557,
+    # FP32 step on the 2048 x 1024 impact, sources 927ef239fb157979: read 107.30 MB + write
+    # 149.85 MB per launch
+    ("927ef239fb157979", "impact", "fp32"): 257_148_757,
+    # FP16-storage step on the same grid and sources: read 47.39 MB + write 92.31 MB per launch
+    ("927ef239fb157979", "impact", "fp16"): 139_706_539,
     # batched step of the 512-case ensemble (autotuned: 8 rows per task, 128-thread blocks), same
-    # sources: read 833.36 MB + write 759.27 MB per launch
-    ("988d57dd778814ff", "ensemble", "fp32"): 1_592_624_725,
+    # sources: read 832.55 MB + write 760.84 MB per launch
+    ("927ef239fb157979", "ensemble", "fp32"): 1_593_382_229,
 }
 
 
