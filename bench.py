@@ -89,14 +89,14 @@ def kernel_source_hash() -> str:
 # node count to the bench workload.  The figures are steady-state launches (caches not flushed
 # between launches, as in the timed run; mean of three consecutive launches).
 NCU_TRAFFIC = {
-    # FP32 step on the 2048 x 1024 impact, sources 927ef239fb157979: read 107.30 MB + write
-    # 149.85 MB per launch
-    ("927ef239fb157979", "impact", "fp32"): 257_148_757,
-    # FP16-storage step on the same grid and sources: read 47.39 MB + write 92.31 MB per launch
-    ("927ef239fb157979", "impact", "fp16"): 139_706_539,
+    # FP32 step on the 2048 x 1024 impact, sources 20753e7a8ad56b8d: read 107.08 MB + write
+    # 149.93 MB per launch
+    ("20753e7a8ad56b8d", "impact", "fp32"): 257_005_312,
+    # FP16-storage step on the same grid and sources: read 47.83 MB + write 92.33 MB per launch
+    ("20753e7a8ad56b8d", "impact", "fp16"): 140_161_536,
     # batched step of the 512-case ensemble (autotuned: 8 rows per task, 128-thread blocks), same
-    # sources: read 832.55 MB + write 760.84 MB per launch
-    ("927ef239fb157979", "ensemble", "fp32"): 1_593_382_229,
+    # sources: read 844.90 MB + write 760.66 MB per launch
+    ("20753e7a8ad56b8d", "ensemble", "fp32"): 1_605_556_395,
 }
 
 

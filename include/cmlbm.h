@@ -66,9 +66,10 @@ extern "C" {
 #define LBM_ERR_UNSUPPORTED (-7)/* precision mode not built into this library, or a collision
                                    model / flow mode not offered with the precision or in a
                                    batch */
-#define LBM_ERR_TIMEOUT (-8)    /* a bounded wait inside the step kernel gave up; the state of
-                                   that step is invalid (reported by the next synchronising
-                                   call or lbm_check) */
+#define LBM_ERR_TIMEOUT (-8)    /* a bounded wait inside the step kernel gave up (every wait
+                                   gives up after two seconds of the GPU's global timer); the
+                                   state of that step is invalid (reported by the next
+                                   synchronising call or lbm_check) */
 #define LBM_ERR_INDEX (-9)      /* the bounds-checked step kernel (lbm_set_checked) met a load,
                                    store or copy outside the state buffers and skipped it; the
                                    state is invalid (reported as LBM_ERR_TIMEOUT is) */

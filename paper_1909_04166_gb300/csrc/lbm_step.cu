@@ -42,7 +42,10 @@ namespace cmlbm {
 
 static constexpr unsigned FULL = 0xffffffffu;
 static constexpr int TILE = 18 * 32;               // elements per warp-row tile
-static constexpr unsigned WAIT_LIMIT = 1u << 22;   // bounded mbarrier polling
+static constexpr unsigned WAIT_LIMIT = 1u << 22;   // bounded mbarrier polling (iterations)
+// and in time: a row copy arrives within microseconds, so two seconds of the global timer
+// without it means it never will
+static constexpr unsigned long long WAIT_NS = 2000000000ull;
 
 struct StepLaunch {
     int seg_h;     // rows per segment
@@ -129,11 +132,28 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
         : "memory");
 }
 
-// Warp-collective bounded wait for phase `parity` of barrier `bar`; false on timeout.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Warp-collective bounded wait for phase `parity` of barrier `bar`; false on timeout (after
+// WAIT_NS of the global timer, or WAIT_LIMIT polls should the timer not advance).  The timer is
+// read only once the first poll has failed, every 64 polls, by lane 0 for the warp.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity)
 {
-    for (unsigned it = 0; it < WAIT_LIMIT; ++it)
+    if (__all_sync(FULL, mbar_try_wait(bar, parity))) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1; it < WAIT_LIMIT; ++it) {
         if (__all_sync(FULL, mbar_try_wait(bar, parity))) return true;
+        if ((it & 63) == 0) {
+            int late = 0;
+            if ((threadIdx.x & 31) == 0) late = global_ns() - t0 > WAIT_NS ? 1 : 0;
+            if (__shfl_sync(FULL, late, 0)) return false;
+        }
+    }
     return false;
 }
 
@@ -1307,12 +1327,6 @@ constexpr auto step_kernel_of()
 constexpr unsigned long long NEIGHBOUR_WAIT_NS = 2000000000ull;
 constexpr unsigned NEIGHBOUR_WAIT_ITERS = 1u << 27;
 
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
 {
     unsigned v;
