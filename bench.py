@@ -37,6 +37,7 @@ STORAGE = {"fp32": "FP32 populations", "fp64": "FP64 populations",
 HBM_FALLBACK_GBS = 6800.0
 L2_BYTES = 129e6
 METRIC = "MLUPS (million node updates of both lattices per second)"
+MULTI_MAX_STEPS = 65536     # steps per launch of the multi-step kernel (lbm_step splits longer runs)
 
 
 def workload(name: str):
@@ -84,19 +85,22 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-# DRAM traffic per launch of the step kernel from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), keyed by the hash of the kernel sources it was taken on; scaled by
-# node count to the bench workload.  The figures are steady-state launches (caches not flushed
-# between launches, as in the timed run; mean of three consecutive launches).
+# DRAM traffic per step of the step kernels from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by the hash of the kernel sources they were taken on, the
+# workload, the precision and the launch form ("step": one launch per step, the mean of three
+# consecutive launches; "multi": one launch of the multi-step kernel divided by its steps).
+# Caches are not flushed between launches, as in the timed run; the bench line reports the
+# bytes of one of its launches.
 NCU_TRAFFIC = {
-    # FP32 step on the 2048 x 1024 impact, sources 20753e7a8ad56b8d: read 107.08 MB + write
-    # 149.93 MB per launch
-    ("20753e7a8ad56b8d", "impact", "fp32"): 257_005_312,
-    # FP16-storage step on the same grid and sources: read 47.83 MB + write 92.33 MB per launch
-    ("20753e7a8ad56b8d", "impact", "fp16"): 140_161_536,
+    # multi-step kernel (FP32, the default for runs on the 2048 x 1024 impact), sources
+    # af3e6ee07f38003d: one launch of 32 steps read 3972.53 MB + wrote 4842.83 MB; per step
+    ("af3e6ee07f38003d", "impact", "fp32", "multi"): 275_480_024,
+    # FP16-storage step kernel (graph replays, one launch per step) on the same grid and
+    # sources: read 48.10 MB + write 92.37 MB per launch
+    ("af3e6ee07f38003d", "impact", "fp16", "step"): 140_464_128,
     # batched step of the 512-case ensemble (autotuned: 8 rows per task, 128-thread blocks), same
-    # sources: read 844.90 MB + write 760.66 MB per launch
-    ("20753e7a8ad56b8d", "ensemble", "fp32"): 1_605_556_395,
+    # sources: read 858.07 MB + write 762.30 MB per launch
+    ("af3e6ee07f38003d", "ensemble", "fp32", "step"): 1_620_377_088,
 }
 
 
@@ -213,6 +217,7 @@ def run_ours(args):
     dev = {k: torch.tensor(fl[k], dtype=torch.float64, device="cuda") for k in
            ("phi", "p", "ux", "uy")}
     lbm.lbm_init_fields_device(ctx, *(dev[k].data_ptr() for k in ("phi", "p", "ux", "uy")))
+    path = lbm.lbm_get_step_path(ctx)
     clk = Clocks(local, "warm-up, timed region and e2e leg").__enter__()
     lbm.lbm_step(ctx, args.warmup)
     torch.cuda.synchronize()
@@ -225,13 +230,17 @@ def run_ours(args):
     torch.cuda.synchronize()
     queue_behind_spin(stream)
     ev0.record(stream)
-    lbm.lbm_step(ctx, K)             # K fused-kernel launches (graph replays)
+    lbm.lbm_step(ctx, K)             # one multi-step launch, or K graph-replayed launches
     ev1.record(stream)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     ms_total = ev0.elapsed_time(ev1)
-    ms_launch = ms_total / K         # every launch in the region is the step kernel
+    # every launch in the region is the step kernel: K launches, or ceil(K / 65536) launches of
+    # the multi-step kernel (each of up to 65536 steps)
+    multi = K >= 2 and path == lbm.LBM_PATH_MULTI
+    launches = -(-K // MULTI_MAX_STEPS) if multi else K
+    ms_launch = ms_total / launches
     ms_max = max_over_ranks(ms_total, ws)
     diag = lbm.lbm_diagnostics(ctx)
 
@@ -269,12 +278,19 @@ def run_ours(args):
         return
     bpl = BYTES_PER_LU[args.precision]
     peak, peak_kind = measured_peak()
-    achieved = bpl * N / (ms_launch * 1e-3) / 1e9
+    steps_per_launch = K / launches
+    achieved = bpl * N * steps_per_launch / (ms_launch * 1e-3) / 1e9
     traffic = None
     hsh = kernel_source_hash()
-    key = (hsh, args.workload, args.precision)
-    if key in NCU_TRAFFIC:
-        traffic = NCU_TRAFFIC[key]
+    key = (hsh, args.workload, args.precision, "multi" if multi else "step")
+    if key in NCU_TRAFFIC:   # DRAM bytes per step, for this launch's steps
+        traffic = int(round(NCU_TRAFFIC[key] * steps_per_launch))
+    if multi:
+        kname = "cmlbm::step_kernel_multi" + ("_narrow" if args.precision in ("fp16", "bf16")
+                                              else "")
+    else:
+        kname = ("cmlbm::step_kernel_narrow" if args.precision in ("fp16", "bf16")
+                 else "cmlbm::step_kernel")
     seg, block = None, None
     value = job_mlups(ws, N, K, ms_max)
     line = {
@@ -307,12 +323,15 @@ def run_ours(args):
             "frac": round(achieved / peak, 4), "traffic": traffic,
             "peak_source": f"{peak_kind} HBM copy bandwidth",
             "bytes_per_lu": bpl, "ms_per_launch": round(ms_launch, 5),
-            "kernel": ("cmlbm::step_kernel_narrow" if args.precision in ("fp16", "bf16")
-                       else "cmlbm::step_kernel"), "kernel_hash": hsh,
+            "steps_per_launch": round(steps_per_launch, 3),
+            "kernel": kname, "kernel_hash": hsh,
         },
         "clocks": clk.summary(),
         "e2e": e2e,
-        "gpu_launches": K,
+        "gpu_launches": launches,
+        "step_path": ("one cooperative launch of the multi-step kernel per run (waits only "
+                      "between neighbouring warps)" if multi else
+                      "graph replays of one step-kernel launch per step"),
         "state_check": {"sum_phi": diag["sum_phi"], "max_speed": diag["max_speed"],
                         "nonfinite": diag["nonfinite"]},
     }
@@ -611,7 +630,7 @@ def run_ensemble_line(args):
         "roofline": {"bound": "hbm", "achieved": r["batched_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": round(r["batched_gbs"] / peak, 4),
                      "traffic": NCU_TRAFFIC.get((kernel_source_hash(), "ensemble",
-                                                 args.precision)),
+                                                 args.precision, "step")),
                      "peak_source": f"{peak_kind} HBM copy bandwidth",
                      "kernel": "cmlbm::batch_step_kernel"},
         "clocks": clk.summary(), "ensemble": r, "gpu_launches": args.steps,

@@ -208,24 +208,28 @@ int lbm_init_fields_device(lbm_ctx* ctx, const double* phi, const double* p, con
                            const double* uy);
 
 /* Advance nsteps (>= 0) time steps (the update of Secs. 3 - 5 on every node) on params.stream,
- * asynchronous; launch errors are returned.  A run of two or more steps is issued as replays of
- * CUDA graphs of one launch per step: graphs of 32 launches while 32 or more steps are left,
- * then one graph for the even rest (2 .. 30 launches); the first call that needs a graph builds
- * all of them (every even size up to 32, from either state buffer; a few milliseconds), so
- * later calls of any length launch at once; lbm_set_launch drops them, lbm_set_graphs switches
- * them off.  With lbm_set_persistent(ctx, 1) such a run is instead one launch of the multi-step
- * kernel: every warp keeps its strip of columns and segment of rows from step to step and
- * waits, between steps, only for the warps of the neighbouring strips and segments (a
- * cooperative launch, used when the launch shape of lbm_set_launch fits on the device at once;
- * runs longer than 65536 steps take several launches).  A last odd step is a single launch.
+ * asynchronous; launch errors are returned.  A run of two or more steps is, where the multi-step
+ * kernel is enabled (lbm_set_persistent; by default with LBM_FP32 storage on grids of tall
+ * segments) and the grid's warps fit on the device at once, one launch of that kernel: every warp keeps its strip of columns
+ * and segment of rows from step to step and waits, between steps, only for the warps of the
+ * neighbouring strips and segments (a cooperative launch of one 12-warp block per SM; runs
+ * longer than 65536 steps take several launches).  Otherwise it is issued as replays of CUDA
+ * graphs of one launch per step: graphs of 32 launches while 32 or more steps are left, then
+ * one graph for the even rest (2 .. 30 launches); the first call that needs a graph builds all
+ * of them (every even size up to 32, from either state buffer; a few milliseconds), so later
+ * calls of any length launch at once; lbm_set_launch drops them, lbm_set_graphs switches them
+ * off.  A last odd step is a single launch.  lbm_get_step_path tells which form a run takes.
  * Every form computes the same values, bit for bit. */
 int lbm_step(lbm_ctx* ctx, int32_t nsteps);
 
 /* Enable (default) or disable the graph replays of lbm_step; results are identical. */
 int lbm_set_graphs(lbm_ctx* ctx, int32_t enable);
 
-/* Enable (enable = 1) or disable (0, default) the multi-step kernel of lbm_step; results are
- * identical.  Other values: LBM_ERR_ARG. */
+/* The multi-step kernel of lbm_step: enable = 1 uses it wherever the grid's warps fit on the
+ * device at once, 0 never, 2 (automatic) where they fit and the warp segments are at least 16
+ * rows tall (shorter segments spend more of a step in the waits between steps).  Results are
+ * identical.  Default: 2 with LBM_FP32 storage, 0 with the others (where it measured slower
+ * than graph replays).  Other values: LBM_ERR_ARG. */
 int lbm_set_persistent(lbm_ctx* ctx, int32_t enable);
 
 /* How lbm_step issues a run of two or more steps under the current settings: *path receives
@@ -292,10 +296,10 @@ int lbm_check(lbm_ctx* ctx);
  * waits).  With enable = 2, runs of two or more steps of a context with the multi-step kernel
  * enabled (lbm_set_persistent) go to it as usual, but its waits for the neighbouring warps
  * between steps never succeed: after the first step every warp waits out its bound (two
- * seconds), records LBM_ERR_TIMEOUT and returns, with no copy in flight.  Nothing faults or hangs in either mode; the state of those steps is invalid,
- * lbm_check reports LBM_ERR_TIMEOUT, and re-initialising the state (lbm_init_fields*,
- * lbm_set_populations, lbm_load_state) clears the error.  enable = 0 (default) returns to normal
- * waits; other values: LBM_ERR_ARG. */
+ * seconds), records LBM_ERR_TIMEOUT and returns, with no copy in flight.  Nothing faults or
+ * hangs in either mode; the state of those steps is invalid, lbm_check reports LBM_ERR_TIMEOUT,
+ * and re-initialising the state (lbm_init_fields*, lbm_set_populations, lbm_load_state) clears
+ * the error.  enable = 0 (default) returns to normal waits; other values: LBM_ERR_ARG. */
 int lbm_inject_timeout(lbm_ctx* ctx, int32_t enable);
 
 /* Diagnostics of the current state; see lbm_diag.  r_in < 0 skips dp_laplace.  Synchronises.
@@ -304,7 +308,9 @@ int lbm_diagnostics(lbm_ctx* ctx, double xc, double yc, double r_in, double r_ou
                     lbm_diag* out);
 
 /* Tuning of the step launch: rows per warp segment (>= 1) and threads per block (a multiple of
- * 32, 32..256).  0 keeps the current value.  Results do not depend on these. */
+ * 32, 32..256) of the one-launch-per-step kernels; the multi-step kernel takes the segment rows
+ * and always runs blocks of 12 warps, one per SM.  0 keeps the current value.  Results do not
+ * depend on these. */
 int lbm_set_launch(lbm_ctx* ctx, int32_t seg_rows, int32_t block_threads);
 int lbm_get_launch(lbm_ctx* ctx, int32_t* seg_rows, int32_t* block_threads);
 

@@ -58,6 +58,12 @@ constexpr int kGraphSizes = 16;
 constexpr int kMultiMaxSteps = 1 << 16;
 // Progress words allocated per SM (an SM holds at most 64 resident warps).
 constexpr int kMaxWarpsPerSm = 64;
+// lbm_set_persistent 2 (the default with FP32 storage): the multi-step kernel where it fits and
+// the segments have at least this many rows (measured on one GB300, FP32 drop impact: 18-row
+// segments 51.9 against 54.9 us per step for graph replays; 9-row segments of a 1024 x 1024
+// grid 27.7 against 27.1; 1 - 3-row segments of small grids up to twice as slow).
+constexpr int kMultiAuto = 2;
+constexpr int kMultiAutoMinRows = 16;
 
 template <typename R> const Consts<R>& kref(const lbm_ctx* c);
 template <> const Consts<double>& kref<double>(const lbm_ctx* c) { return c->Kd; }
@@ -115,8 +121,8 @@ cudaError_t configure(lbm_ctx* c)
         cudaError_t e = configure_step<R, S, V>(c->block);
         if (e != cudaSuccess) return e;
         // the multi-step kernel is optional: without it runs go to the graphs
-        c->multi_bps = configure_multi<R, S, V>(c->block) == cudaSuccess
-                           ? multi_blocks_per_sm<R, S, V>(c->block)
+        c->multi_bps = configure_multi<R, S, V>(kMultiBlock) == cudaSuccess
+                           ? multi_blocks_per_sm<R, S, V>(kMultiBlock)
                            : 0;
         cudaGetLastError();
         return cudaSuccess;
@@ -128,12 +134,14 @@ cudaError_t configure(lbm_ctx* c)
 bool multi_fits(const lbm_ctx* c)
 {
     if (!c->use_multi || c->multi_bps <= 0 || c->checked || c->cut_first_wait == 1) return false;
+    // automatic: only with segments tall enough that a step outlasts the waits between steps
+    if (c->use_multi == kMultiAuto && c->seg_h < kMultiAutoMinRows) return false;
     const int strips = with_variant(c->P.precision, c->variant, [&](auto r, auto s, auto v) {
         return step_warp_strips<decltype(r), decltype(s), decltype(v)::value>(c->G.nstrips);
     });
     const long long nseg = (c->G.ny + c->seg_h - 1) / c->seg_h;
     const long long warps = (long long)strips * nseg;
-    const int wpb = c->block / 32;
+    const int wpb = kMultiBlock / 32;
     const long long blocks = (warps + wpb - 1) / wpb;
     return blocks <= (long long)c->nsm * c->multi_bps && warps <= (long long)c->nsm * kMaxWarpsPerSm;
 }
@@ -145,7 +153,7 @@ cudaError_t launch_multi_run(lbm_ctx* c, int nsteps, int sign)
     return with_variant(c->P.precision, c->variant, [&](auto r, auto s, auto v) {
         using R = decltype(r);
         return launch_multi<R, decltype(s), decltype(v)::value>(
-            a, b, c->G, kref<R>(c), c->seg_h, c->block, c->err, sign ? sign : 1, nsteps,
+            a, b, c->G, kref<R>(c), c->seg_h, kMultiBlock, c->err, sign ? sign : 1, nsteps,
             c->prog, c->cut_first_wait == 2 ? 1 : 0, c->st);
     });
 }
@@ -259,7 +267,9 @@ int make_ctx(const lbm_params* params, void* ext, size_t ext_bytes, lbm_ctx** ou
     c->nsm = nsm > 0 ? nsm : 1;
     c->block = 128;
     c->use_graph = 1;
-    c->use_multi = 0;
+    // the multi-step kernel automatically for FP32 storage (measured faster than graph replays
+    // there on grids of tall segments; slower with FP64 and 16-bit storage)
+    c->use_multi = params->precision == LBM_FP32 ? kMultiAuto : 0;
     if (ext) {
         if (ext_bytes < 2 * c->state_bytes || (reinterpret_cast<uintptr_t>(ext) & 15)) {
             delete c;
@@ -613,7 +623,7 @@ int lbm_set_graphs(lbm_ctx* c, int32_t enable)
 
 int lbm_set_persistent(lbm_ctx* c, int32_t enable)
 {
-    if (!c || enable < 0 || enable > 1) return LBM_ERR_ARG;
+    if (!c || enable < 0 || enable > 2) return LBM_ERR_ARG;
     c->use_multi = enable;
     return LBM_OK;
 }

@@ -41,6 +41,10 @@ struct Consts {
     R st_scale[2], st_inv[2];
 };
 
+// Threads per block of the multi-step step kernel (lbm_step.cu, step_kernel_multi): 12 warps,
+// one block per SM.
+constexpr int kMultiBlock = 384;
+
 // D2Q9 weights (the populations of the rest state are w_a times the zeroth moment).
 __host__ __device__ constexpr double d2q9_w(int a)
 {

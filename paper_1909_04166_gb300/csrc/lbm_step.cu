@@ -1429,8 +1429,12 @@ __device__ __forceinline__ void multi_body(S* a, S* b, const Geometry& G, const 
     }
 }
 
+// Launched with one block of 12 warps per SM (kMultiBlock threads, lbm_device.cuh): the warps
+// of an SM then share one block, and the scheduler favours none of them over the others, as it
+// favours the older of several blocks; with several blocks per SM the warps of the youngest
+// block fall behind, and through the waits between neighbours they pace every warp.
 template <typename R, typename S, int V>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kMultiBlock)
 step_kernel_multi(S* a, S* b, Geometry G, Consts<R> K, StepLaunch L, MultiLaunch M)
 {
     multi_body<R, S, V>(a, b, G, K, L, M);
@@ -1438,7 +1442,7 @@ step_kernel_multi(S* a, S* b, Geometry G, Consts<R> K, StepLaunch L, MultiLaunch
 
 // The 16-bit forms, held to the register budget of step_kernel_narrow.
 template <typename R, typename S, int V>
-__global__ void __launch_bounds__(256) __maxnreg__(NarrowRegs<S>::value)
+__global__ void __launch_bounds__(kMultiBlock) __maxnreg__(NarrowRegs<S>::value)
 step_kernel_multi_narrow(S* a, S* b, Geometry G, Consts<R> K, StepLaunch L, MultiLaunch M)
 {
     multi_body<R, S, V>(a, b, G, K, L, M);

@@ -292,8 +292,9 @@ def lbm_set_graphs(ctx, enable: bool) -> None:
     _check(lib().lbm_set_graphs(ctx, int(bool(enable))), "lbm_set_graphs")
 
 
-def lbm_set_persistent(ctx, enable: bool) -> None:
-    _check(lib().lbm_set_persistent(ctx, 1 if enable else 0), "lbm_set_persistent")
+def lbm_set_persistent(ctx, enable) -> None:
+    """True / 1: the multi-step kernel wherever it fits; False / 0: never; 2: automatic."""
+    _check(lib().lbm_set_persistent(ctx, int(enable)), "lbm_set_persistent")
 
 
 LBM_PATH_SINGLE, LBM_PATH_GRAPHS, LBM_PATH_MULTI = 0, 1, 2
