@@ -1,9 +1,11 @@
 """Throughput of the fused cascaded two-phase LB step on GB300.
 
-One bench step = one time step of both D2Q9 lattices over the whole grid (one fused kernel
-launch).  Default workload: drop impact on a thin film at density ratio 1000 on a 2048 x 1024
-grid (the paper's Sec. 6.6 parameters at Re = 100, We = 8000), FP32 populations (the bandwidth
-headline).  Prints one JSON line.
+One bench step = one time step of both D2Q9 lattices over the whole grid; the timed steps are
+one launch of the multi-step kernel, or one fused kernel launch per step where lbm_step takes
+graph replays (the line names the kernel, its launches and the form).  Default workload: drop
+impact on a thin film at density ratio 1000 on a 2048 x 1024 grid (the paper's Sec. 6.6
+parameters at Re = 100, We = 8000), FP32 populations (the bandwidth headline).  Prints one JSON
+line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload impact|rt|marangoni|laplace] [--precision fp32|fp64]
