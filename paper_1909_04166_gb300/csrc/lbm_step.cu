@@ -1361,9 +1361,10 @@ __device__ __forceinline__ bool wait_neighbours(const unsigned* prog, int seg, i
     for (unsigned it = 0; it < NEIGHBOUR_WAIT_ITERS; ++it) {
         const unsigned v = mine ? ld_acquire(p) : target;
         if (__all_sync(FULL, (int)(v - target) >= 0)) {
+            // the warp barrier orders every lane's later accesses after the acquires of lanes
+            // 0 .. 24; the next copies go through the async proxy, so a proxy fence orders them
+            // after the acquired stores as well
             __syncwarp();
-            __threadfence();
-            // the next copies go through the async proxy: order them after the acquired stores
             asm volatile("fence.proxy.async.global;" ::: "memory");
             return true;
         }
@@ -1382,11 +1383,11 @@ __device__ __forceinline__ bool wait_neighbours(const unsigned* prog, int seg, i
     return false;
 }
 
-// Publish the end of step s of this warp: every lane's stores are made visible at device scope,
-// then lane 0 releases the progress word.
+// Publish the end of step s of this warp: after the warp barrier, lane 0's release store of the
+// progress word orders every lane's stores of the step before it (release is cumulative over
+// what the barrier made lane 0 observe), as a grid barrier's single releasing thread does.
 __device__ __forceinline__ void publish_step(unsigned* word, unsigned v, int lane)
 {
-    __threadfence();
     __syncwarp();
     if (lane == 0) st_release(word, v);
 }
