@@ -95,14 +95,14 @@ def kernel_source_hash() -> str:
 # bytes of one of its launches.
 NCU_TRAFFIC = {
     # multi-step kernel (FP32, the default for runs on the 2048 x 1024 impact), sources
-    # af3e6ee07f38003d: one launch of 32 steps read 3972.53 MB + wrote 4842.83 MB; per step
-    ("af3e6ee07f38003d", "impact", "fp32", "multi"): 275_480_024,
+    # b5616b88d86f514e: one launch of 32 steps read 3806.02 MB + wrote 4842.92 MB; per step
+    ("b5616b88d86f514e", "impact", "fp32", "multi"): 270_279_320,
     # FP16-storage step kernel (graph replays, one launch per step) on the same grid and
-    # sources: read 48.10 MB + write 92.37 MB per launch
-    ("af3e6ee07f38003d", "impact", "fp16", "step"): 140_464_128,
+    # sources: read 48.08 MB + write 92.28 MB per launch
+    ("b5616b88d86f514e", "impact", "fp16", "step"): 140_359_168,
     # batched step of the 512-case ensemble (autotuned: 8 rows per task, 128-thread blocks), same
-    # sources: read 858.07 MB + write 762.30 MB per launch
-    ("af3e6ee07f38003d", "ensemble", "fp32", "step"): 1_620_377_088,
+    # sources: read 843.78 MB + write 760.40 MB per launch
+    ("b5616b88d86f514e", "ensemble", "fp32", "step"): 1_604_177_920,
 }
 
 

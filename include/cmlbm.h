@@ -226,7 +226,7 @@ int lbm_step(lbm_ctx* ctx, int32_t nsteps);
 int lbm_set_graphs(lbm_ctx* ctx, int32_t enable);
 
 /* The multi-step kernel of lbm_step: enable = 1 uses it wherever the grid's warps fit on the
- * device at once, 0 never, 2 (automatic) where they fit and the warp segments are at least 16
+ * device at once, 0 never, 2 (automatic) where they fit and the warp segments are at least 3
  * rows tall (shorter segments spend more of a step in the waits between steps).  Results are
  * identical.  Default: 2 with LBM_FP32 storage, 0 with the others (where it measured slower
  * than graph replays).  Other values: LBM_ERR_ARG. */

@@ -59,11 +59,12 @@ constexpr int kMultiMaxSteps = 1 << 16;
 // Progress words allocated per SM (an SM holds at most 64 resident warps).
 constexpr int kMaxWarpsPerSm = 64;
 // lbm_set_persistent 2 (the default with FP32 storage): the multi-step kernel where it fits and
-// the segments have at least this many rows (measured on one GB300, FP32 drop impact: 18-row
-// segments 51.9 against 54.9 us per step for graph replays; 9-row segments of a 1024 x 1024
-// grid 27.7 against 27.1; 1 - 3-row segments of small grids up to twice as slow).
+// the segments have at least this many rows (measured on one GB300, FP32, us per step against
+// graph replays: drop impact 2048 x 1024, 18-row segments, 48.7 against 54.4; 1024 x 1024,
+// 9 rows, 24.5 against 26.9; Rayleigh-Taylor 256 x 1024, 3 rows, 11.0 against 11.6; Marangoni
+// 512 x 256, 2 rows, 8.9 against 7.1; Laplace 64 x 64, 1 row, 5.9 against 3.7).
 constexpr int kMultiAuto = 2;
-constexpr int kMultiAutoMinRows = 16;
+constexpr int kMultiAutoMinRows = 3;
 
 template <typename R> const Consts<R>& kref(const lbm_ctx* c);
 template <> const Consts<double>& kref<double>(const lbm_ctx* c) { return c->Kd; }

@@ -116,7 +116,7 @@ def test_multistep_at_the_benchmark_size(precision):
 
 def test_default_paths():
     """FP32 storage takes the multi-step kernel by default where one wave of warps of segments
-    at least 16 rows tall covers the grid; grids of shorter segments or several waves, and the
+    at least 3 rows tall covers the grid; grids of shorter segments or several waves, and the
     other storage modes, take graph replays; 1 forces the multi-step kernel where it fits."""
     with lbm.Simulation(W.random_drop(96, 64, seed=2), precision="fp32") as sim:
         assert lbm.lbm_get_step_path(sim.ctx) == lbm.LBM_PATH_GRAPHS
@@ -127,6 +127,8 @@ def test_default_paths():
         with pytest.raises(lbm.LbmError):
             lbm.lbm_set_persistent(sim.ctx, 3)
     for case, prec, path in ((W.impact(), "fp32", lbm.LBM_PATH_MULTI),
+                             (W.rt(), "fp32", lbm.LBM_PATH_MULTI),
+                             (W.marangoni(), "fp32", lbm.LBM_PATH_GRAPHS),
                              (W.random_drop(96, 64, seed=2), "fp32", lbm.LBM_PATH_GRAPHS),
                              (W.impact(ny=4096), "fp32", lbm.LBM_PATH_GRAPHS),
                              (W.impact(), "fp16", lbm.LBM_PATH_GRAPHS),
