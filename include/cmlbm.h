@@ -209,8 +209,9 @@ int lbm_init_fields_device(lbm_ctx* ctx, const double* phi, const double* p, con
 
 /* Advance nsteps (>= 0) time steps (the update of Secs. 3 - 5 on every node) on params.stream,
  * asynchronous; launch errors are returned.  A run of two or more steps is, where the multi-step
- * kernel is enabled (lbm_set_persistent; by default with LBM_FP32 storage on grids of tall
- * segments) and the grid's warps fit on the device at once, one launch of that kernel: every warp keeps its strip of columns
+ * kernel is enabled (lbm_set_persistent; by default with LBM_FP32 storage where the warp
+ * segments have at least 3 rows) and the grid's warps fit on the device at once, one launch of
+ * that kernel: every warp keeps its strip of columns
  * and segment of rows from step to step and waits, between steps, only for the warps of the
  * neighbouring strips and segments (a cooperative launch of one 12-warp block per SM; runs
  * longer than 65536 steps take several launches).  Otherwise it is issued as replays of CUDA
