@@ -415,6 +415,17 @@ int lbm_batch_get_populations(lbm_batch* b, int32_t c, double* g, double* f);
 int lbm_batch_set_launch(lbm_batch* b, int32_t seg_rows, int32_t block_threads);
 int lbm_batch_get_launch(const lbm_batch* b, int32_t* seg_rows, int32_t* block_threads);
 
+/* The batched multi-step kernel: with enable = 1, lbm_batch_step issues a run of two or more
+ * steps as one cooperative launch (runs longer than 65536 steps take several) of one 12-warp
+ * block per SM, whose warps share the batch's warp tasks out once, balanced by nodes, and take
+ * their tasks in a fixed order every step; a task waits, before its step, only for the tasks of
+ * the same case within reach of its reads and writes.  enable = 0 (default): graph replays of
+ * one launch per step.  The results are the same, bit for bit.  Other values: LBM_ERR_ARG.
+ * lbm_batch_get_step_path: LBM_PATH_MULTI where the multi-step kernel takes the runs (enabled,
+ * and its warps fit on the device at once), else LBM_PATH_GRAPHS. */
+int lbm_batch_set_persistent(lbm_batch* b, int32_t enable);
+int lbm_batch_get_step_path(const lbm_batch* b, int32_t* path);
+
 /* Autotuner: times trial_steps (>= 1) steps of the live batch for each candidate launch shape
  * (rows per task 8..64, blocks of 64 or 128 threads), keeps the fastest and restores the state
  * it started from (a temporary device copy).  Synchronises. */

@@ -83,6 +83,13 @@ struct lbm_batch {
     int seg_h, block;
     cudaGraphExec_t graph[2][16];  // 2 (k + 1) steps from parity 0 / 1
     int last_cuda;
+    // the batched multi-step kernel (lbm_batch_set_persistent): the warps' task lists and one
+    // progress word per task
+    int nsm;
+    int use_multi, multi_bps, nwarps_multi;
+    int* dorder;
+    int* dwbeg;
+    unsigned* dprog;
 };
 
 namespace {
@@ -103,11 +110,63 @@ void drop_batch_graphs(lbm_batch* b)
             }
 }
 
+// Task lists of the batched multi-step kernel: the tasks go to the warps of one 12-warp block
+// per SM by the longest-first rule on their nodes (each task also reloads the two rows around
+// its segment), and every warp takes its tasks in the order of their indices.
+cudaError_t build_assignment(lbm_batch* b, const std::vector<int2>& tasks,
+                             const std::vector<int>& seg_rows, const std::vector<int>& width)
+{
+    const int ntasks = (int)tasks.size();
+    const int nwarps = std::max(1, std::min(ntasks, b->nsm * (kMultiBlock / 32)));
+    std::vector<long long> cost(ntasks);
+    for (int i = 0; i < ntasks; ++i) cost[i] = (long long)(seg_rows[i] + 2) * width[i];
+    std::vector<int> idx(ntasks);
+    for (int i = 0; i < ntasks; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    std::vector<std::pair<long long, int>> heap;   // (load, warp), smallest load on top
+    for (int w = 0; w < nwarps; ++w) heap.push_back({0, w});
+    auto later = [](const std::pair<long long, int>& a, const std::pair<long long, int>& c) {
+        return a.first != c.first ? a.first > c.first : a.second > c.second;
+    };
+    std::make_heap(heap.begin(), heap.end(), later);
+    std::vector<std::vector<int>> lists(nwarps);
+    for (int i : idx) {
+        std::pop_heap(heap.begin(), heap.end(), later);
+        heap.back().first += cost[i];
+        lists[heap.back().second].push_back(i);
+        std::push_heap(heap.begin(), heap.end(), later);
+    }
+    std::vector<int> order, wbeg(nwarps + 1, 0);
+    order.reserve(ntasks);
+    for (int w = 0; w < nwarps; ++w) {
+        std::sort(lists[w].begin(), lists[w].end());
+        wbeg[w] = (int)order.size();
+        order.insert(order.end(), lists[w].begin(), lists[w].end());
+    }
+    wbeg[nwarps] = (int)order.size();
+    if (b->dorder) cudaFree(b->dorder);
+    if (b->dwbeg) cudaFree(b->dwbeg);
+    if (b->dprog) cudaFree(b->dprog);
+    b->dorder = nullptr;
+    b->dwbeg = nullptr;
+    b->dprog = nullptr;
+    cudaError_t e = cudaMalloc(&b->dorder, ntasks * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dwbeg, (nwarps + 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dprog, ntasks * sizeof(unsigned));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->dorder, order.data(), ntasks * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->dwbeg, wbeg.data(), (nwarps + 1) * sizeof(int), cudaMemcpyHostToDevice);
+    b->nwarps_multi = e == cudaSuccess ? nwarps : 0;
+    return e;
+}
+
 // (Re)build the per-case descriptors and the flattened warp-task list for segment height h.
 int build_tasks(lbm_batch* b, int h)
 {
     const int n = (int)b->cases.size();
     std::vector<int2> tasks;
+    std::vector<int> seg_rows, width;   // rows and columns of each task
     std::vector<BatchCase<double>> cd(b->precision == LBM_FP64 ? n : 0);
     std::vector<BatchCase<float>> cf(b->precision != LBM_FP64 ? n : 0);
     for (int c = 0; c < n; ++c) {
@@ -117,7 +176,13 @@ int build_tasks(lbm_batch* b, int h)
             return step_warp_strips<decltype(r), decltype(s), 0>(hc.G.nstrips);
         });
         const int nw = wstrips * nseg;
-        for (int k = 0; k < nw; ++k) tasks.push_back(make_int2(c, k));
+        const int cols = hc.G.nstrips == wstrips ? 32 : 64;   // columns per warp strip
+        for (int k = 0; k < nw; ++k) {
+            tasks.push_back(make_int2(c, k));
+            const int strip = k % wstrips, seg = k / wstrips;
+            seg_rows.push_back(std::min(h, hc.G.ny - seg * h));
+            width.push_back(std::min(cols, hc.G.nx - strip * cols));
+        }
         if (b->precision == LBM_FP64)
             cd[c] = BatchCase<double>{hc.G, h, nseg, hc.off0, hc.off1, hc.Kd};
         else
@@ -140,6 +205,7 @@ int build_tasks(lbm_batch* b, int h)
             e = cudaMemcpy(b->dcases, cf.data(), n * sizeof(BatchCase<float>),
                            cudaMemcpyHostToDevice);
     }
+    if (e == cudaSuccess) e = build_assignment(b, tasks, seg_rows, width);
     if (e != cudaSuccess) return fail_cuda(b, e);
     b->ntasks = (int)tasks.size();
     b->seg_h = h;
@@ -160,7 +226,36 @@ cudaError_t with_batch_kernel(const lbm_batch* b, F&& f)
 cudaError_t configure(lbm_batch* b)
 {
     return with_batch_kernel(b, [&](auto r, auto s, auto v) {
-        return configure_batch<decltype(r), decltype(s), decltype(v)::value>(b->block);
+        using R = decltype(r);
+        using S = decltype(s);
+        constexpr int V = decltype(v)::value;
+        cudaError_t e = configure_batch<R, S, V>(b->block);
+        if (e != cudaSuccess) return e;
+        // the multi-step kernel is optional: without it runs go to the graphs
+        b->multi_bps = configure_batch_multi<R, S, V>() == cudaSuccess
+                           ? batch_multi_blocks_per_sm<R, S, V>()
+                           : 0;
+        cudaGetLastError();
+        return cudaSuccess;
+    });
+}
+
+// The batched multi-step kernel takes runs of this batch: enabled, and its warps resident at
+// once.
+bool multi_fits(const lbm_batch* b)
+{
+    if (!b->use_multi || b->multi_bps <= 0 || b->nwarps_multi <= 0) return false;
+    const int wpb = kMultiBlock / 32;
+    return (b->nwarps_multi + wpb - 1) / wpb <= b->nsm * b->multi_bps;
+}
+
+cudaError_t launch_multi_run(lbm_batch* b, int nsteps)
+{
+    return with_batch_kernel(b, [&](auto r, auto s, auto v) {
+        using R = decltype(r);
+        return launch_batch_multi<R, decltype(s), decltype(v)::value>(
+            b->base, static_cast<BatchCase<R>*>(b->dcases), b->dtasks, b->dorder, b->dwbeg,
+            b->dprog, b->ntasks, b->nwarps_multi, nsteps, b->cur, 0, b->err, b->st);
     });
 }
 
@@ -246,6 +341,9 @@ int lbm_batch_create_ex(const lbm_params* params, int32_t ncases, int32_t layout
     b->elem = elem_bytes(b->precision);
     b->st = static_cast<cudaStream_t>(params[0].stream);
     b->block = 128;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+    b->nsm = nsm > 0 ? nsm : 1;
     long long off = 0;
     for (int c = 0; c < ncases; ++c) {
         HostCase hc;
@@ -331,6 +429,13 @@ int lbm_batch_step(lbm_batch* b, int32_t nsteps)
     if (!b || nsteps < 0) return LBM_ERR_ARG;
     cudaSetDevice(b->device);
     int32_t k = 0;
+    while (nsteps - k >= 2 && multi_fits(b)) {   // one multi-step launch per 65536 steps
+        const int chunk = std::min(nsteps - k, 1 << 16);
+        cudaError_t e = launch_multi_run(b, chunk);
+        if (e != cudaSuccess) return fail_cuda(b, e);
+        k += chunk;
+        b->cur ^= chunk & 1;
+    }
     while (nsteps - k >= 2) {
         const int chunk = std::min((nsteps - k) & ~1, 2 * kBatchGraphSizes);
         cudaError_t e = ensure_graphs(b);
@@ -421,6 +526,20 @@ int lbm_batch_set_launch(lbm_batch* b, int32_t seg_rows, int32_t block_threads)
         if (e != cudaSuccess) return fail_cuda(b, e);
     }
     return seg_rows ? build_tasks(b, seg_rows) : LBM_OK;
+}
+
+int lbm_batch_set_persistent(lbm_batch* b, int32_t enable)
+{
+    if (!b || enable < 0 || enable > 1) return LBM_ERR_ARG;
+    b->use_multi = enable;
+    return LBM_OK;
+}
+
+int lbm_batch_get_step_path(const lbm_batch* b, int32_t* path)
+{
+    if (!b || !path) return LBM_ERR_ARG;
+    *path = multi_fits(b) ? LBM_PATH_MULTI : LBM_PATH_GRAPHS;
+    return LBM_OK;
 }
 
 int lbm_batch_get_launch(const lbm_batch* b, int32_t* seg_rows, int32_t* block_threads)
@@ -522,6 +641,9 @@ void lbm_batch_destroy(lbm_batch* b)
     if (b->dtasks) cudaFree(b->dtasks);
     if (b->err) cudaFree(b->err);
     if (b->scratch) cudaFree(b->scratch);
+    if (b->dorder) cudaFree(b->dorder);
+    if (b->dwbeg) cudaFree(b->dwbeg);
+    if (b->dprog) cudaFree(b->dprog);
     delete b;
 }
 

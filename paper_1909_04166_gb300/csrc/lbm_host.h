@@ -60,6 +60,17 @@ cudaError_t launch_unpack(const double*, void*, const Geometry&, const Consts<R>
 // 16-bit storage modes 0 only).
 template <typename R, typename S, int V>
 cudaError_t configure_batch(int block);
+// Several batched steps in one cooperative launch (lbm_step.cu, batch_multi_body): the tasks
+// order[wbeg[w] .. wbeg[w + 1]) go to warp w, one progress word per task.
+template <typename R, typename S, int V>
+cudaError_t configure_batch_multi();
+template <typename R, typename S, int V>
+int batch_multi_blocks_per_sm();
+template <typename R, typename S, int V>
+cudaError_t launch_batch_multi(void* base, const BatchCase<R>*, const int2* tasks,
+                               const int* order, const int* wbeg, unsigned* prog, int ntasks,
+                               int nwarps, int nsteps, int parity0, int far_wait, int* err,
+                               cudaStream_t);
 template <typename R, typename S, int V>
 cudaError_t launch_batch_step(void*, const BatchCase<R>*, const int2*, int, int, int, int*,
                               cudaStream_t);

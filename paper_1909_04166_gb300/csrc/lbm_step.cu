@@ -1509,6 +1509,93 @@ constexpr auto batch_kernel_of()
 }
 
 // ---------------------------------------------------------------------------------------------
+// Several time steps of a batch in one launch.  The warps (one 12-warp block per SM, all
+// resident: a cooperative launch) share the batch's tasks out once, balanced by nodes; every
+// step, a warp takes its tasks in a fixed order, and before a task's step it waits only for the
+// tasks of the same case within reach of that task's reads and writes (cases never wait for one
+// another), through one progress word per task, as the single-grid multi-step kernel does per
+// warp.  A step's waits are for work of the previous step only, so with every warp resident the
+// waits always end; each is bounded all the same.
+// ---------------------------------------------------------------------------------------------
+struct BatchMulti {
+    const int* order;   // task indices in the order the warps take them
+    const int* wbeg;    // warp w takes order[wbeg[w] .. wbeg[w + 1])
+    unsigned* prog;     // one progress word per task (tasks of a case are consecutive), zero at
+                        // launch
+    int nwarps, nsteps, parity0;
+    int far_wait;       // test hook: the waits for neighbouring tasks never succeed
+};
+
+template <typename R, typename S, int V>
+__device__ __forceinline__ void batch_multi_body(S* base, const BatchCase<R>* __restrict__ cases,
+                                                 const int2* __restrict__ tasks,
+                                                 const BatchMulti& M, int* err)
+{
+    static_assert((V & kVarShear) == 0, "batches take the coupled lattices");
+    const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= M.nwarps) return;                    // warp-uniform
+    constexpr int NT = tiles_per_warp<R, S, V>();
+    const int j0 = M.wbeg[warp], j1 = M.wbeg[warp + 1];
+    for (int s = 0; s < M.nsteps; ++s) {
+        const int parity = M.parity0 ^ (s & 1);
+        for (int j = j0; j < j1; ++j) {
+            const int id = M.order[j];
+            const int2 t = tasks[id];                // (case, local index seg * wstrips + strip)
+            const BatchCase<R>& c = cases[t.x];
+            const Geometry G = c.G;
+            const int wstrips = (G.nstrips + NT - 1) / NT;
+            const int strip = t.y % wstrips;
+            const int seg = t.y / wstrips;
+            if (s > 0) {
+                // reach 2 where the case's last strip or segment is one node wide
+                const int last_w = G.nx - (wstrips - 1) * 32 * NT;
+                const int last_h = G.ny - (c.nseg - 1) * c.seg_h;
+                const int rx = last_w >= 2 || wstrips == 1 ? 1 : 2;
+                const int ry = (c.seg_h >= 2 && last_h >= 2) || c.nseg == 1 ? 1 : 2;
+                if (!wait_neighbours(M.prog + (id - t.y), seg, strip, c.nseg, wstrips, rx, ry,
+                                     (unsigned)s, err, lane, M.far_wait != 0))
+                    return;
+            }
+            const S* src = base + (parity ? c.off1 : c.off0);
+            S* dst = base + (parity ? c.off0 : c.off1);
+            bool ok;
+            if constexpr (NT == 2)
+                ok = march2<S, V, false, true>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1,
+                                               parity);
+            else
+                ok = march<R, S, V, false, true>(src, dst, G, c.K, strip, seg, c.seg_h, err, 1,
+                                                 parity);
+            if (!ok) return;
+            publish_step(M.prog + id, (unsigned)(s + 1), lane);
+        }
+    }
+}
+
+template <typename R, typename S, int V>
+__global__ void __launch_bounds__(kMultiBlock)
+batch_multi_kernel(S* base, const BatchCase<R>* __restrict__ cases,
+                   const int2* __restrict__ tasks, BatchMulti M, int* err)
+{
+    batch_multi_body<R, S, V>(base, cases, tasks, M, err);
+}
+
+template <typename R, typename S, int V>
+__global__ void __launch_bounds__(kMultiBlock) __maxnreg__(NarrowRegs<S>::value)
+batch_multi_kernel_narrow(S* base, const BatchCase<R>* __restrict__ cases,
+                          const int2* __restrict__ tasks, BatchMulti M, int* err)
+{
+    batch_multi_body<R, S, V>(base, cases, tasks, M, err);
+}
+
+template <typename R, typename S, int V>
+constexpr auto batch_multi_kernel_of()
+{
+    if constexpr (Narrow<S>::value) return batch_multi_kernel_narrow<R, S, V>;
+    else return batch_multi_kernel<R, S, V>;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Initialisation, field extraction, packing (one thread per node; not on the hot path)
 // ---------------------------------------------------------------------------------------------
 // Element index of population plane p (0..17) of node (x, y) in a state of storage type S, and
@@ -1873,6 +1960,50 @@ cudaError_t launch_batch_step(void* base, const BatchCase<R>* cases, const int2*
     return cudaGetLastError();
 }
 
+// The batched multi-step kernel: configuration, residency and launch (cooperative; the host
+// calls it only when its warps fit on the device at once).
+template <typename R, typename S, int V>
+cudaError_t configure_batch_multi()
+{
+    cudaError_t e = cudaFuncSetAttribute(batch_multi_kernel_of<R, S, V>(),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)step_smem_bytes<R, S, V>(kMultiBlock));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(batch_multi_kernel_of<R, S, V>(),
+                                cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+
+template <typename R, typename S, int V>
+int batch_multi_blocks_per_sm()
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_multi_kernel_of<R, S, V>(),
+                                                      kMultiBlock,
+                                                      step_smem_bytes<R, S, V>(kMultiBlock)) !=
+        cudaSuccess)
+        return 0;
+    return nb;
+}
+
+template <typename R, typename S, int V>
+cudaError_t launch_batch_multi(void* base, const BatchCase<R>* cases, const int2* tasks,
+                               const int* order, const int* wbeg, unsigned* prog, int ntasks,
+                               int nwarps, int nsteps, int parity0, int far_wait, int* err,
+                               cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(prog, 0, (size_t)ntasks * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    BatchMulti M = {order, wbeg, prog, nwarps, nsteps, parity0, far_wait};
+    S* b = static_cast<S*>(base);
+    const int wpb = kMultiBlock / 32;
+    const unsigned grid = (unsigned)((nwarps + wpb - 1) / wpb);
+    void* args[] = {(void*)&b, (void*)&cases, (void*)&tasks, (void*)&M, (void*)&err};
+    return cudaLaunchCooperativeKernel((const void*)batch_multi_kernel_of<R, S, V>(), dim3(grid),
+                                       dim3(kMultiBlock), args,
+                                       step_smem_bytes<R, S, V>(kMultiBlock), st);
+}
+
 // A graph of `chunk` consecutive batched steps starting from buffer parity `parity0`.
 template <typename R, typename S, int V>
 cudaError_t build_batch_graph(void* base, const BatchCase<R>* cases, const int2* tasks,
@@ -1976,6 +2107,11 @@ cudaError_t launch_unpack(const double* in, void* state, const Geometry& G, cons
                                              cudaStream_t);
 
 #define CMLBM_INSTANTIATE_BATCH(R, S, V)                                                          \
+    template cudaError_t configure_batch_multi<R, S, V>();                                      \
+    template int batch_multi_blocks_per_sm<R, S, V>();                                          \
+    template cudaError_t launch_batch_multi<R, S, V>(void*, const BatchCase<R>*, const int2*,   \
+                                                     const int*, const int*, unsigned*, int,    \
+                                                     int, int, int, int, int*, cudaStream_t);   \
     template cudaError_t configure_batch<R, S, V>(int);                                         \
     template cudaError_t build_batch_graph<R, S, V>(void*, const BatchCase<R>*, const int2*,    \
                                                     int, int, int, int*, int,                   \

@@ -56,7 +56,8 @@ EXPORTS = [
     "lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_get_fields",
     "lbm_batch_get_populations", "lbm_batch_set_launch", "lbm_batch_get_launch",
     "lbm_batch_tune", "lbm_batch_nodes", "lbm_batch_check", "lbm_batch_destroy",
-    "lbm_batch_create_ex", "lbm_batch_case_transposed",
+    "lbm_batch_create_ex", "lbm_batch_case_transposed", "lbm_batch_set_persistent",
+    "lbm_batch_get_step_path",
 ]
 
 
@@ -155,6 +156,8 @@ def lib(build_if_missing: bool = True):
     L.lbm_batch_get_populations.argtypes = [vp, i32, dp, dp]
     L.lbm_batch_set_launch.argtypes = [vp, i32, i32]
     L.lbm_batch_get_launch.argtypes = [vp, P(i32), P(i32)]
+    L.lbm_batch_set_persistent.argtypes = [vp, i32]
+    L.lbm_batch_get_step_path.argtypes = [vp, P(i32)]
     L.lbm_batch_tune.argtypes = [vp, i32, P(i32), P(i32)]
     L.lbm_batch_nodes.argtypes = [vp]
     L.lbm_batch_nodes.restype = i64
@@ -404,6 +407,16 @@ def lbm_batch_get_launch(b):
     a, c = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().lbm_batch_get_launch(b, ctypes.byref(a), ctypes.byref(c)), "lbm_batch_get_launch")
     return int(a.value), int(c.value)
+
+
+def lbm_batch_set_persistent(b, enable) -> None:
+    _check(lib().lbm_batch_set_persistent(b, int(enable)), "lbm_batch_set_persistent")
+
+
+def lbm_batch_get_step_path(b) -> int:
+    v = ctypes.c_int32()
+    _check(lib().lbm_batch_get_step_path(b, ctypes.byref(v)), "lbm_batch_get_step_path")
+    return int(v.value)
 
 
 def lbm_batch_tune(b, trial_steps: int = 8):

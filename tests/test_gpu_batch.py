@@ -209,3 +209,62 @@ def test_transposed_case_fields_with_some_outputs_omitted():
             p, uy = np.empty(shape), np.empty(shape)
             lbm.lbm_batch_get_fields(b.b, i, None, p, None, uy, None)
             assert np.array_equal(p, full["p"]) and np.array_equal(uy, full["uy"])
+
+
+def _batch_states(cases, prec, persistent, runs, layout=lbm.LBM_BATCH_FEWEST_COLUMNS,
+                  seg_rows=0):
+    with lbm.Batch(cases, precision=prec, layout=layout) as b:
+        if seg_rows:
+            lbm.lbm_batch_set_launch(b.b, seg_rows, 0)
+        lbm.lbm_batch_set_persistent(b.b, persistent)
+        assert lbm.lbm_batch_get_step_path(b.b) == (lbm.LBM_PATH_MULTI if persistent
+                                                    else lbm.LBM_PATH_GRAPHS)
+        b.init_all()
+        for n in runs:
+            b.step(n)
+        lbm.lbm_batch_check(b.b)
+        return [b.populations(i) for i in range(len(cases))]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("layout", [lbm.LBM_BATCH_AS_GIVEN, lbm.LBM_BATCH_FEWEST_COLUMNS])
+def test_batch_multistep_matches_graph_replays(prec, layout):
+    """The batched multi-step kernel (one cooperative launch per run, each task waiting only for
+    the tasks of its own case within reach) gives every case the same state, bit for bit, as one
+    launch per step; runs of odd and even lengths."""
+    cases = mixed_cases()
+    runs = (7, 2, 1, 12)
+    a = _batch_states(cases, prec, 1, runs, layout)
+    b = _batch_states(cases, prec, 0, runs, layout)
+    for i in range(len(cases)):
+        assert np.array_equal(a[i][0], b[i][0]) and np.array_equal(a[i][1], b[i][1]), i
+
+
+@pytest.mark.parametrize("seg_rows", [1, 2, 5, 64])
+def test_batch_multistep_with_any_task_height(seg_rows):
+    """Tasks of one row (every task waits for two segments either side), two, five, and whole
+    cases; FP32."""
+    cases = mixed_cases()
+    a = _batch_states(cases, "fp32", 1, (9, 4), seg_rows=seg_rows)
+    b = _batch_states(cases, "fp32", 0, (9, 4), seg_rows=seg_rows)
+    for i in range(len(cases)):
+        assert np.array_equal(a[i][0], b[i][0]) and np.array_equal(a[i][1], b[i][1]), i
+
+
+@pytest.mark.parametrize("collision,sigma_model", [(1, 0), (0, 1)])
+def test_batch_multistep_step_variants(collision, sigma_model):
+    cases = [W.random_drop(nx, ny, seed=nx + ny, wall_y=1, rho_ratio=10.0, gravity=1e-6,
+                           collision=collision, sigma_model=sigma_model, beta=0.4, psi0=0.2,
+                           gradpsi_x=1e-3) for nx, ny in ((40, 33), (97, 64), (65, 20))]
+    a = _batch_states(cases, "fp32", 1, (6, 3))
+    b = _batch_states(cases, "fp32", 0, (6, 3))
+    for i in range(len(cases)):
+        assert np.array_equal(a[i][0], b[i][0]) and np.array_equal(a[i][1], b[i][1]), i
+
+
+def test_batch_persistent_rejects_bad_values():
+    with lbm.Batch(mixed_cases()[:2]) as b:
+        for bad in (2, -1):
+            with pytest.raises(lbm.LbmError) as e:
+                lbm.lbm_batch_set_persistent(b.b, bad)
+            assert e.value.status == lbm.LBM_ERR_ARG
