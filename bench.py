@@ -95,14 +95,14 @@ def kernel_source_hash() -> str:
 # bytes of one of its launches.
 NCU_TRAFFIC = {
     # multi-step kernel (FP32, the default for runs on the 2048 x 1024 impact), sources
-    # b5616b88d86f514e: one launch of 32 steps read 3806.02 MB + wrote 4842.92 MB; per step
-    ("b5616b88d86f514e", "impact", "fp32", "multi"): 270_279_320,
+    # 52b32e0d7565347e: one launch of 32 steps read 3711.62 MB + wrote 4843.53 MB; per step
+    ("52b32e0d7565347e", "impact", "fp32", "multi"): 267_348_568,
     # FP16-storage step kernel (graph replays, one launch per step) on the same grid and
-    # sources: read 48.08 MB + write 92.28 MB per launch
-    ("b5616b88d86f514e", "impact", "fp16", "step"): 140_359_168,
+    # sources: read 48.05 MB + write 92.33 MB per launch
+    ("52b32e0d7565347e", "impact", "fp16", "step"): 140_380_757,
     # batched step of the 512-case ensemble (autotuned: 8 rows per task, 128-thread blocks), same
-    # sources: read 843.78 MB + write 760.40 MB per launch
-    ("b5616b88d86f514e", "ensemble", "fp32", "step"): 1_604_177_920,
+    # sources: read 839.67 MB + write 760.12 MB per launch
+    ("52b32e0d7565347e", "ensemble", "fp32", "step"): 1_599_791_019,
 }
 
 
