@@ -59,7 +59,8 @@
  * moving at the stream's speed; the -grad p* part advects p, so a pressure wave in a uniform
  * stream follows the linear modes of the paper's macroscopic equations.  Not separable by any
  * test: p* in place of the corrected p inside that gradient (R7); the two differ by
- * F_p . u / 2, second order in the flow.
+ * F_p . u / 2, second order in the flow.  That one reading is parity unpinned: the GPU path
+ * takes it too and matches this file element by element, but no test would tell it from p.
  *
  * Layout: a population field is 9 planes [alpha][y][x], plane size nx*ny, row-major in x.
  * Node coordinates are (x, y) = (i, j), i in [0, nx), j in [0, ny).
