@@ -308,18 +308,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32",
         "data": "synthetic (seeded initial fields of the paper's setup; no dataset)",
-        "config": {
-            "workload": f"{args.workload} {case['nx']}x{case['ny']} {args.precision} "
-                        f"populations",
-            "storage": STORAGE[args.precision],
-            **describe(case),
-            "nodes": N,
-            "l2": f"inputs larger than L2 (no flush): state {N * bpl / 1e6:.0f} MB "
-                  f"vs {L2_BYTES / 1e6:.0f} MB L2",
-            "timed_region": "the K steps, queued behind a device spin issued after the "
-                            "synchronize (host submission latency outside the region)",
-            "parallelism": f"replicas x{ws}",
-        },
+        "config": line_config(args, case, ws),
         "roofline": {
             "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -578,6 +567,22 @@ def cpu_baseline(case, seconds):
                       f"grid ({nodes} node updates, {dt:.1f} s)"}
 
 
+def line_config(args, case, ws) -> dict:
+    """The `config` of the bench line; the reference arm prints the same one."""
+    N = case.nodes
+    return {
+        "workload": f"{args.workload} {case['nx']}x{case['ny']} {args.precision} populations",
+        "storage": STORAGE[args.precision],
+        **describe(case),
+        "nodes": N,
+        "l2": f"inputs larger than L2 (no flush): state {N * BYTES_PER_LU[args.precision] / 1e6:.0f}"
+              f" MB vs {L2_BYTES / 1e6:.0f} MB L2",
+        "timed_region": "the K steps, queued behind a device spin issued after the "
+                        "synchronize (host submission latency outside the region)",
+        "parallelism": f"replicas x{ws}",
+    }
+
+
 def run_reference(args):
     ws, rank, _ = dist_setup()
     if rank != 0:
@@ -600,13 +605,12 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded initial fields of the paper's setup; no dataset)",
-        "config": {"workload": f"{args.workload} {case['nx']}x{case['ny']} {args.precision} "
-                               f"populations", **describe(case), "nodes": case.nodes,
-                   "parallelism": "host cores (OpenMP over rows)"},
+        "config": line_config(args, case, ws),
         "impl": "reference",
         "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": O.num_threads(),
                          "kind": "oracle",
-                         "sample": f"each step: one time step of rows [{y0},{y1}) of the grid"},
+                         "sample": f"each step: one time step of rows [{y0},{y1}) of the grid, "
+                                   f"on the host cores (OpenMP over rows)"},
         "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
