@@ -60,3 +60,22 @@ def test_reference_arm_under_torchrun_prints_once_from_rank_0():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_prints_the_config_of_the_bench_line():
+    """Both arms describe the same workload: the reference line's config is the one the GPU arm
+    builds for the same flags (the GPU arm itself needs a GPU; its config comes from the same
+    builder)."""
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3",
+           "--precision", "fp16"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    args = argparse.Namespace(workload="impact", precision="fp16")
+    assert d["config"] == json.loads(json.dumps(
+        bench.line_config(args, bench.workload("impact"), 1)))
+    assert d["config"]["storage"] == bench.STORAGE["fp16"]
+    assert d["metric"] == bench.METRIC and d["unit"] == "MLUPS" and d["higher_is_better"]
